@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""LOVE on GB300: predictive variances/sec at 1M test points + pre-compute ms.
+
+Workload (1-D KISS-GP, FP32): n = 1,000,000 training points, m = 10,000 grid
+points (Toeplitz K_UU), k = 100 Lanczos steps with full reorthogonalisation;
+predictive mean and variance at t = 1,000,000 test points, then 1,000
+posterior samples at 10,000 test points through the low-rank root.  Inputs are
+seeded synthetic data (see workloads/), resident in HBM before timing.
+
+One step = the whole hot path once: ski_build (cell sort) + love_precompute
+(probe, Lanczos + reorth, T = LL^T, cache, mean CG, sampler) +
+love_predict_mean_var (1M points) + love_sample (1000 x 10,000).  L2 is
+flushed (a 256 MB write) before every step, outside the event-timed phases.
+
+  value        predictive variances/sec of love_predict_mean_var at 1M test
+               points (after pre-compute), device-resident inputs, summed over ranks
+  precompute_ms  device time of love_precompute per step
+  e2e          the same predict metric through the public API with pinned host
+               buffers: H2D of x*, predict, D2H of mean and var, per step
+  roofline     the predict kernel: algorithmic bytes (d*4 + 8 + 4^d (k+1) 4 per
+               point) / its CUDA-event time, against the measured HBM copy peak
+
+--impl reference times the FP64 CPU oracle (numpy) on the host cores on the
+same metric: oracle predict on the 1M test points with an oracle cache from a
+200,000-point training subsample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "predictive variances/sec at 1M test pts + precompute ms; % HBM roofline"
+UNIT = "variances/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _profile_traffic(name):
+    """dram bytes per launch from a committed ncu summary (line 'traffic_bytes_per_launch: N')."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    for ln in open(p):
+        if ln.strip().startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(ln.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        loaded = [s for s in sm if s > 0.5 * (mx or max(sm))] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle(wl, n_sample=200_000, t_sample=None, reps=1):
+    """FP64 oracle (numpy) on the host cores: pre-compute on a training subsample,
+    then predict throughput on the test points."""
+    import numpy as np
+    from oracle import grid as og
+    from oracle import love as ol
+    from oracle import ski as os_
+    x = wl.x_train()
+    y = wl.y_train(x)
+    xs = wl.x_test()
+    if t_sample:
+        xs = xs[:t_sample]
+    t0 = time.perf_counter()
+    ski = os_.SKI(og.grid_from_workload(wl), x[:n_sample], wl.noise, y[:n_sample])
+    cache = ol.precompute(ski, k=wl.k, want_mean=True)
+    pre_s = time.perf_counter() - t0
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ol.predict(cache, xs)
+        times.append(time.perf_counter() - t0)
+    return {"vars_per_s": xs.shape[0] / min(times), "precompute_s": pre_s, "t": xs.shape[0],
+            "n_sample": n_sample, "times": times, "cores": os.cpu_count(), "np": np}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import workloads
+    wl = workloads.C2
+    import numpy as np
+    from oracle import grid as og
+    from oracle import love as ol
+    from oracle import ski as os_
+    x = wl.x_train()
+    y = wl.y_train(x)
+    xs = wl.x_test()
+    n_s = 200_000
+    t0 = time.perf_counter()
+    cache = ol.precompute(os_.SKI(og.grid_from_workload(wl), x[:n_s], wl.noise, y[:n_s]), k=wl.k,
+                          want_mean=True)
+    pre_ms = (time.perf_counter() - t0) * 1e3
+    for _ in range(args.warmup):
+        ol.predict(cache, xs)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ol.predict(cache, xs)
+        times.append(time.perf_counter() - t0)
+    per = statistics.mean(times)
+    value = xs.shape[0] / per
+    sample = (f"FP64 numpy oracle: LOVE predict (mean+var) on all {xs.shape[0]} test points per step; "
+              f"cache from an oracle pre-compute (k={wl.k}) on the first {n_s} of the {wl.n} training points")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "precompute_ms": pre_ms,
+            "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "k": wl.k, "t": int(xs.shape[0]),
+                       "precompute_sample_n": n_s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1803_06058_gb300 as love
+    import workloads
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    wl = workloads.C2
+    t = wl.t
+    # ---- inputs (host, pinned) and their device copies
+    x_h = torch.tensor(wl.x_train(), dtype=torch.float32).pin_memory()
+    y_h = torch.tensor(wl.y_train(), dtype=torch.float32).pin_memory()
+    xs_h = torch.tensor(wl.x_test(), dtype=torch.float32).pin_memory()
+    xq_h = torch.tensor(wl.x_sample(), dtype=torch.float32).pin_memory()
+    x_d, y_d, xs_d, xq_d = (a.to(dev) for a in (x_h, y_h, xs_h, xq_h))
+    mean_d = torch.empty(t, dtype=torch.float32, device=dev)
+    var_d = torch.empty(t, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    lib = love.lib()
+    sampler = [True]
+
+    def step(seed):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record()
+        ski = love.ski_build(x_d, y_d, wl.grid_size, wl.grid_lo, wl.grid_hi, wl.lengthscale,
+                             wl.outputscale, wl.noise)
+        ev[1].record()
+        try:
+            cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=sampler[0],
+                                         sampler_seed=seed)
+        except love.LoveError as e:
+            if e.status != 9 or not sampler[0]:
+                raise
+            sampler[0] = False
+            cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=False)
+        ev[2].record()
+        love.love_predict_mean_var(cache, xs_d, out_mean=mean_d, out_var=var_d)
+        ev[3].record()
+        smp = love.love_sample(cache, xq_d, wl.s, seed=seed) if sampler[0] else None
+        ev[4].record()
+        return ev, cache, smp
+
+    for i in range(args.warmup):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    launches0 = lib.love_launch_count()
+    w0 = time.perf_counter()
+    records = []
+    phases = []
+    for i in range(args.steps):
+        flush.zero_()
+        ev, cache, smp = step(1000 + i)
+        records.append(ev)
+        inf_ = cache.info()
+        phases.append(inf_["phase_ms"])
+        cg_iters = inf_["cg_iters"]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - w0
+    launches = lib.love_launch_count() - launches0
+    clocks = clk.stop()
+    ph = {"ski_build": [], "precompute": [], "predict": [], "sample": [], "step": []}
+    for ev in records:
+        ph["ski_build"].append(ev[0].elapsed_time(ev[1]))
+        ph["precompute"].append(ev[1].elapsed_time(ev[2]))
+        ph["predict"].append(ev[2].elapsed_time(ev[3]))
+        ph["sample"].append(ev[3].elapsed_time(ev[4]))
+        ph["step"].append(ev[0].elapsed_time(ev[4]))
+    mean_ms = {k: statistics.mean(v) for k, v in ph.items()}
+    pnames = ["lanczos", "mean_cg", "cache_build", "sampler"]
+    pre_split = {nm: statistics.mean(p[i] for p in phases) for i, nm in enumerate(pnames)}
+    # ---- predict kernel alone, repeated, for the roofline (L2 flushed before each)
+    pe = []
+    for _ in range(max(5, args.steps)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        love.love_predict_mean_var(cache, xs_d, out_mean=mean_d, out_var=var_d)
+        b.record()
+        torch.cuda.synchronize()
+        pe.append(a.elapsed_time(b))
+    pred_ms = statistics.median(pe)
+    # ---- e2e through the public API with host buffers
+    mean_h = torch.empty(t, dtype=torch.float32).pin_memory()
+    var_h = torch.empty(t, dtype=torch.float32).pin_memory()
+    ee = []
+    for i in range(max(3, args.steps)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        xs_in = xs_h.to(dev, non_blocking=True)
+        m_, v_ = love.love_predict_mean_var(cache, xs_in)
+        mean_h.copy_(m_, non_blocking=True)
+        var_h.copy_(v_, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        ee.append(a.elapsed_time(b))
+    e2e_ms = statistics.median(ee)
+
+    def red_max(v):
+        if world == 1:
+            return v
+        tt = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    pred_step_ms = red_max(mean_ms["predict"])
+    step_ms = red_max(mean_ms["step"])
+    pre_ms = red_max(mean_ms["precompute"])
+    pred_ms = red_max(pred_ms)
+    e2e_ms = red_max(e2e_ms)
+    wall = red_max(wall)
+    value = world * t / (pred_step_ms * 1e-3)
+    dim, k_eff = 1, cache.info()["k_eff"]
+    bytes_per_pt = dim * 4 + 8 + 4 ** dim * (k_eff + 1) * 4
+    achieved = bytes_per_pt * t / (pred_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            c = cpu_oracle(wl, n_sample=200_000)
+            cpu = {"value": c["vars_per_s"], "unit": UNIT, "cores": c["cores"], "kind": "oracle",
+                   "sample": (f"FP64 numpy oracle: LOVE predict on all {c['t']} test points, cache from an "
+                              f"oracle pre-compute (k={wl.k}) on the first {c['n_sample']} training points "
+                              f"({c['precompute_s']:.1f} s)")}
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "precompute_ms": pre_ms,
+               "precompute_split_ms": pre_split,
+               "variance_precompute_ms": pre_split["lanczos"] + pre_split["cache_build"],
+               "phase_ms": {k: red_max(v) if world > 1 else v for k, v in mean_ms.items()},
+               "predict_kernel_ms": pred_ms,
+               "from_scratch_vars_per_s": world * t / (step_ms * 1e-3),
+               "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "k": wl.k, "k_eff": k_eff,
+                          "t": t, "s": wl.s if sampler[0] else 0, "t_sample": wl.t_sample, "cg_iters": cg_iters,
+                          "cache_dtype": "f32",
+                          "l2": "flushed before every step and every predict timing (256 MB write)",
+                          "parallelism": f"replicas x{world} (each rank: full step on its own copy)"},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "peak_kind": peak_kind,
+                            "bytes_per_point": bytes_per_pt,
+                            "traffic": _profile_traffic("predict_c2_ncu.md"),
+                            "note": "cache (4 MB) is L2-resident; achieved counts algorithmic bytes"},
+               "e2e": {"value": world * t / (e2e_ms * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": int(t * 4), "d2h_bytes_per_step": int(t * 8)},
+               "gpu_launches": int(launches),
+               "clocks": clocks, "wall_s": wall,
+               "cpu_baseline": cpu}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * love.h -- C ABI of the GB300 (sm_103a) implementation of LOVE
+ * (LanczOs Variance Estimates) for KISS-GP.
+ *
+ * Paper: Pleiss, Gardner, Weinberger, Wilson, "Constant-Time Predictive
+ * Distributions for Gaussian Processes", ICML 2018.
+ *
+ * Phases follow the paper's pre-compute / test split (Sec. 3, "pre-compute
+ * phase and test phase"):
+ *   ski_build              KISS-GP structure of the training set (Sec. 2.3, eq. ski)
+ *   love_precompute        Lanczos on W^T K_UU W + s^2 I, caches (Sec. 3.2, Algorithm 1)
+ *   love_predict_mean_var  O(k) predictive mean and variance (eqs. pred_mean_ski,
+ *                          pred_covar_ski_fast; Algorithm 1)
+ *   love_sample            posterior samples via the low-rank root (Sec. 3.3, eq. sample)
+ *   love_var_backward      vector-Jacobian product of the variances (not in the
+ *                          paper; derived from eq. pred_covar_ski_cache)
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named x_*, y_*, v, out, mean, var, grad_* are DEVICE pointers
+ *     owned by the caller unless the comment says "host".  They must stay valid
+ *     until the work enqueued on `stream` has finished.
+ *   - Arrays are dense, row-major, with the element type of the handle's dtype
+ *     (LOVE_F32 -> float, LOVE_F64 -> double).  Point sets are t x d (d = dim).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     stream-ordered and asynchronous unless stated.
+ *   - Every call returns a love_status; no C++ exception crosses the ABI.
+ *     Argument and launch errors are returned synchronously.  Errors found by
+ *     a kernel (a point outside the interpolable grid, a NaN, a non-positive
+ *     Cholesky pivot, an expired bounded wait) are recorded in the handle's
+ *     device status word, read by love_get_device_status().
+ *   - Handles are not safe for concurrent use from several host threads.
+ */
+#ifndef LOVE_H_
+#define LOVE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LOVE_API __attribute__((visibility("default")))
+#else
+#define LOVE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* love_stream_t;   /* == cudaStream_t */
+
+typedef enum {
+  LOVE_OK = 0,
+  LOVE_ERR_ARG = 1,        /* invalid argument (NULL, size, dim, dtype)            */
+  LOVE_ERR_DOMAIN = 2,     /* a point whose 4-point stencil leaves the grid, or NaN */
+  LOVE_ERR_NOT_PD = 3,     /* non-positive pivot in the tridiagonal Cholesky        */
+  LOVE_ERR_NAN = 4,        /* NaN/Inf met in a reduction                            */
+  LOVE_ERR_OOM = 5,        /* allocation failed                                     */
+  LOVE_ERR_CUDA = 6,       /* a CUDA runtime error (see love_last_cuda_error)       */
+  LOVE_ERR_TIMEOUT = 7,    /* a bounded device wait expired                         */
+  LOVE_ERR_STATE = 8,      /* the handle lacks what the call needs                  */
+  LOVE_ERR_UNSUPPORTED = 9 /* configuration outside what this build implements      */
+} love_status;
+
+typedef enum { LOVE_F32 = 0, LOVE_F64 = 1, LOVE_BF16 = 2 } love_dtype;
+
+/* Device-memory provider.  alloc returns a device pointer of at least `bytes`
+ * bytes usable on `stream` (NULL on failure -> LOVE_ERR_OOM); free releases it.
+ * With a NULL allocator the library uses cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+  void* (*alloc)(void* ctx, size_t bytes, love_stream_t stream);
+  void (*free)(void* ctx, void* ptr, size_t bytes, love_stream_t stream);
+  void* ctx;
+} love_allocator;
+
+/* KISS-GP description (Sec. 2.3).  The grid of dimension e has grid_size[e]
+ * points at grid_lo[e] + j h_e, h_e = (grid_hi[e] - grid_lo[e]) / (grid_size[e]-1);
+ * the grid linear index is row-major over dimensions (last fastest).  The
+ * kernel is the product RBF  outputscale * prod_e exp(-(x_e - x'_e)^2 / (2 l_e^2)),
+ * so K_UU is a Kronecker product of symmetric Toeplitz factors. */
+typedef struct {
+  int dim;                    /* 1..3                                        */
+  int64_t n;                  /* training points (>= 1)                      */
+  int64_t grid_size[3];       /* points per dimension (>= 4)                 */
+  double grid_lo[3];
+  double grid_hi[3];
+  double outputscale;         /* s_f > 0                                     */
+  double lengthscale[3];      /* l_e > 0                                     */
+  double noise;               /* sigma^2 > 0                                 */
+  love_dtype dtype;           /* LOVE_F32 or LOVE_F64: x, y and the Lanczos  */
+  const love_allocator* allocator;  /* NULL -> cudaMallocAsync             */
+} love_ski_desc;
+
+typedef struct love_ski* love_ski_t;
+typedef struct love_cache* love_cache_t;
+
+/* ski_build -- sort the training set by interpolation cell and prepare K_UU.
+ * (Sec. 2.3, eq. ski: W_X holds the cubic interpolation weights of each x;
+ * K_UU is Toeplitz / Kronecker-Toeplitz on the regular grid.)
+ * x_train: n x dim device array (dtype); y_train: n device array or NULL.
+ * Copies what it needs; the caller may free x_train/y_train on return.
+ * Synchronises `stream` once.  Returns LOVE_ERR_DOMAIN if a training point's
+ * stencil leaves the grid or is NaN.  *out is owned by the caller and freed
+ * with ski_destroy. */
+LOVE_API love_status ski_build(const love_ski_desc* desc, const void* x_train,
+                      const void* y_train, love_stream_t stream, love_ski_t* out);
+LOVE_API love_status ski_destroy(love_ski_t ski);
+
+/* ski_mvm -- out = (W^T K_UU W + sigma^2 I) v   (Algorithm 1's mvm_K_XX).
+ * v, out: n device arrays in the caller's training-point order.  May not alias. */
+LOVE_API love_status ski_mvm(love_ski_t ski, const void* v, void* out, love_stream_t stream);
+
+/* ski_mvm_kuu -- out = K_UU v for m = prod(grid_size) grid values (Sec. 2.3,
+ * Toeplitz/Kronecker MVM by FFT).  v, out: m device arrays (dtype). */
+LOVE_API love_status ski_mvm_kuu(love_ski_t ski, const void* v, void* out, love_stream_t stream);
+
+/* Flags of love_precompute_opts.flags */
+#define LOVE_WANT_MEAN 0x1u     /* solve K^ z = y by CG, cache a = K_UU W z   */
+#define LOVE_WANT_SAMPLER 0x2u  /* Lanczos on K_UU - R^T R', cache S          */
+#define LOVE_WANT_GRAD 0x4u     /* keep P = W Q L^{-T} for love_var_backward  */
+#define LOVE_PRIOR_EXACT 0x8u   /* prior k(x*,x*) = s_f instead of w^T K_UU w */
+
+typedef struct {
+  int k;                   /* Lanczos steps (1..200)                           */
+  love_dtype cache_dtype;  /* F32, BF16 (with an F32 ski) or F64 (F64 ski)     */
+  unsigned flags;
+  double breakdown_tol;    /* stop when beta_j <= tol * max|alpha|; <=0: 1e-12 (F64) / 1e-8 (F32) */
+  double cg_tol;           /* relative residual of the FP64 CG; <=0: 1e-12 (F64 ski) / 1e-8 (F32 ski) */
+  int cg_max_iter;         /* <=0: 4000                                        */
+  int sampler_k;           /* Lanczos steps for S; <=0: k                      */
+  uint64_t sampler_seed;   /* SplitMix64 seed of the Rademacher probe          */
+} love_precompute_opts;
+
+/* love_precompute -- the LOVE pre-compute phase (Sec. 3.2, Algorithm 1):
+ * k Lanczos steps with full reorthogonalisation (Sec. 5) on K^ from the probe
+ * b = (1/m) W^T K_UU 1; T = L L^T; the variance cache Rt = K_UU W Q L^{-T}
+ * (so Rt Rt^T = R^T R'), the mean cache a (eq. pred_mean_ski) and optionally
+ * the sampler root S (Sec. 3.3).  Synchronises `stream` once at the end and
+ * writes the number of steps kept (<= k, fewer after a Lanczos breakdown) to
+ * *k_eff (host pointer, may be NULL).  Returns LOVE_ERR_NOT_PD if T is not
+ * positive definite.  *out is freed with love_cache_destroy.  The ski handle
+ * may be destroyed afterwards; the cache does not reference it. */
+LOVE_API love_status love_precompute(love_ski_t ski, const love_precompute_opts* opts,
+                            love_stream_t stream, love_cache_t* out, int* k_eff);
+LOVE_API love_status love_cache_destroy(love_cache_t cache);
+
+/* love_predict_mean_var -- for each of t test points (t x dim device array,
+ * the ski dtype): mean = w*^T a (eq. pred_mean_ski; requires LOVE_WANT_MEAN,
+ * else pass mean = NULL) and var = p(x*) - |Rt^T w*|^2 (eq. pred_covar_ski_fast
+ * with i = j; Algorithm 1), p the SKI prior w*^T K_UU w* (or s_f with
+ * LOVE_PRIOR_EXACT).  Outputs are t device arrays in the ski dtype.  var is
+ * clamped at 0 (the clamp count is in the device status).  A point whose stencil
+ * leaves the grid gets NaN and sets LOVE_ERR_DOMAIN in the device status.
+ * t = 0 is a no-op. */
+LOVE_API love_status love_predict_mean_var(love_cache_t cache, int64_t t, const void* x_test,
+                                  void* mean, void* var, love_stream_t stream);
+
+/* love_sample -- s posterior samples at t test points (Sec. 3.3, eq. sample):
+ * out[j, i] = mean_i + (W*^T S z)_{i j}, out an s x t device array (sample-major,
+ * ski dtype).  z: k_s x s device array of standard normals (row-major, float for
+ * an F32 ski, double for F64), or NULL to draw them on the device from
+ * Philox4x32-10 with `seed` (Box-Muller).  Requires LOVE_WANT_SAMPLER. */
+LOVE_API love_status love_sample(love_cache_t cache, int64_t t, const void* x_test, int s,
+                        const void* z, uint64_t seed, void* out, love_stream_t stream);
+
+/* love_var_backward -- vector-Jacobian product of L = sum_i g_i var_i (not in
+ * the paper; derived from eq. pred_covar_ski_cache with K^^{-1} ~ Q T^{-1} Q^T,
+ * Q held fixed):
+ *   grad_x[i, e]      = g_i d var_i / d x*_{i,e}                (t x dim, may be NULL)
+ *   grad_lengthscale  = dL / d l_e  (HOST array of dim doubles, may be NULL)
+ *   grad_noise        = dL / d sigma^2 (HOST double, may be NULL)
+ * grad_var: t device array (ski dtype).  Requires LOVE_WANT_GRAD.  Synchronises
+ * `stream` when a host output is requested. */
+LOVE_API love_status love_var_backward(love_cache_t cache, int64_t t, const void* x_test,
+                              const void* grad_var, void* grad_x,
+                              double* grad_lengthscale, double* grad_noise,
+                              love_stream_t stream);
+
+/* Cache description, filled by love_cache_info (host struct). */
+typedef struct {
+  int dim;
+  int64_t grid_size[3];
+  int64_t m;
+  int k_eff;               /* columns of Rt                                   */
+  int ld;                  /* row stride (elements) of the predict cache      */
+  int sampler_k;           /* columns of S (0 if absent)                      */
+  int cg_iters;            /* CG iterations used for the mean (0 if absent)   */
+  int sampler_fallback;    /* 1 if T' was not PD and S came from its eigenpairs */
+  love_dtype dtype;        /* ski dtype                                       */
+  love_dtype cache_dtype;
+  unsigned flags;
+  /* device time (ms, CUDA events) of the pre-compute phases: [0] Lanczos with
+   * reorthogonalisation (incl. probe), [1] mean CG, [2] cache build (and the
+   * gradient tables), [3] sampler; 0 for a cache that was imported or loaded */
+  float phase_ms[4];
+} love_cache_info_t;
+
+LOVE_API love_status love_cache_info(love_cache_t cache, love_cache_info_t* info);
+
+/* love_cache_import -- build a cache from HOST arrays instead of running the
+ * pre-compute (used to check the test-phase kernels against an independently
+ * computed cache).  Rt: m x k row-major doubles; a: m doubles or NULL; S: m x ks
+ * doubles or NULL; alpha (k), beta (k-1): the tridiagonal T (for gradients and
+ * the noise derivative), P: m x k doubles or NULL.  Values are rounded to
+ * cache_dtype.  The grid and kernel come from `desc` (n is ignored). */
+LOVE_API love_status love_cache_import(const love_ski_desc* desc, int k, love_dtype cache_dtype,
+                              unsigned flags, const double* Rt, const double* a,
+                              int ks, const double* S, const double* alpha,
+                              const double* beta, const double* P,
+                              love_stream_t stream, love_cache_t* out);
+
+/* love_cache_export -- copy cache contents to HOST arrays (any may be NULL):
+ * Rt (m x k_eff), a (m), S (m x sampler_k), P (m x k_eff) as doubles, row-major;
+ * alpha (k_eff), beta (k_eff - 1).  Synchronises `stream`. */
+LOVE_API love_status love_cache_export(love_cache_t cache, double* Rt, double* a, double* S,
+                              double* P, double* alpha, double* beta,
+                              love_stream_t stream);
+
+/* love_cache_save / love_cache_load -- a versioned, self-describing binary file
+ * holding the grid, hyperparameters, alpha, beta and the cached matrices
+ * (checkpoint of the pre-compute, which the paper runs as part of training).
+ * Save/load round-trips bit-exactly.  Both synchronise `stream`. */
+LOVE_API love_status love_cache_save(love_cache_t cache, const char* path, love_stream_t stream);
+LOVE_API love_status love_cache_load(const char* path, const love_allocator* allocator,
+                            love_stream_t stream, love_cache_t* out);
+
+/* Device status: bit (1 << status) for each error a kernel recorded since the
+ * last reset, plus the count of points with a domain error and of clamped
+ * negative variances.  Synchronises `stream`.  reset != 0 clears them. */
+typedef struct {
+  uint32_t bits;
+  int64_t domain_errors;
+  int64_t clamped;
+} love_device_status_t;
+
+LOVE_API love_status love_get_device_status(love_cache_t cache, int reset, love_device_status_t* st,
+                                   love_stream_t stream);
+
+/* Host-side helpers. */
+LOVE_API const char* love_status_string(love_status s);
+LOVE_API int love_last_cuda_error(void);            /* last cudaError_t seen by the library */
+/* Number of kernels this library has launched in this process (all entry
+ * points, all devices); a host-side counter, no synchronisation. */
+LOVE_API uint64_t love_launch_count(void);
+LOVE_API const char* love_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOVE_H_ */

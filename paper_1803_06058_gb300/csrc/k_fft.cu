@@ -1,0 +1,468 @@
+// k_fft.cu -- K_UU matrix-vector products by FFT (Sec. 2.3: a regular grid makes
+// K_UU Toeplitz, or a Kronecker product of Toeplitz factors, so K_UU v costs
+// O(m log m)).
+//
+// Each factor T_e (g x g, symmetric Toeplitz, first column c) is embedded in a
+// circulant of power-of-two length N >= 2g - 1 whose first column is
+// c[0..g-1], zeros, c[g-1..1].  T_e v = first g entries of
+// IFFT(lambda .* FFT([v; 0])) with lambda = FFT(circulant column), real because
+// the column is symmetric.  A Kronecker K_UU applies one such product per mode
+// to every fibre of that mode.
+//
+// Two kernel shapes:
+//   * short modes (N <= 4096): one CTA transforms F fibres entirely in shared
+//     memory (DIT forward on bit-reversed input, pointwise lambda, DIF inverse
+//     giving bit-reversed output) -- one launch per mode.
+//   * long modes: the four-step split N = N1 N2 in three launches:
+//     A  length-N2 FFTs over n2 for each n1, times the twiddle W_N^{n1 k2}
+//     B  length-N1 FFTs over n1 for each k2, times lambda, inverse length-N1 FFTs
+//     C  conjugate twiddles, inverse length-N2 FFTs, real part, crop to g.
+// The twiddle table W_N^j and lambda are computed once per grid in FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "love_internal.cuh"
+
+namespace love {
+namespace {
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+
+__device__ __forceinline__ int bitrev(int i, int logL) { return (int)(__brev((unsigned)i) >> (32 - logL)); }
+
+// F interleaved arrays x[i * F + f] of length L; decimation in time on
+// bit-reversed input, natural-order output.  tw: master table W_N^j.
+template <typename C>
+__device__ void fft_dit(C* x, int L, int logF, const C* __restrict__ tw, int N, bool inverse) {
+  const int F = 1 << logF;
+  const int work = (L >> 1) << logF;
+  for (int half = 1; half < L; half <<= 1) {
+    const int tws = N / (2 * half);
+    for (int t = threadIdx.x; t < work; t += blockDim.x) {
+      int f = t & (F - 1), b = t >> logF;
+      int j = b & (half - 1);
+      int i1 = ((b - j) << 1) + j, i2 = i1 + half;
+      C w = tw[j * tws];
+      if (inverse) w.y = -w.y;
+      C a = x[(i1 << logF) + f];
+      C c = cmul(x[(i2 << logF) + f], w);
+      x[(i1 << logF) + f] = cadd(a, c);
+      x[(i2 << logF) + f] = csub(a, c);
+    }
+    __syncthreads();
+  }
+}
+// decimation in frequency: natural-order input, bit-reversed output
+template <typename C>
+__device__ void fft_dif(C* x, int L, int logF, const C* __restrict__ tw, int N, bool inverse) {
+  const int F = 1 << logF;
+  const int work = (L >> 1) << logF;
+  for (int half = L >> 1; half >= 1; half >>= 1) {
+    const int tws = N / (2 * half);
+    for (int t = threadIdx.x; t < work; t += blockDim.x) {
+      int f = t & (F - 1), b = t >> logF;
+      int j = b & (half - 1);
+      int i1 = ((b - j) << 1) + j, i2 = i1 + half;
+      C w = tw[j * tws];
+      if (inverse) w.y = -w.y;
+      C a = x[(i1 << logF) + f];
+      C c = x[(i2 << logF) + f];
+      x[(i1 << logF) + f] = cadd(a, c);
+      x[(i2 << logF) + f] = cmul(csub(a, c), w);
+    }
+    __syncthreads();
+  }
+}
+
+// address of element i of fibre `fid` of column `col` along mode e
+struct ModeGeom {
+  int64_t g;        // length of the mode
+  int64_t stride;   // stride of the mode
+  int64_t nfib;     // fibres per column = m / g
+  int64_t ldc;      // column stride
+  __device__ __forceinline__ int64_t offset(int64_t col, int64_t fid, int64_t i) const {
+    int64_t outer = fid / stride, inner = fid - outer * stride;
+    return col * ldc + outer * (g * stride) + i * stride + inner;
+  }
+};
+
+// ----- short modes: whole transform in shared memory -----------------------
+template <typename IO, typename R>
+__global__ void k_toep_small(const IO* __restrict__ in, IO* __restrict__ out, ModeGeom mg, int64_t total_fib,
+                             int N, int logN, int logF, const typename Cplx<R>::type* __restrict__ tw,
+                             const R* __restrict__ lam) {
+  using C = typename Cplx<R>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const int F = 1 << logF;
+  const int64_t fib0 = (int64_t)blockIdx.x * F;
+  // load (fibre fastest), zero padded, into bit-reversed slots
+  for (int t = threadIdx.x; t < (N << logF); t += blockDim.x) {
+    int f = t & (F - 1), i = t >> logF;
+    int64_t fb = fib0 + f;
+    R v = R(0);
+    if (i < mg.g && fb < total_fib) {
+      int64_t col = fb / mg.nfib, fid = fb - col * mg.nfib;
+      v = (R)in[mg.offset(col, fid, i)];
+    }
+    C c;
+    c.x = v;
+    c.y = R(0);
+    x[(bitrev(i, logN) << logF) + f] = c;
+  }
+  __syncthreads();
+  fft_dit(x, N, logF, tw, N, false);
+  for (int t = threadIdx.x; t < (N << logF); t += blockDim.x) {
+    int i = t >> logF;
+    R l = lam[i];
+    x[t].x *= l;
+    x[t].y *= l;
+  }
+  __syncthreads();
+  fft_dif(x, N, logF, tw, N, true);
+  for (int t = threadIdx.x; t < (N << logF); t += blockDim.x) {
+    int f = t & (F - 1), i = t >> logF;
+    int64_t fb = fib0 + f;
+    if (i < mg.g && fb < total_fib) {
+      int64_t col = fb / mg.nfib, fid = fb - col * mg.nfib;
+      out[mg.offset(col, fid, i)] = (IO)x[(bitrev(i, logN) << logF) + f].x;
+    }
+  }
+}
+
+// ----- long modes: four-step -------------------------------------------------
+// A: for each n1 in a group of FA, FFT over n2 of x[n1 + N1 n2], times W_N^{n1 k2};
+//    work[fb][k2 * N1 + n1]
+template <typename IO, typename R>
+__global__ void k_four_a(const IO* __restrict__ in, typename Cplx<R>::type* __restrict__ work, ModeGeom mg,
+                         int N, int N1, int N2, int logN2, int logFA,
+                         const typename Cplx<R>::type* __restrict__ tw) {
+  using C = typename Cplx<R>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const int FA = 1 << logFA;
+  const int n1_0 = blockIdx.x * FA;
+  const int64_t fb = blockIdx.y;
+  const int64_t col = fb / mg.nfib, fid = fb - col * mg.nfib;
+  for (int t = threadIdx.x; t < (N2 << logFA); t += blockDim.x) {
+    int f = t & (FA - 1), n2 = t >> logFA;
+    int64_t idx = (int64_t)(n1_0 + f) + (int64_t)N1 * n2;
+    C c;
+    c.x = R(0);
+    c.y = R(0);
+    if (idx < mg.g) c.x = (R)in[mg.offset(col, fid, idx)];
+    x[(bitrev(n2, logN2) << logFA) + f] = c;
+  }
+  __syncthreads();
+  fft_dit(x, N2, logFA, tw, N, false);
+  C* wdst = work + fb * (int64_t)N;
+  for (int t = threadIdx.x; t < (N2 << logFA); t += blockDim.x) {
+    int f = t & (FA - 1), k2 = t >> logFA;
+    int n1 = n1_0 + f;
+    C v = x[t];
+    C w = tw[((int64_t)n1 * k2) & (N - 1)];
+    wdst[(int64_t)k2 * N1 + n1] = cmul(v, w);
+  }
+}
+
+// B: for each k2 in a group of FB rows: FFT over n1, times lambda, inverse FFT
+//    over k1 (or, with lam == nullptr, write X[k2 + N2 k1] to xout).
+template <typename R>
+__global__ void k_four_b(typename Cplx<R>::type* __restrict__ work, int N, int N1, int N2, int logN1, int logFB,
+                         const typename Cplx<R>::type* __restrict__ tw, const R* __restrict__ lam,
+                         typename Cplx<R>::type* __restrict__ xout) {
+  using C = typename Cplx<R>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const int FB = 1 << logFB;
+  const int k2_0 = blockIdx.x * FB;
+  const int64_t fb = blockIdx.y;
+  C* wrow = work + fb * (int64_t)N;
+  // load row-major (n1 fastest) for coalescing; store transposed in smem
+  for (int t = threadIdx.x; t < (N1 << logFB); t += blockDim.x) {
+    int n1 = t & (N1 - 1), f = t >> logN1;
+    x[(bitrev(n1, logN1) << logFB) + f] = wrow[(int64_t)(k2_0 + f) * N1 + n1];
+  }
+  __syncthreads();
+  fft_dit(x, N1, logFB, tw, N, false);
+  if (lam == nullptr) {
+    for (int t = threadIdx.x; t < (N1 << logFB); t += blockDim.x) {
+      int f = t & (FB - 1), k1 = t >> logFB;
+      xout[fb * (int64_t)N + (int64_t)(k2_0 + f) + (int64_t)N2 * k1] = x[t];
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < (N1 << logFB); t += blockDim.x) {
+    int f = t & (FB - 1), k1 = t >> logFB;
+    R l = lam[(k2_0 + f) + N2 * k1];
+    x[t].x *= l;
+    x[t].y *= l;
+  }
+  __syncthreads();
+  fft_dif(x, N1, logFB, tw, N, true);
+  for (int t = threadIdx.x; t < (N1 << logFB); t += blockDim.x) {
+    int n1 = t & (N1 - 1), f = t >> logN1;
+    wrow[(int64_t)(k2_0 + f) * N1 + n1] = x[(bitrev(n1, logN1) << logFB) + f];
+  }
+}
+
+// C: for each n1 in a group of FA: conjugate twiddle, inverse FFT over k2,
+//    real part of x[n1 + N1 n2] cropped to the mode length.
+template <typename IO, typename R>
+__global__ void k_four_c(const typename Cplx<R>::type* __restrict__ work, IO* __restrict__ out, ModeGeom mg, int N,
+                         int N1, int N2, int logN2, int logFA, const typename Cplx<R>::type* __restrict__ tw) {
+  using C = typename Cplx<R>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* x = reinterpret_cast<C*>(smem_raw);
+  const int FA = 1 << logFA;
+  const int n1_0 = blockIdx.x * FA;
+  const int64_t fb = blockIdx.y;
+  const int64_t col = fb / mg.nfib, fid = fb - col * mg.nfib;
+  const C* wsrc = work + fb * (int64_t)N;
+  for (int t = threadIdx.x; t < (N2 << logFA); t += blockDim.x) {
+    int f = t & (FA - 1), k2 = t >> logFA;
+    int n1 = n1_0 + f;
+    C w = tw[((int64_t)n1 * k2) & (N - 1)];
+    w.y = -w.y;
+    x[t] = cmul(wsrc[(int64_t)k2 * N1 + n1], w);
+  }
+  __syncthreads();
+  fft_dif(x, N2, logFA, tw, N, true);
+  for (int t = threadIdx.x; t < (N2 << logFA); t += blockDim.x) {
+    int f = t & (FA - 1), n2 = t >> logFA;
+    int64_t idx = (int64_t)(n1_0 + f) + (int64_t)N1 * n2;
+    if (idx < mg.g) out[mg.offset(col, fid, idx)] = (IO)x[(bitrev(n2, logN2) << logFA) + f].x;
+  }
+}
+
+// ----- plan set-up kernels ---------------------------------------------------
+__global__ void k_twiddles(double2* tw_d, float2* tw_f, int64_t N) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double s, c;
+  sincospi(-2.0 * (double)j / (double)N, &s, &c);
+  tw_d[j] = make_double2(c, s);
+  tw_f[j] = make_float2((float)c, (float)s);
+}
+// embedded circulant column of T_e (or dT_e/dl), times `scale`
+__global__ void k_embed_column(double2* out, int64_t N, int64_t g, double h, double ls, double scale, int deriv) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  int64_t r = j < g ? j : (N - j < g ? N - j : -1);
+  double v = 0.0;
+  if (r >= 0) {
+    double d = (double)r * h;
+    v = scale * exp(-(d * d) / (2.0 * ls * ls));
+    if (deriv) v *= d * d / (ls * ls * ls);
+  }
+  out[j] = make_double2(v, 0.0);
+}
+__global__ void k_lambda_store(const double2* X, int64_t N, double* lam_d, float* lam_f) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double v = X[j].x / (double)N;
+  lam_d[j] = v;
+  lam_f[j] = (float)v;
+}
+
+inline int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) ++l;
+  return l;
+}
+
+constexpr int SMALL_MAX_N = 4096;
+
+// FFTs per CTA in the four-step kernels: at most `cap` complex values per CTA
+// and at most 16 transforms
+inline int four_logF(int L, int cap) {
+  int F = std::max(1, std::min(16, cap / L));
+  int l = 0;
+  while ((2 << l) <= F) ++l;
+  return l;
+}
+
+template <typename K>
+love_status allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return LOVE_OK;
+  return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <typename R>
+int small_logF(int N) {
+  // total complex elements per CTA: 4096 (FP32, 32 KB) / 2048 (FP64, 32 KB)
+  int cap = sizeof(R) == 4 ? 4096 : 2048;
+  int F = std::max(1, cap / N);
+  return ilog2(F);
+}
+
+// One mode of K_UU applied to FP32 or FP64 data; the transform itself always
+// runs in FP64 (twiddles and lambda in FP64): K_UU is m-sized, so this costs
+// little, and it keeps the Toeplitz product accurate to the rounding of its
+// inputs and outputs (an FP32 transform of length N carries ~log2(N) 2^-24).
+template <typename IO>
+love_status toeplitz_mode(const FftPlan& p, const IO* in, IO* out, ModeGeom mg, int ncol, void* work,
+                          bool deriv, cudaStream_t s) {
+  using R = double;
+  using C = double2;
+  const C* tw = (const C*)p.tw_d;
+  const R* lam = (const R*)(deriv ? p.lamdl_d : p.lam_d);
+  const int N = (int)p.N;
+  const int64_t total = mg.nfib * ncol;
+  if (p.N2 == 1) {
+    int logF = small_logF<R>(N);
+    int F = 1 << logF;
+    size_t sm = (size_t)N * F * sizeof(C);
+    int threads = std::min(512, std::max(64, (N * F) / 4));
+    int64_t blocks = (total + F - 1) / F;
+    LOVE_TRY(allow_smem(k_toep_small<IO, R>, sm));
+    LOVE_COUNT_LAUNCH(); k_toep_small<IO, R><<<(unsigned)blocks, threads, sm, s>>>(in, out, mg, total, N, ilog2(N), logF, tw, lam);
+    return cuda_check(cudaGetLastError());
+  }
+  const int N1 = p.N1, N2 = p.N2;
+  C* wk = (C*)work;
+  const int cap = 2048;
+  int logFA = four_logF(N2, cap);
+  int FA = 1 << logFA;
+  int logFB = four_logF(N1, cap);
+  int FB = 1 << logFB;
+  dim3 ga(N1 / FA, (unsigned)total), gb(N2 / FB, (unsigned)total);
+  size_t sma = (size_t)N2 * FA * sizeof(C), smb = (size_t)N1 * FB * sizeof(C);
+  LOVE_TRY(allow_smem(k_four_a<IO, R>, sma));
+  LOVE_TRY(allow_smem(k_four_b<R>, smb));
+  LOVE_TRY(allow_smem(k_four_c<IO, R>, sma));
+  LOVE_COUNT_LAUNCH(); k_four_a<IO, R><<<ga, 256, sma, s>>>(in, wk, mg, N, N1, N2, ilog2(N2), logFA, tw);
+  LOVE_COUNT_LAUNCH(); k_four_b<R><<<gb, 256, smb, s>>>(wk, N, N1, N2, ilog2(N1), logFB, tw, lam, nullptr);
+  LOVE_COUNT_LAUNCH(); k_four_c<IO, R><<<ga, 256, sma, s>>>(wk, out, mg, N, N1, N2, ilog2(N2), logFA, tw);
+  return cuda_check(cudaGetLastError());
+}
+
+// forward FFT (FP64) of `src` (N complex, N <= 4096) into `dst`: one CTA runs
+// the DIT transform of k_four_b with N1 = N, N2 = 1 in forward-only mode.
+love_status fft_forward_small_f64(const FftPlan& p, const double2* src, double2* dst, double2* work,
+                                  cudaStream_t s) {
+  const int N = (int)p.N;
+  cudaError_t e = cudaMemcpyAsync(work, src, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_check(e);
+  size_t sm = (size_t)N * sizeof(double2);
+  LOVE_TRY(allow_smem(k_four_b<double>, sm));
+  LOVE_COUNT_LAUNCH(); k_four_b<double><<<dim3(1, 1), 256, sm, s>>>(work, N, N, 1, ilog2(N), 0, (const double2*)p.tw_d, nullptr, dst);
+  return cuda_check(cudaGetLastError());
+}
+
+__global__ void k_real_part(const double2* a, double* out, int64_t N) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < N) out[j] = a[j].x;
+}
+
+}  // namespace
+
+love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocator& al, cudaStream_t s) {
+  p.g = g.g[e];
+  int64_t N = 4;
+  while (N < 2 * p.g - 1) N <<= 1;
+  p.N = N;
+  if (N <= SMALL_MAX_N) {
+    p.N1 = (int)N;
+    p.N2 = 1;
+  } else {
+    int l = ilog2(N);
+    p.N1 = 1 << (l / 2);
+    p.N2 = (int)(N >> (l / 2));
+  }
+  if (N > (int64_t(1) << 22)) return LOVE_ERR_UNSUPPORTED;
+  p.tw_d = al.alloc(sizeof(double2) * N, s);
+  p.tw_f = al.alloc(sizeof(float2) * N, s);
+  p.lam_d = al.alloc(sizeof(double) * N, s);
+  p.lam_f = al.alloc(sizeof(float) * N, s);
+  p.lamdl_d = al.alloc(sizeof(double) * N, s);
+  p.lamdl_f = al.alloc(sizeof(float) * N, s);
+  double2* col = (double2*)al.alloc(sizeof(double2) * N, s);
+  double2* X = (double2*)al.alloc(sizeof(double2) * N, s);
+  double2* wk = (double2*)al.alloc(sizeof(double2) * N, s);
+  double* re = (double*)al.alloc(sizeof(double) * N, s);
+  if (!p.tw_d || !p.tw_f || !p.lam_d || !p.lam_f || !p.lamdl_d || !p.lamdl_f || !col || !X || !wk || !re)
+    return LOVE_ERR_OOM;
+  int nb = ceil_div(N, 256);
+  LOVE_COUNT_LAUNCH(); k_twiddles<<<nb, 256, 0, s>>>((double2*)p.tw_d, (float2*)p.tw_f, N);
+  for (int deriv = 0; deriv < 2; ++deriv) {
+    double scale = (e == 0) ? g.sf : 1.0;
+    LOVE_COUNT_LAUNCH(); k_embed_column<<<nb, 256, 0, s>>>(col, N, p.g, g.h[e], g.ls[e], scale, deriv);
+    if (p.N2 == 1) {
+      LOVE_TRY(fft_forward_small_f64(p, col, X, wk, s));
+    } else {
+      // four-step forward with a real input: A (reads real parts) then B (forward only)
+      LOVE_COUNT_LAUNCH(); k_real_part<<<nb, 256, 0, s>>>(col, re, N);
+      ModeGeom mg{N, 1, 1, N};
+      int logFA = four_logF(p.N2, 2048);
+      int logFB = four_logF(p.N1, 2048);
+      dim3 ga(p.N1 >> logFA, 1), gb(p.N2 >> logFB, 1);
+      LOVE_COUNT_LAUNCH(); k_four_a<double, double><<<ga, 256, (size_t)p.N2 * (1 << logFA) * sizeof(double2), s>>>(
+          re, wk, mg, (int)N, p.N1, p.N2, ilog2(p.N2), logFA, (const double2*)p.tw_d);
+      LOVE_COUNT_LAUNCH(); k_four_b<double><<<gb, 256, (size_t)p.N1 * (1 << logFB) * sizeof(double2), s>>>(
+          wk, (int)N, p.N1, p.N2, ilog2(p.N1), logFB, (const double2*)p.tw_d, nullptr, X);
+    }
+    LOVE_COUNT_LAUNCH(); k_lambda_store<<<nb, 256, 0, s>>>(X, N, (double*)(deriv ? p.lamdl_d : p.lam_d),
+                                      (float*)(deriv ? p.lamdl_f : p.lam_f));
+  }
+  LOVE_TRY(cuda_check(cudaGetLastError()));
+  al.free(col, sizeof(double2) * N, s);
+  al.free(X, sizeof(double2) * N, s);
+  al.free(wk, sizeof(double2) * N, s);
+  al.free(re, sizeof(double) * N, s);
+  return LOVE_OK;
+}
+
+void fft_plan_destroy(FftPlan& p, const Allocator& al, cudaStream_t s) {
+  al.free(p.tw_d, sizeof(double2) * p.N, s);
+  al.free(p.tw_f, sizeof(float2) * p.N, s);
+  al.free(p.lam_d, sizeof(double) * p.N, s);
+  al.free(p.lam_f, sizeof(float) * p.N, s);
+  al.free(p.lamdl_d, sizeof(double) * p.N, s);
+  al.free(p.lamdl_f, sizeof(float) * p.N, s);
+  p = FftPlan{};
+}
+
+size_t fft_work_bytes(const GridHost& g, const FftPlan* plans, int ncol, bool dbl) {
+  size_t best = 0;
+  for (int e = 0; e < g.dim; ++e) {
+    if (plans[e].N2 == 1) continue;
+    (void)dbl;  // the transforms always run in FP64
+    size_t b = (size_t)plans[e].N * (size_t)(g.m / g.g[e]) * (size_t)ncol * 16;
+    best = std::max(best, b);
+  }
+  return best;
+}
+
+template <typename T>
+love_status kuu_apply(const GridHost& g, const FftPlan* plans, const T* v, T* out, int ncol, int64_t ldc,
+                      void* work, int deriv_dim, cudaStream_t s) {
+  const T* src = v;
+  for (int e = 0; e < g.dim; ++e) {
+    ModeGeom mg{g.g[e], g.stride[e], g.m / g.g[e], ldc};
+    LOVE_TRY(toeplitz_mode<T>(plans[e], src, out, mg, ncol, work, e == deriv_dim, s));
+    src = out;
+  }
+  return LOVE_OK;
+}
+
+template love_status kuu_apply<float>(const GridHost&, const FftPlan*, const float*, float*, int, int64_t, void*, int,
+                                      cudaStream_t);
+template love_status kuu_apply<double>(const GridHost&, const FftPlan*, const double*, double*, int, int64_t, void*,
+                                       int, cudaStream_t);
+
+}  // namespace love

@@ -1,0 +1,1167 @@
+// k_lanczos.cu -- SKI matrix-vector products, Lanczos with full
+// reorthogonalisation, CG, and the LOVE cache build.
+//
+// Lanczos (Sec. 2.2) on K^ = W^T K_UU W + s^2 I with full reorthogonalisation
+// (Sec. 5) by classical Gram-Schmidt applied twice to the raw product:
+//   y = K^ q_j ;  c = Q_j^T y ;  y -= Q_j c ;  c' = Q_j^T y ;  y -= Q_j c'
+//   alpha_j = c_j ;  beta_j = |y| ;  q_{j+1} = y / beta_j
+// (in exact arithmetic c holds the three-term coefficients alpha_j, beta_{j-1}
+// and zeros, so pass 1 is the Lanczos recurrence plus reorthogonalisation).
+//
+// One step is five launches, all stream-ordered with every scalar kept on the
+// device (graph-capturable, no host synchronisation):
+//   scatter    u = W q_j            warp per grid node, gather over the
+//                                   cell-sorted training points (deterministic)
+//   K_UU       u = K_UU u           FFT Toeplitz / Kronecker (k_fft.cu)
+//   gather+dot y = W^T u + s^2 q_j; c = Q_j^T y
+//   update+dot y -= Q_j c;  c' = Q_j^T y
+//   update+norm y -= Q_j c';  beta = |y|;  q_{j+1} = y (scaled on next use)
+// The last three stream row tiles of Q_j (256 rows x (j+1) columns) through a
+// double-buffered shared-memory ring filled by bulk async copies (TMA, 1-D
+// form, one copy per column segment, completion on an mbarrier); Q_j is read
+// three times per step.  Dot products accumulate in double-float per thread
+// and per CTA, and CTA partials are combined by the last CTA to finish, in a
+// fixed order (deterministic, no floating-point atomics).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "love_internal.cuh"
+
+namespace love {
+
+// device-side Lanczos / CG scalars
+struct LanczosState {
+  double alpha[LOVE_MAX_K + 1];
+  double beta[LOVE_MAX_K + 1];
+  double scal[LOVE_MAX_K + 2];   // 1 / |q_j| of the stored (unnormalised) column j
+  double coef[LOVE_MAX_K + 1];   // pass-1 coefficients c
+  double coef2[LOVE_MAX_K + 1];  // pass-2 coefficients c'
+  double maxabs;
+  double tau;
+  double norm2;
+  int done;
+  int k_eff;
+  int kmax;
+  unsigned counter;
+  // CG
+  double rr, rr0, pap, cg_alpha, cg_beta, tol2;
+  int cg_done, cg_iters;
+  unsigned counter2;
+};
+
+namespace {
+
+constexpr int TILE_R = 256;     // rows per tile = threads per CTA
+constexpr int NWARP = TILE_R / 32;
+
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = DotAccF; };
+template <> struct AccOf<double> { using type = DotAccD; };
+
+__device__ __forceinline__ void acc_store(double2* p, const DotAccF& a) { *p = make_double2(a.s, a.c); }
+__device__ __forceinline__ void acc_store(double2* p, const DotAccD& a) { *p = make_double2(a.s, 0.0); }
+
+// ---------------------------------------------------------------------------
+// per-point interpolation (4^D nonzeros)
+template <typename T, int D>
+struct Stencil {
+  int base[D];
+  T w[D][4];
+  bool ok;
+  __device__ __forceinline__ void compute(const T* xp, const GridDev& g) {
+    ok = true;
+#pragma unroll
+    for (int e = 0; e < D; ++e) ok &= keys_weights(grid_coord(xp[e], g, e), g.g[e], base[e], w[e]);
+  }
+  // sum_r w_r u[node_r], weights in T, values and accumulation in V
+  template <typename V>
+  __device__ __forceinline__ V apply(const V* __restrict__ u, const GridDev& g) const {
+    V acc = V(0);
+    if (D == 1) {
+      const V* p = u + (base[0] - 1);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc += (V)w[0][r] * p[r];
+    } else if (D == 2) {
+#pragma unroll
+      for (int r0 = 0; r0 < 4; ++r0) {
+        const V* p = u + (int64_t)(base[0] - 1 + r0) * g.stride[0] + (base[1] - 1);
+        V a = V(0);
+#pragma unroll
+        for (int r1 = 0; r1 < 4; ++r1) a += (V)w[1][r1] * p[r1];
+        acc += (V)w[0][r0] * a;
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < 4; ++r0) {
+        V a0 = V(0);
+#pragma unroll
+        for (int r1 = 0; r1 < 4; ++r1) {
+          const V* p = u + (int64_t)(base[0] - 1 + r0) * g.stride[0] + (int64_t)(base[1] - 1 + r1) * g.stride[1] +
+                       (base[2] - 1);
+          V a = V(0);
+#pragma unroll
+          for (int r2 = 0; r2 < 4; ++r2) a += (V)w[2][r2] * p[r2];
+          a0 += (V)w[1][r1] * a;
+        }
+        acc += (V)w[0][r0] * a0;
+      }
+    }
+    return acc;
+  }
+};
+
+// weight of a cell-sorted point at grid node nd[] (same arithmetic as keys_weights)
+template <typename T, int D>
+__device__ __forceinline__ T node_weight(const T* xp, const GridDev& g, const int* nd) {
+  T w = T(1);
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    T s = grid_coord(xp[e], g, e);
+    int i = (int)floor(s);
+    if (i > g.g[e] - 3) i = g.g[e] - 3;
+    T f = s - T(i);
+    int r = nd[e] - (i - 1);
+    w *= keys_u(f + T(1) - T(r));
+  }
+  return w;
+}
+
+// ranges of sorted points whose stencil covers node nd[]: 4^(D-1) ranges, each
+// 4 consecutive cells of the last dimension.  Lane l < NR computes range l.
+template <int D>
+struct NodeRanges {
+  static constexpr int NR = D == 1 ? 1 : (D == 2 ? 4 : 16);
+  int lo[NR];
+  int ex[NR];  // exclusive prefix of lengths
+  int total;
+  __device__ __forceinline__ void build(const GridDev& g, const int* nd, const int* __restrict__ cell_start,
+                                        int lane) {
+    int mylo = 0, mylen = 0;
+    if (lane < NR) {
+      int64_t cbase = 0;
+      bool ok = true;
+      int rem = lane;
+#pragma unroll
+      for (int e = 0; e < D - 1; ++e) {
+        int re = rem & 3;
+        rem >>= 2;
+        int c = nd[e] - re + 1;
+        if (c < 0 || c >= g.g[e]) ok = false;
+        cbase += (int64_t)c * g.stride[e];
+      }
+      int clo = max(nd[D - 1] - 2, 0), chi = min(nd[D - 1] + 1, g.g[D - 1] - 1);
+      if (ok && clo <= chi) {
+        mylo = cell_start[cbase + clo];
+        mylen = cell_start[cbase + chi + 1] - mylo;
+      }
+    }
+    int incl = mylen;
+#pragma unroll
+    for (int o = 1; o < NR; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int excl = incl - mylen;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      lo[q] = __shfl_sync(0xffffffffu, mylo, q);
+      ex[q] = __shfl_sync(0xffffffffu, excl, q);
+    }
+    total = __shfl_sync(0xffffffffu, incl, NR - 1);
+  }
+  __device__ __forceinline__ int point(int f) const {
+    int ri = 0;
+#pragma unroll
+    for (int q = 1; q < NR; ++q)
+      if (ex[q] <= f) ri = q;
+    return lo[ri] + (f - ex[ri]);
+  }
+};
+
+template <int D>
+__device__ __forceinline__ void node_index(int64_t node, const GridDev& g, int* nd) {
+  int64_t r = node;
+#pragma unroll
+  for (int e = D - 1; e >= 0; --e) {
+    nd[e] = (int)(r % g.g[e]);
+    r /= g.g[e];
+  }
+}
+
+// u[node] = scale * sum over sorted points of w_p(node) v[p]   (u = W v).
+// A node collects ~4 n/m points in 1-D (400 on the n = 1e6, m = 1e4 grid), so
+// the sum is accumulated in double-float (Dot2) and rounded once.
+template <typename T, int D, typename V = T>
+__global__ void k_scatter(GridDev g, const T* __restrict__ xs, const int* __restrict__ cell_start,
+                          const V* __restrict__ v, const double* __restrict__ scal, V scale, V* __restrict__ u) {
+  using Acc = typename AccOf<V>::type;
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double sc = (double)scale * (scal ? *scal : 1.0);
+  for (int64_t node = wg; node < g.m; node += nw) {
+    int nd[D];
+    node_index<D>(node, g, nd);
+    NodeRanges<D> rg;
+    rg.build(g, nd, cell_start, lane);
+    Acc acc;
+    acc.zero();
+    for (int f = lane; f < rg.total; f += 32) {
+      int p = rg.point(f);
+      acc.add_prod((V)node_weight<T, D>(xs + (int64_t)p * D, g, nd), v[p]);
+    }
+    warp_merge(acc);
+    if (lane == 0) u[node] = (V)(acc.value() * sc);
+  }
+}
+
+// out[:, c] = W Q[:, c] for ncol columns (chunks of CH columns per pass),
+// double-float accumulation as in k_scatter
+template <typename T, int D, int CH>
+__global__ void k_scatter_multi(GridDev g, const T* __restrict__ xs, const int* __restrict__ cell_start,
+                                const T* __restrict__ Q, int64_t ldq, int ncol, T* __restrict__ out, int64_t ldo) {
+  using Acc = typename AccOf<T>::type;
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t node = wg; node < g.m; node += nw) {
+    int nd[D];
+    node_index<D>(node, g, nd);
+    NodeRanges<D> rg;
+    rg.build(g, nd, cell_start, lane);
+    for (int c0 = 0; c0 < ncol; c0 += CH) {
+      Acc acc[CH];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) acc[c].zero();
+      for (int f = lane; f < rg.total; f += 32) {
+        int p = rg.point(f);
+        T w = node_weight<T, D>(xs + (int64_t)p * D, g, nd);
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (c0 + c < ncol) acc[c].add_prod(w, Q[(int64_t)(c0 + c) * ldq + p]);
+      }
+      double val = 0.0;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        warp_merge(acc[c]);
+        if (lane == c) val = acc[c].value();
+      }
+      if (lane < CH && c0 + lane < ncol) out[(int64_t)(c0 + lane) * ldo + node] = (T)val;
+    }
+  }
+}
+
+// out[p] = a * sum_r w_r u[node_r] + b * v[p]   (p < n; 0 on padding rows)
+template <typename T, int D>
+__global__ void k_gather(GridDev g, const T* __restrict__ xs, int64_t n, int64_t n_pad, const T* __restrict__ u,
+                         T a, T b, const T* __restrict__ v, T* __restrict__ out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pad) return;
+  T r = T(0);
+  if (p < n) {
+    Stencil<T, D> st;
+    st.compute(xs + p * D, g);
+    r = a * st.apply(u, g);
+    if (v) r += b * v[p];
+  }
+  out[p] = r;
+}
+
+// ---------------------------------------------------------------------------
+// block reduction of a DotAcc into partial[blockIdx.x]; then the last CTA
+// merges all partials into result[0..ncols) (fixed order).  Returns true in
+// the last CTA (after the merge), so the caller can finish scalar work.
+template <typename Acc>
+__device__ __forceinline__ void block_merge(Acc& a, Acc* sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  warp_merge(a);
+  if (lane == 0) sm[w] = a;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    Acc b;
+    b.zero();
+    if (lane < nw) b = sm[lane];
+    warp_merge(b);
+    if (lane == 0) sm[0] = b;
+  }
+  __syncthreads();
+  a = sm[0];
+}
+
+template <typename Acc>
+__device__ bool last_cta_reduce(const double2* __restrict__ partial, int stride, int ncols, double* result,
+                                unsigned* counter) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = w; i < ncols; i += nw) {
+    Acc a;
+    a.zero();
+    for (int c = lane; c < (int)gridDim.x; c += 32) {
+      double2 p = __ldcg(partial + (int64_t)c * stride + i);
+      a.merge(p.x, p.y);
+    }
+    warp_merge(a);
+    if (lane == 0) result[i] = a.value();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos tile kernels
+enum { MODE_GATHER_DOT = 0, MODE_UPDATE_DOT = 1, MODE_UPDATE_NORM = 2, MODE_DOT = 3 };
+
+template <typename T>
+struct TileArgs {
+  GridDev g;
+  int64_t n, n_pad;
+  int j;
+  int kcols;          // allocated columns of Q (and of the smem tile)
+  int stages;
+  const T* xs;
+  const T* u;         // GATHER: K_UU W q_j
+  T noise;
+  T* Q;
+  int64_t ldq;
+  T* y;
+  double2* partial;   // [gridDim][kcols + 1]
+  LanczosState* st;
+  DevStatus* status;
+};
+
+template <typename T, int D, int MODE, int KPW>
+__global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(TileArgs<T> a) {
+  using Acc = typename AccOf<T>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  LanczosState* st = a.st;
+  if (st->done) return;
+  const int j = a.j;
+  const int ncols = j + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* Qs = reinterpret_cast<T*>(smem_raw);                              // [stages][kcols][R]
+  T* ys = Qs + (size_t)a.stages * a.kcols * TILE_R;                     // [R]
+  T* cf = ys + TILE_R;                                                 // [kcols]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(cf + a.kcols) + 15) & ~uintptr_t(15));  // [stages]
+  __shared__ Acc red[NWARP];
+
+  if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
+    const double* c = MODE == MODE_UPDATE_DOT ? st->coef : st->coef2;
+    for (int i = tid; i < ncols; i += TILE_R) cf[i] = (T)c[i];
+  }
+  const T scal_j = (MODE == MODE_GATHER_DOT) ? (T)st->scal[j] : T(1);
+  const int64_t ntiles = a.n_pad / TILE_R;
+  if (tid == 0) {
+    for (int s = 0; s < a.stages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const uint32_t col_bytes = TILE_R * sizeof(T);
+  auto issue = [&](int64_t tile, int s) {
+    mbar_arrive_expect_tx(&bar[s], col_bytes * (uint32_t)ncols);
+    const T* src = a.Q + tile * TILE_R;
+    T* dst = Qs + (size_t)s * a.kcols * TILE_R;
+    for (int i = 0; i < ncols; ++i) bulk_g2s(dst + (size_t)i * TILE_R, src + (int64_t)i * a.ldq, col_bytes, &bar[s]);
+  };
+  if (tid == 0) {
+    int64_t t0 = blockIdx.x;
+    for (int s = 0; s < a.stages; ++s) {
+      int64_t t = t0 + (int64_t)s * gridDim.x;
+      if (t < ntiles) issue(t, s);
+    }
+  }
+
+  Acc acc[KPW];
+#pragma unroll
+  for (int s = 0; s < KPW; ++s) acc[s].zero();
+  Acc nacc;
+  nacc.zero();
+
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int s = it % a.stages;
+    const uint32_t parity = (uint32_t)((it / a.stages) & 1);
+    bool ok = mbar_wait_bounded(&bar[s], parity);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) dev_flag(a.status, LOVE_ERR_TIMEOUT);
+      st->done = 1;
+      return;
+    }
+    T* Qt = Qs + (size_t)s * a.kcols * TILE_R;
+    const int64_t p = tile * TILE_R + tid;
+    // ---- phase A: one row per thread
+    if (MODE == MODE_GATHER_DOT || MODE == MODE_DOT) {
+      T q = Qt[(size_t)j * TILE_R + tid] * scal_j;
+      T yv;
+      if (MODE == MODE_GATHER_DOT) {
+        yv = T(0);
+        if (p < a.n) {
+          Stencil<T, D> stc;
+          stc.compute(a.xs + p * D, a.g);
+          yv = stc.apply(a.u, a.g) + a.noise * q;
+        } else {
+          q = T(0);
+        }
+        a.y[p] = yv;
+        a.Q[(int64_t)j * a.ldq + p] = q;
+      } else {
+        yv = a.y[p];
+      }
+      Qt[(size_t)j * TILE_R + tid] = q;
+      ys[tid] = yv;
+    } else {
+      T yv = a.y[p];
+      for (int i = ncols - 1; i >= 0; --i) yv = fma(-Qt[(size_t)i * TILE_R + tid], cf[i], yv);
+      if (MODE == MODE_UPDATE_DOT) {
+        a.y[p] = yv;
+        ys[tid] = yv;
+      } else {
+        if (j + 1 < a.kcols)
+          a.Q[(int64_t)(j + 1) * a.ldq + p] = yv;
+        else
+          a.y[p] = yv;
+        nacc.add_prod(yv, yv);
+      }
+    }
+    __syncthreads();
+    // ---- phase B: column dots, warp w owns columns w, w + 8, ...
+    if (MODE != MODE_UPDATE_NORM) {
+      T yr[TILE_R / 32];
+#pragma unroll
+      for (int r = 0; r < TILE_R / 32; ++r) yr[r] = ys[lane + 32 * r];
+#pragma unroll
+      for (int s2 = 0; s2 < KPW; ++s2) {
+        const int i = warp + NWARP * s2;
+        if (i < ncols) {
+          const T* qc = Qt + (size_t)i * TILE_R;
+#pragma unroll
+          for (int r = 0; r < TILE_R / 32; ++r) acc[s2].add_prod(qc[lane + 32 * r], yr[r]);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int64_t nt = tile + (int64_t)a.stages * gridDim.x;
+      if (nt < ntiles) {
+        fence_proxy_async();
+        issue(nt, s);
+      }
+    }
+  }
+
+  // ---- CTA partials
+  const int pstride = a.kcols + 1;
+  if (MODE == MODE_UPDATE_NORM) {
+    block_merge(nacc, red);
+    if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride, nacc);
+  } else {
+#pragma unroll
+    for (int s2 = 0; s2 < KPW; ++s2) {
+      const int i = warp + NWARP * s2;
+      warp_merge(acc[s2]);
+      if (lane == 0 && i < ncols) acc_store(a.partial + (int64_t)blockIdx.x * pstride + i, acc[s2]);
+    }
+  }
+  double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
+  bool last = last_cta_reduce<Acc>(a.partial, pstride, MODE == MODE_UPDATE_NORM ? 1 : ncols, result, &st->counter);
+  if (!last || tid != 0) return;
+  if (MODE == MODE_GATHER_DOT || MODE == MODE_DOT) {
+    double al = st->coef[j];
+    st->alpha[j] = al;
+    if (!isfinite(al)) {
+      dev_flag(a.status, LOVE_ERR_NAN);
+      st->done = 1;
+      st->k_eff = j;
+    }
+    st->maxabs = fmax(st->maxabs, fabs(al));
+  } else if (MODE == MODE_UPDATE_NORM) {
+    double b = sqrt(st->norm2);
+    st->beta[j] = b;
+    if (!isfinite(b)) {
+      dev_flag(a.status, LOVE_ERR_NAN);
+      st->done = 1;
+      st->k_eff = j;
+    } else if (j + 1 >= st->kmax) {
+      st->k_eff = st->kmax;
+      st->done = 1;
+    } else if (b <= st->tau * st->maxabs) {
+      st->k_eff = j + 1;
+      st->done = 1;
+    } else {
+      st->scal[j + 1] = 1.0 / b;
+    }
+  }
+}
+
+// probe b = (1/m) W^T K_UU 1 into Q[:, 0]; scal[0] = 1/|b|
+template <typename T, int D>
+__global__ void k_probe(GridDev g, const T* __restrict__ xs, int64_t n, int64_t n_pad, const T* __restrict__ u1,
+                        T* __restrict__ q0, double2* partial, LanczosState* st) {
+  using Acc = typename AccOf<T>::type;
+  __shared__ Acc red[32];
+  Acc a;
+  a.zero();
+  T inv_m = T(1) / T(g.m);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
+    T b = T(0);
+    if (p < n) {
+      Stencil<T, D> stc;
+      stc.compute(xs + p * D, g);
+      b = stc.apply(u1, g) * inv_m;
+    }
+    q0[p] = b;
+    a.add_prod(b, b);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<Acc>(partial, 1, 1, &st->norm2, &st->counter);
+  if (last && threadIdx.x == 0) st->scal[0] = 1.0 / sqrt(st->norm2);
+}
+
+__global__ void k_state_init(LanczosState* st, int kmax, double tau) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->maxabs = 0.0;
+  st->tau = tau;
+  st->done = 0;
+  st->k_eff = kmax;
+  st->kmax = kmax;
+  st->counter = 0;
+  st->counter2 = 0;
+  st->cg_done = 0;
+  st->cg_iters = 0;
+}
+
+// ---------------------------------------------------------------------------
+// CG (Sec. 2.1) for the mean cache: K^ z = y on the cell-sorted vectors.  The
+// vectors and all reductions are FP64 whatever the coordinate type T (the
+// interpolation weights stay in T, as in the Lanczos MVMs): an FP32 CG stalls
+// on this ill-conditioned system (cond(K^) ~ 1e7 on the n = 1e6 workload).
+// Ap = W^T u + s^2 p ; pAp = p . Ap
+template <typename T, int D>
+__global__ void k_cg_gather_dot(GridDev g, const T* __restrict__ xs, int64_t n, int64_t n_pad,
+                                const double* __restrict__ u, double noise, const double* __restrict__ pv,
+                                double* __restrict__ Ap, double2* partial, LanczosState* st) {
+  __shared__ DotAccD red[32];
+  if (st->cg_done) return;
+  DotAccD a;
+  a.zero();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
+    double r = 0.0;
+    if (p < n) {
+      Stencil<T, D> stc;
+      stc.compute(xs + p * D, g);
+      r = stc.apply(u, g) + noise * pv[p];
+    }
+    Ap[p] = r;
+    a.add_prod(pv[p], r);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->pap, &st->counter2);
+  if (last && threadIdx.x == 0) st->cg_alpha = st->rr / st->pap;
+}
+// x += a p ; r -= a Ap ; rr' = r.r
+__global__ void k_cg_update(int64_t n_pad, double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ pv, const double* __restrict__ Ap, double2* partial,
+                            LanczosState* st, int max_iter, DevStatus* status) {
+  __shared__ DotAccD red[32];
+  if (st->cg_done) return;
+  const double al = st->cg_alpha;
+  DotAccD a;
+  a.zero();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
+    x[p] += al * pv[p];
+    double rv = r[p] - al * Ap[p];
+    r[p] = rv;
+    a.add_prod(rv, rv);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    double rrn = st->norm2;
+    st->cg_beta = rrn / st->rr;
+    st->rr = rrn;
+    st->cg_iters += 1;
+    if (!isfinite(rrn)) {
+      dev_flag(status, LOVE_ERR_NAN);
+      st->cg_done = 1;
+    } else if (rrn <= st->tol2 || st->cg_iters >= max_iter) {
+      st->cg_done = 1;
+    }
+  }
+}
+__global__ void k_cg_pupdate(int64_t n_pad, double* __restrict__ pv, const double* __restrict__ r, LanczosState* st) {
+  if (st->cg_done) return;
+  const double be = st->cg_beta;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x)
+    pv[p] = r[p] + be * pv[p];
+}
+template <typename T>
+__global__ void k_cg_init(int64_t n_pad, const T* __restrict__ b, double* __restrict__ x, double* __restrict__ r,
+                          double* __restrict__ pv, double2* partial, LanczosState* st, double tol) {
+  __shared__ DotAccD red[32];
+  DotAccD a;
+  a.zero();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)b[p];
+    x[p] = 0.0;
+    r[p] = v;
+    pv[p] = v;
+    a.add_prod(v, v);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    st->rr = st->norm2;
+    st->rr0 = st->norm2;
+    st->tol2 = tol * tol * st->norm2;
+    st->cg_iters = 0;
+    st->cg_done = st->norm2 == 0.0 ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tridiagonal Cholesky T = L L^T (one thread, FP64): l_11 = sqrt(alpha_1),
+// e_j = beta_j / l_jj, l_{j+1,j+1} = sqrt(alpha_{j+1} - e_j^2)
+__global__ void k_tridiag_chol(const double* alpha, const double* beta, const int* k_eff_ptr, int k_fixed,
+                               double* d, double* e, DevStatus* status, int* ok) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int k = k_eff_ptr ? *k_eff_ptr : k_fixed;
+  double piv = alpha[0];
+  *ok = 1;
+  for (int j = 0; j < k; ++j) {
+    if (j > 0) {
+      e[j - 1] = beta[j - 1] / d[j - 1];
+      piv = alpha[j] - e[j - 1] * e[j - 1];
+    }
+    if (!(piv > 0.0)) {
+      dev_flag(status, LOVE_ERR_NOT_PD);
+      *ok = 0;
+      for (int q = j; q < k; ++q) d[q] = 1.0;
+      return;
+    }
+    d[j] = sqrt(piv);
+  }
+}
+
+// X L^T = A row-wise (A, X: m x k column-major, lda), i.e. L x^T = a^T per row:
+// x_0 = a_0 / d_0 ; x_c = (a_c - e_{c-1} x_{c-1}) / d_c   (FP64 scalars)
+template <typename T>
+__global__ void k_lt_solve(const T* __restrict__ A, int64_t lda, int64_t m, int k, const double* __restrict__ d,
+                           const double* __restrict__ e, T* __restrict__ X, int64_t ldx) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  double prev = 0.0;
+  for (int c = 0; c < k; ++c) {
+    double v = (double)A[(int64_t)c * lda + r];
+    if (c > 0) v -= e[c - 1] * prev;
+    prev = v / d[c];
+    X[(int64_t)c * ldx + r] = (T)prev;
+  }
+}
+
+// pack the predict cache: row r = [Rt[r, 0..k) | a[r] | 0 pad] in cache dtype
+template <typename T, typename OutT>
+__global__ void k_pack_rows(const T* __restrict__ Rt, int64_t ldr, int64_t m, int k, const double* __restrict__ a,
+                            OutT* __restrict__ out, int ld) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * ld) return;
+  int64_t r = idx / ld;
+  int c = (int)(idx - r * ld);
+  double v = 0.0;
+  if (c < k) v = (double)Rt[(int64_t)c * ldr + r];
+  else if (c == k && a) v = (double)a[r];
+  if constexpr (std::is_same<OutT, __nv_bfloat16>::value) out[idx] = __double2bfloat16(v);
+  else out[idx] = (OutT)v;
+}
+
+template <typename T>
+__global__ void k_fill(T* p, int64_t n, T v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+template <typename T>
+__global__ void k_permute_in(const T* __restrict__ v, const int32_t* __restrict__ perm, int64_t n, int64_t n_pad,
+                             T* __restrict__ out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pad) return;
+  out[p] = p < n ? v[perm[p]] : T(0);
+}
+template <typename T>
+__global__ void k_permute_out(const T* __restrict__ v, const int32_t* __restrict__ perm, int64_t n,
+                              T* __restrict__ out) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) out[perm[p]] = v[p];
+}
+
+// ---------------------------------------------------------------------------
+template <typename K>
+love_status allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return LOVE_OK;
+  return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+struct DevBuf {
+  const Allocator* al;
+  cudaStream_t s;
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf(const Allocator& a, cudaStream_t st) : al(&a), s(st) {}
+  bool get(size_t b) {
+    bytes = b;
+    p = al->alloc(b, s);
+    return p != nullptr || b == 0;
+  }
+  ~DevBuf() {
+    if (p) al->free(p, bytes, s);
+  }
+  template <typename X> X* as() const { return (X*)p; }
+};
+
+template <typename T, int D, typename V>
+love_status scatter_launch(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s) {
+  GridDev g = ski->grid.dev();
+  int64_t warps = g.m;
+  int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  LOVE_COUNT_LAUNCH(); k_scatter<T, D, V><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, v, scal, scale, u);
+  return cuda_check(cudaGetLastError());
+}
+// u = W v with coordinates of type T (the ski dtype) and values of type V
+template <typename T, typename V = T>
+love_status scatter_any(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s) {
+  switch (ski->grid.dim) {
+    case 1: return scatter_launch<T, 1, V>(ski, v, scal, scale, u, s);
+    case 2: return scatter_launch<T, 2, V>(ski, v, scal, scale, u, s);
+    default: return scatter_launch<T, 3, V>(ski, v, scal, scale, u, s);
+  }
+}
+template <typename T>
+love_status gather_any(love_ski* ski, const T* u, T a, T b, const T* v, T* out, cudaStream_t s) {
+  GridDev g = ski->grid.dev();
+  int blocks = ceil_div(ski->n_pad, 256);
+  switch (g.dim) {
+    case 1: LOVE_COUNT_LAUNCH(); k_gather<T, 1><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, ski->n_pad, u, a, b, v, out); break;
+    case 2: LOVE_COUNT_LAUNCH(); k_gather<T, 2><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, ski->n_pad, u, a, b, v, out); break;
+    default: LOVE_COUNT_LAUNCH(); k_gather<T, 3><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, ski->n_pad, u, a, b, v, out);
+  }
+  return cuda_check(cudaGetLastError());
+}
+
+template <typename T, int D, int MODE>
+love_status tile_launch(TileArgs<T> a, int grid, size_t smem, cudaStream_t s) {
+  const int kc = a.kcols;
+#define LOVE_TILE_CASE(KPW)                                                         \
+  if (kc <= NWARP * KPW) {                                                          \
+    auto kern = k_lanczos_tile<T, D, MODE, KPW>;                                    \
+    LOVE_TRY(allow_smem(kern, smem));                                               \
+    LOVE_COUNT_LAUNCH(); kern<<<grid, TILE_R, smem, s>>>(a);                                             \
+    return cuda_check(cudaGetLastError());                                          \
+  }
+  LOVE_TILE_CASE(2)
+  LOVE_TILE_CASE(4)
+  LOVE_TILE_CASE(8)
+  LOVE_TILE_CASE(16)
+  LOVE_TILE_CASE(32)
+#undef LOVE_TILE_CASE
+  return LOVE_ERR_UNSUPPORTED;
+}
+template <typename T, int MODE>
+love_status tile_any(int dim, TileArgs<T> a, int grid, size_t smem, cudaStream_t s) {
+  switch (dim) {
+    case 1: return tile_launch<T, 1, MODE>(a, grid, smem, s);
+    case 2: return tile_launch<T, 2, MODE>(a, grid, smem, s);
+    default: return tile_launch<T, 3, MODE>(a, grid, smem, s);
+  }
+}
+
+inline size_t tile_smem(int stages, int kcols, size_t elem) {
+  return (size_t)stages * kcols * TILE_R * elem + TILE_R * elem + kcols * elem + 64;
+}
+inline int tile_stages(int kcols, size_t elem) {
+  const size_t cap = 225 * 1024;
+  if (tile_smem(2, kcols, elem) <= cap) return 2;
+  if (tile_smem(1, kcols, elem) <= cap) return 1;
+  return 0;
+}
+
+}  // namespace
+
+int num_sms() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaStream_t s) {
+  const GridHost& gh = ski->grid;
+  T* u = (T*)work;
+  T* u2 = u + gh.m;
+  void* fftw = (void*)(u2 + gh.m);
+  LOVE_TRY(scatter_any<T>(ski, v, nullptr, T(1), u, s));
+  LOVE_TRY(kuu_apply<T>(gh, ski->fft, u, u2, 1, gh.m, fftw, -1, s));
+  return gather_any<T>(ski, u2, T(1), (T)gh.noise, v, out, s);
+}
+
+template <typename T>
+love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, double* alpha_h, double* beta_h,
+                        int* k_eff, cudaStream_t s) {
+  const GridHost& gh = ski->grid;
+  const int dim = gh.dim;
+  if (k < 1 || k > LOVE_MAX_K) return LOVE_ERR_ARG;
+  const int stages = tile_stages(k, sizeof(T));
+  if (stages == 0) return LOVE_ERR_UNSUPPORTED;
+  const size_t smem = tile_smem(stages, k, sizeof(T));
+  const int64_t ntiles = ski->n_pad / TILE_R;
+  const int grid = (int)std::min<int64_t>(ntiles, num_sms());
+  DevBuf stb(ski->alloc, s), part(ski->alloc, s), u(ski->alloc, s), y(ski->alloc, s), fw(ski->alloc, s);
+  size_t fwb = fft_work_bytes(gh, ski->fft, 1, sizeof(T) == 8);
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)std::max(grid, 1024) * (k + 1)) ||
+      !u.get(sizeof(T) * gh.m * 2) || !y.get(sizeof(T) * ski->n_pad) || !fw.get(std::max<size_t>(fwb, 16)))
+    return LOVE_ERR_OOM;
+  LanczosState* st = stb.as<LanczosState>();
+  T* u1 = u.as<T>();
+  T* u2 = u1 + gh.m;
+  const GridDev g = gh.dev();
+  LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, k, tau);
+  // probe: b = (1/m) W^T K_UU 1
+  LOVE_COUNT_LAUNCH(); k_fill<T><<<ceil_div(gh.m, 256), 256, 0, s>>>(u1, gh.m, T(1));
+  LOVE_TRY(kuu_apply<T>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
+  {
+    int pb = std::min(1024, ceil_div(ski->n_pad, 256));
+    switch (dim) {
+      case 1: LOVE_COUNT_LAUNCH(); k_probe<T, 1><<<pb, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, ski->n_pad, u2, Q, part.as<double2>(), st); break;
+      case 2: LOVE_COUNT_LAUNCH(); k_probe<T, 2><<<pb, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, ski->n_pad, u2, Q, part.as<double2>(), st); break;
+      default: LOVE_COUNT_LAUNCH(); k_probe<T, 3><<<pb, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, ski->n_pad, u2, Q, part.as<double2>(), st);
+    }
+    LOVE_LAUNCH_CHECK();
+  }
+  TileArgs<T> ta{};
+  ta.g = g;
+  ta.n = ski->n;
+  ta.n_pad = ski->n_pad;
+  ta.kcols = k;
+  ta.stages = stages;
+  ta.xs = (const T*)ski->xs;
+  ta.u = u2;
+  ta.noise = (T)gh.noise;
+  ta.Q = Q;
+  ta.ldq = ldq;
+  ta.y = y.as<T>();
+  ta.partial = part.as<double2>();
+  ta.st = st;
+  ta.status = ski->status;
+  for (int j = 0; j < k; ++j) {
+    // u = W q_j (q_j stored unnormalised, scaled by scal[j])
+    LOVE_TRY(scatter_any<T>(ski, Q + (int64_t)j * ldq, st->scal + j, T(1), u1, s));
+    LOVE_TRY(kuu_apply<T>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
+    ta.j = j;
+    LOVE_TRY(tile_any<T, MODE_GATHER_DOT>(dim, ta, grid, smem, s));
+    LOVE_TRY(tile_any<T, MODE_UPDATE_DOT>(dim, ta, grid, smem, s));
+    LOVE_TRY(tile_any<T, MODE_UPDATE_NORM>(dim, ta, grid, smem, s));
+  }
+  int keff = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaMemcpyAsync(alpha_h, st->alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaMemcpyAsync(beta_h, st->beta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  *k_eff = keff;
+  return LOVE_OK;
+}
+
+template <typename T>
+love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* out, int64_t ldo, cudaStream_t s) {
+  GridDev g = ski->grid.dev();
+  int blocks = (int)std::min<int64_t>((g.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  switch (g.dim) {
+    case 1: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 1, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo); break;
+    case 2: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 2, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo); break;
+    default: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 3, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo);
+  }
+  return cuda_check(cudaGetLastError());
+}
+
+template <typename T>
+love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_iter, int* iters, cudaStream_t s) {
+  const GridHost& gh = ski->grid;
+  const GridDev g = gh.dev();
+  const int64_t np = ski->n_pad;
+  DevBuf stb(ski->alloc, s), part(ski->alloc, s), r(ski->alloc, s), pv(ski->alloc, s), Ap(ski->alloc, s),
+      u(ski->alloc, s), fw(ski->alloc, s);
+  size_t fwb = fft_work_bytes(gh, ski->fft, 1, true);
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * 1024) || !r.get(sizeof(double) * np) ||
+      !pv.get(sizeof(double) * np) || !Ap.get(sizeof(double) * np) || !u.get(sizeof(double) * gh.m * 2) ||
+      !fw.get(std::max<size_t>(fwb, 16)))
+    return LOVE_ERR_OOM;
+  LanczosState* st = stb.as<LanczosState>();
+  double* u1 = u.as<double>();
+  double* u2 = u1 + gh.m;
+  int blocks = std::min(1024, ceil_div(np, 256));
+  LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, 1, 0.0);
+  LOVE_COUNT_LAUNCH(); k_cg_init<T><<<blocks, 256, 0, s>>>(np, b, x, r.as<double>(), pv.as<double>(), part.as<double2>(), st, tol);
+  LOVE_LAUNCH_CHECK();
+  int it = 0;
+  const int chunk = 32;
+  while (it < max_iter) {
+    for (int c = 0; c < chunk && it < max_iter; ++c, ++it) {
+      LOVE_TRY(scatter_any<T, double>(ski, pv.as<double>(), nullptr, 1.0, u1, s));
+      LOVE_TRY(kuu_apply<double>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
+      switch (g.dim) {
+        case 1: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 1><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, pv.as<double>(), Ap.as<double>(), part.as<double2>(), st); break;
+        case 2: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 2><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, pv.as<double>(), Ap.as<double>(), part.as<double2>(), st); break;
+        default: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 3><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, pv.as<double>(), Ap.as<double>(), part.as<double2>(), st);
+      }
+      LOVE_COUNT_LAUNCH(); k_cg_update<<<blocks, 256, 0, s>>>(np, x, r.as<double>(), pv.as<double>(), Ap.as<double>(), part.as<double2>(), st, max_iter,
+                                           ski->status);
+      LOVE_COUNT_LAUNCH(); k_cg_pupdate<<<blocks, 256, 0, s>>>(np, pv.as<double>(), r.as<double>(), st);
+      LOVE_LAUNCH_CHECK();
+    }
+    int done = 0;
+    LOVE_CUDA(cudaMemcpyAsync(&done, &st->cg_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    if (done) break;
+  }
+  int n_it = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&n_it, &st->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  if (iters) *iters = n_it;
+  return LOVE_OK;
+}
+
+// cache build: Rt = K_UU W Q L^{-T}; a = K_UU W z; packed rows [Rt | a | 0]
+template <typename T>
+love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, const double* zmean, cudaStream_t s,
+                        T* keep_rt) {
+  const GridHost& gh = ski->grid;
+  const int64_t m = gh.m;
+  const int k = c->k_eff;
+  DevBuf P0(ski->alloc, s), R0(ski->alloc, s), Rt(ski->alloc, s), av(ski->alloc, s), fw(ski->alloc, s),
+      dd(ski->alloc, s), okb(ski->alloc, s);
+  size_t fwb = fft_work_bytes(gh, ski->fft, std::max(k, 1), sizeof(T) == 8);
+  if (!P0.get(sizeof(T) * m * k) || !R0.get(sizeof(T) * m * k) || (!keep_rt && !Rt.get(sizeof(T) * m * k)) ||
+      !av.get(sizeof(double) * m * 2) || !fw.get(std::max<size_t>(fwb, 16)) || !dd.get(sizeof(double) * 2 * (k + 1)) ||
+      !okb.get(sizeof(int)))
+    return LOVE_ERR_OOM;
+  // T = L L^T on the device
+  T* RT = keep_rt ? keep_rt : Rt.as<T>();  // Rt = K_UU W Q L^{-T}, m x k column-major
+  double* dptr = dd.as<double>();
+  double* eptr = dptr + (k + 1);
+  {
+    DevBuf ab(ski->alloc, s);
+    if (!ab.get(sizeof(double) * 2 * (k + 1))) return LOVE_ERR_OOM;
+    LOVE_CUDA(cudaMemcpyAsync(ab.as<double>(), c->alpha, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    if (k > 1)
+      LOVE_CUDA(cudaMemcpyAsync(ab.as<double>() + (k + 1), c->beta, sizeof(double) * (k - 1), cudaMemcpyHostToDevice, s));
+    LOVE_COUNT_LAUNCH(); k_tridiag_chol<<<1, 32, 0, s>>>(ab.as<double>(), ab.as<double>() + (k + 1), nullptr, k, dptr, eptr, c->status,
+                                    okb.as<int>());
+    LOVE_LAUNCH_CHECK();
+    int ok = 0;
+    LOVE_CUDA(cudaMemcpyAsync(&ok, okb.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    if (!ok) return LOVE_ERR_NOT_PD;
+  }
+  // P0 = W Q, R0 = K_UU P0
+  LOVE_TRY(scatter_multi<T>(ski, Q, ldq, k, P0.as<T>(), m, s));
+  LOVE_TRY(kuu_apply<T>(gh, ski->fft, P0.as<T>(), R0.as<T>(), k, m, fw.p, -1, s));
+  int blocks = ceil_div(m, 256);
+  LOVE_COUNT_LAUNCH(); k_lt_solve<T><<<blocks, 256, 0, s>>>(R0.as<T>(), m, m, k, dptr, eptr, RT, m);
+  LOVE_LAUNCH_CHECK();
+  const double* aptr = nullptr;
+  if (zmean) {
+    // a = K_UU W z (eq. pred_mean_ski) in FP64
+    double* a1 = av.as<double>();
+    size_t fwb2 = fft_work_bytes(gh, ski->fft, 1, true);
+    DevBuf fw2(ski->alloc, s);
+    if (!fw2.get(std::max<size_t>(fwb2, 16))) return LOVE_ERR_OOM;
+    LOVE_TRY(scatter_any<T, double>(ski, zmean, nullptr, 1.0, a1, s));
+    LOVE_TRY(kuu_apply<double>(gh, ski->fft, a1, a1 + m, 1, m, fw2.p, -1, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    aptr = a1 + m;
+  }
+  // packed predict cache
+  const int64_t tot = m * c->ld;
+  int pb = ceil_div(tot, 256);
+  LOVE_COUNT_LAUNCH();
+  if (c->cache_dtype == LOVE_BF16)
+    k_pack_rows<T, __nv_bfloat16><<<pb, 256, 0, s>>>(RT, m, m, k, aptr, (__nv_bfloat16*)c->Rc, c->ld);
+  else if (c->cache_dtype == LOVE_F64)
+    k_pack_rows<T, double><<<pb, 256, 0, s>>>(RT, m, m, k, aptr, (double*)c->Rc, c->ld);
+  else
+    k_pack_rows<T, float><<<pb, 256, 0, s>>>(RT, m, m, k, aptr, (float*)c->Rc, c->ld);
+  LOVE_LAUNCH_CHECK();
+  // keep P = W Q L^{-T} (column-major, dtype) for gradients
+  if (c->flags & LOVE_WANT_GRAD) {
+    LOVE_COUNT_LAUNCH(); k_lt_solve<T><<<blocks, 256, 0, s>>>(P0.as<T>(), m, m, k, dptr, eptr, (T*)c->P, m);
+    LOVE_LAUNCH_CHECK();
+  }
+  return cuda_check(cudaStreamSynchronize(s));
+}
+
+template love_status ski_mvm_sorted<float>(love_ski*, const float*, float*, void*, cudaStream_t);
+template love_status ski_mvm_sorted<double>(love_ski*, const double*, double*, void*, cudaStream_t);
+template love_status lanczos_run<float>(love_ski*, int, double, float*, int64_t, double*, double*, int*, cudaStream_t);
+template love_status lanczos_run<double>(love_ski*, int, double, double*, int64_t, double*, double*, int*,
+                                         cudaStream_t);
+template love_status scatter_multi<float>(love_ski*, const float*, int64_t, int, float*, int64_t, cudaStream_t);
+template love_status scatter_multi<double>(love_ski*, const double*, int64_t, int, double*, int64_t, cudaStream_t);
+template love_status cg_solve<float>(love_ski*, const float*, double*, double, int, int*, cudaStream_t);
+template love_status cg_solve<double>(love_ski*, const double*, double*, double, int, int*, cudaStream_t);
+template love_status build_cache<float>(love_ski*, love_cache*, const float*, int64_t, const double*, cudaStream_t,
+                                        float*);
+template love_status build_cache<double>(love_ski*, love_cache*, const double*, int64_t, const double*,
+                                         cudaStream_t, double*);
+
+// permutation helpers used by the API (caller order <-> cell-sorted order)
+template <typename T>
+love_status permute_in(const T* v, const int32_t* perm, int64_t n, int64_t n_pad, T* out, cudaStream_t s) {
+  LOVE_COUNT_LAUNCH(); k_permute_in<T><<<ceil_div(n_pad, 256), 256, 0, s>>>(v, perm, n, n_pad, out);
+  return cuda_check(cudaGetLastError());
+}
+template <typename T>
+love_status permute_out(const T* v, const int32_t* perm, int64_t n, T* out, cudaStream_t s) {
+  LOVE_COUNT_LAUNCH(); k_permute_out<T><<<ceil_div(n, 256), 256, 0, s>>>(v, perm, n, out);
+  return cuda_check(cudaGetLastError());
+}
+template love_status permute_in<float>(const float*, const int32_t*, int64_t, int64_t, float*, cudaStream_t);
+template love_status permute_in<double>(const double*, const int32_t*, int64_t, int64_t, double*, cudaStream_t);
+template love_status permute_out<float>(const float*, const int32_t*, int64_t, float*, cudaStream_t);
+template love_status permute_out<double>(const double*, const int32_t*, int64_t, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Sampler Lanczos (Sec. 3.3, eq. lancapprox): k' steps on M = K_UU - Rt Rt^T,
+// an m x m operator, in FP64 with the same CGS2 reorthogonalisation kernels.
+// M's entries are differences of nearly equal numbers (K_UU ~ 1, posterior
+// ~ 1e-7 on the 1-D n = 1e6 workload), so FP32 would lose them entirely.
+// The probe (not given by the paper) is the Rademacher vector
+// r_i = +1 if the low bit of SplitMix64 output i (seeded with `seed`) is 1, else -1.
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_rademacher(int64_t m, int64_t m_pad, uint64_t seed, double* __restrict__ q0, LanczosState* st) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m_pad) q0[i] = i < m ? ((splitmix64_output(seed, (uint64_t)i) & 1ull) ? 1.0 : -1.0) : 0.0;
+  if (i == 0) st->scal[0] = 1.0 / sqrt((double)m);
+}
+__global__ void k_normalize_col(double* __restrict__ q, int64_t n_pad, const double* __restrict__ scal,
+                                const LanczosState* st) {
+  if (st->done) return;
+  const double sc = *scal;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x)
+    q[i] *= sc;
+}
+// t[c] = sum_r R[r, c] q[r]   (R column-major, ldr), one block per column
+template <typename T>
+__global__ void k_gemv_t(const T* __restrict__ R, int64_t ldr, int64_t m, const double* __restrict__ q,
+                         double* __restrict__ t, const LanczosState* st) {
+  __shared__ DotAccD red[32];
+  if (st->done) return;
+  const int c = blockIdx.x;
+  DotAccD a;
+  a.zero();
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) a.add_prod((double)R[(int64_t)c * ldr + r], q[r]);
+  block_merge(a, red);
+  if (threadIdx.x == 0) t[c] = a.value();
+}
+// y[r] = Kq[r] - sum_c R[r, c] t[c]  (0 on padding rows)
+template <typename T>
+__global__ void k_gemv_n_sub(const T* __restrict__ R, int64_t ldr, int64_t m, int64_t m_pad, int k,
+                             const double* __restrict__ t, const double* __restrict__ Kq, double* __restrict__ y,
+                             const LanczosState* st) {
+  if (st->done) return;
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m_pad) return;
+  double acc = 0.0;
+  if (r < m) {
+    acc = Kq[r];
+    for (int c = 0; c < k; ++c) acc -= (double)R[(int64_t)c * ldr + r] * t[c];
+  }
+  y[r] = acc;
+}
+
+}  // namespace
+
+template <typename T>
+love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
+                            int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
+                            double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s) {
+  const int64_t m = gh.m, m_pad = ldq;
+  if (ks < 1 || ks > LOVE_MAX_K || m_pad % TILE_R) return LOVE_ERR_ARG;
+  const int stages = tile_stages(ks, sizeof(double));
+  if (stages == 0) return LOVE_ERR_UNSUPPORTED;
+  const size_t smem = tile_smem(stages, ks, sizeof(double));
+  const int grid = (int)std::min<int64_t>(m_pad / TILE_R, num_sms());
+  DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s);
+  size_t fwb = fft_work_bytes(gh, fft, 1, true);
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)std::max(grid, 1024) * (ks + 1)) ||
+      !kq.get(sizeof(double) * m) || !y.get(sizeof(double) * m_pad) || !tv.get(sizeof(double) * (k + 1)) ||
+      !fw.get(std::max<size_t>(fwb, 16)))
+    return LOVE_ERR_OOM;
+  LanczosState* st = stb.as<LanczosState>();
+  LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, ks, tau);
+  LOVE_COUNT_LAUNCH(); k_rademacher<<<ceil_div(m_pad, 256), 256, 0, s>>>(m, m_pad, seed, Q, st);
+  LOVE_LAUNCH_CHECK();
+  TileArgs<double> ta{};
+  ta.g = gh.dev();
+  ta.n = m;
+  ta.n_pad = m_pad;
+  ta.kcols = ks;
+  ta.stages = stages;
+  ta.Q = Q;
+  ta.ldq = ldq;
+  ta.y = y.as<double>();
+  ta.partial = part.as<double2>();
+  ta.st = st;
+  ta.status = status;
+  const int nb = std::min(4 * num_sms(), ceil_div(m_pad, 256));
+  for (int j = 0; j < ks; ++j) {
+    double* qj = Q + (int64_t)j * ldq;
+    LOVE_COUNT_LAUNCH(); k_normalize_col<<<nb, 256, 0, s>>>(qj, m_pad, st->scal + j, st);
+    LOVE_TRY(kuu_apply<double>(gh, fft, qj, kq.as<double>(), 1, m, fw.p, -1, s));
+    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<k, 256, 0, s>>>(Rt, ldr, m, qj, tv.as<double>(), st);
+    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T><<<ceil_div(m_pad, 256), 256, 0, s>>>(Rt, ldr, m, m_pad, k, tv.as<double>(), kq.as<double>(), y.as<double>(), st);
+    LOVE_LAUNCH_CHECK();
+    ta.j = j;
+    LOVE_TRY(tile_launch<double, 1, MODE_DOT>(ta, grid, smem, s));
+    LOVE_TRY(tile_launch<double, 1, MODE_UPDATE_DOT>(ta, grid, smem, s));
+    LOVE_TRY(tile_launch<double, 1, MODE_UPDATE_NORM>(ta, grid, smem, s));
+  }
+  int keff = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaMemcpyAsync(alpha_h, st->alpha, sizeof(double) * ks, cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaMemcpyAsync(beta_h, st->beta, sizeof(double) * ks, cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  *ks_eff = keff;
+  return LOVE_OK;
+}
+
+template love_status sampler_lanczos<float>(const GridHost&, const FftPlan*, const Allocator&, const float*, int64_t,
+                                            int, int, uint64_t, double, double*, int64_t, double*, double*, int*,
+                                            DevStatus*, cudaStream_t);
+template love_status sampler_lanczos<double>(const GridHost&, const FftPlan*, const Allocator&, const double*,
+                                             int64_t, int, int, uint64_t, double, double*, int64_t, double*, double*,
+                                             int*, DevStatus*, cudaStream_t);
+
+}  // namespace love

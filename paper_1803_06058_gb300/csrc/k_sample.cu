@@ -1,0 +1,504 @@
+// k_sample.cu -- posterior sampling through the low-rank root (Sec. 3.3).
+//
+// Pre-compute (eqs. lancapprox, sampling_pre_cholesky, pred_covar_ski_interp_form):
+// k' Lanczos steps on M = K_UU - R^T R' (k_lanczos.cu: sampler_lanczos) give
+// Q', T'; with T' = L' L'^T the root is S = Q' L' (m x k').  When T' is not
+// positive definite (M is a difference of two nearly equal PSD matrices, so
+// rounding can push small eigenvalues below zero) the root is taken from the
+// eigendecomposition T' = V diag(lam) V^T instead: S = Q' V diag(sqrt(max(lam, 0))),
+// with the eigenpairs from cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5).
+//
+// Test phase (eq. sample): F = mu 1^T + (W*^T S Z)^T, F sample-major (s x t):
+//   gather   G = W*^T S (t x k') and mu = W*^T a     (4^d rows of S per point)
+//   product  F[j, i] = mu_i + sum_c G[i, c] Z[c, j]
+// Z (k' x s) is supplied by the caller or drawn on the device from
+// Philox4x32-10 (Salmon et al. 2011) with Box-Muller in FP64.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "love_internal.cuh"
+
+namespace love {
+namespace {
+
+template <typename K>
+love_status allow_smem_s(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return LOVE_OK;
+  return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+// l_11 = sqrt(alpha_1), e_j = beta_j / l_jj, l_{j+1,j+1} = sqrt(alpha_{j+1} - e_j^2)
+__global__ void k_chol_tri(const double* alpha, const double* beta, int k, double* d, double* e, int* ok) {
+  if (threadIdx.x || blockIdx.x) return;
+  double piv = alpha[0];
+  *ok = 1;
+  for (int j = 0; j < k; ++j) {
+    if (j > 0) {
+      e[j - 1] = beta[j - 1] / d[j - 1];
+      piv = alpha[j] - e[j - 1] * e[j - 1];
+    }
+    if (!(piv > 0.0)) {
+      *ok = 0;
+      return;
+    }
+    d[j] = sqrt(piv);
+  }
+}
+
+// S[r, c] = d_c Q'[r, c] + e_c Q'[r, c+1]   (S = Q' L', L' lower bidiagonal), row-major ld_s
+template <typename T>
+__global__ void k_root_from_chol(const double* __restrict__ Q, int64_t ldq, int64_t m, int k, const double* d,
+                                 const double* e, T* __restrict__ S, int ld_s) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * ld_s) return;
+  int64_t r = idx / ld_s;
+  int c = (int)(idx - r * ld_s);
+  double v = 0.0;
+  if (c < k) {
+    v = d[c] * Q[(int64_t)c * ldq + r];
+    if (c + 1 < k) v += e[c] * Q[(int64_t)(c + 1) * ldq + r];
+  }
+  S[idx] = (T)v;
+}
+
+// dense tridiagonal T' into A (n x n)
+__global__ void k_tri_dense(const double* alpha, const double* beta, int n, double* A) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  int i = (int)(idx / n), j = (int)(idx % n);
+  double v = 0.0;
+  if (i == j) v = alpha[i];
+  else if (i == j + 1) v = beta[j];
+  else if (j == i + 1) v = beta[i];
+  A[idx] = v;
+}
+
+// Cyclic Jacobi eigenvalue iteration on a symmetric n x n matrix, one CTA.
+// Each rotation J (c, s at (p, q)) with tan(phi) = t the smaller root of
+// t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq), annihilates a_pq:
+// A <- J^T A J, V <- V J.  Sweeps until the off-diagonal mass is below
+// 1e-28 of the total (or max_sweeps).  A, V in shared memory when they fit.
+__global__ void k_jacobi_eig(double* __restrict__ Ag, double* __restrict__ Vg, int n, int max_sweeps, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* A = use_smem ? reinterpret_cast<double*>(smem_raw) : Ag;
+  double* V = use_smem ? A + (size_t)n * n : Vg;
+  __shared__ double rot[2];
+  __shared__ int skip;
+  __shared__ double red[2][32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t i = tid; i < (int64_t)n * n; i += nt) {
+    if (use_smem) A[i] = Ag[i];
+    V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int64_t i = tid; i < (int64_t)n * n; i += nt) {
+      double a = A[i];
+      tot += a * a;
+      if (i / n != i % n) off += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = off;
+      red[1][tid >> 5] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (nt + 31) / 32; ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+      skip = (a <= 1e-28 * b) ? 1 : 0;
+    }
+    __syncthreads();
+    if (skip) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (tid == 0) {
+          double apq = A[(int64_t)p * n + q];
+          double app = A[(int64_t)p * n + p], aqq = A[(int64_t)q * n + q];
+          if (fabs(apq) <= 1e-300 || fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq))) {
+            skip = 1;
+          } else {
+            skip = 0;
+            double theta = (aqq - app) / (2.0 * apq);
+            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            double c = 1.0 / sqrt(t * t + 1.0);
+            rot[0] = c;
+            rot[1] = t * c;
+          }
+        }
+        __syncthreads();
+        if (skip) continue;
+        const double c = rot[0], s = rot[1];
+        for (int i = tid; i < n; i += nt) {  // A <- A J (columns p, q)
+          double aip = A[(int64_t)i * n + p], aiq = A[(int64_t)i * n + q];
+          A[(int64_t)i * n + p] = c * aip - s * aiq;
+          A[(int64_t)i * n + q] = s * aip + c * aiq;
+        }
+        __syncthreads();
+        for (int j = tid; j < n; j += nt) {  // A <- J^T A (rows p, q); V <- V J
+          double apj = A[(int64_t)p * n + j], aqj = A[(int64_t)q * n + j];
+          A[(int64_t)p * n + j] = c * apj - s * aqj;
+          A[(int64_t)q * n + j] = s * apj + c * aqj;
+          double vjp = V[(int64_t)j * n + p], vjq = V[(int64_t)j * n + q];
+          V[(int64_t)j * n + p] = c * vjp - s * vjq;
+          V[(int64_t)j * n + q] = s * vjp + c * vjq;
+        }
+        __syncthreads();
+      }
+  }
+  if (use_smem)
+    for (int64_t i = tid; i < (int64_t)n * n; i += nt) {
+      Ag[i] = A[i];
+      Vg[i] = V[i];
+    }
+}
+
+// B[j, c] = V[j, c] sqrt(max(lam_c, 0)),  lam_c = A[c, c]
+__global__ void k_scale_eigvec(const double* A, const double* V, int n, double* B) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  int c = (int)(idx % n);
+  double lam = A[(int64_t)c * n + c];
+  B[idx] = V[idx] * sqrt(lam > 0.0 ? lam : 0.0);
+}
+
+// S[r, c] = sum_j Q'[r, j] B[j, c]  (arithmetic in T; S row-major ld_s)
+template <typename T>
+__global__ void k_root_from_eig(const double* __restrict__ Q, int64_t ldq, int64_t m, int k,
+                                const double* __restrict__ B, T* __restrict__ S, int ld_s) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Bs = reinterpret_cast<T*>(smem_raw);  // k x k
+  for (int i = threadIdx.x; i < k * k; i += blockDim.x) Bs[i] = (T)B[i];
+  __syncthreads();
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  for (int c = 0; c < ld_s; ++c) {
+    T acc = T(0);
+    if (c < k)
+      for (int j = 0; j < k; ++j) acc += (T)Q[(int64_t)j * ldq + r] * Bs[j * k + c];
+    S[r * ld_s + c] = acc;
+  }
+}
+
+// ---- test phase -------------------------------------------------------------
+struct SampleGatherArgs {
+  GridDev g;
+  int64_t t;
+  const void* x;
+  const void* S;
+  int ld_s;
+  int ks;
+  const void* Rc;    // predict cache (mean in column k) or null
+  int ld_c;
+  int kc;
+  int cache_dtype;
+  void* G;           // t x ld_g
+  int ld_g;
+  void* mu;          // t
+  DevStatus* status;
+};
+
+template <typename T>
+__device__ __forceinline__ T load_cache_elem(const void* Rc, int64_t idx, int cdt) {
+  if (cdt == LOVE_BF16) return (T)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Rc)[idx]);
+  if (cdt == LOVE_F64) return (T)reinterpret_cast<const double*>(Rc)[idx];
+  return (T)reinterpret_cast<const float*>(Rc)[idx];
+}
+
+// one warp per test point; lanes over the columns of S
+template <typename T, int D>
+__global__ void k_sample_gather(SampleGatherArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const T* x = reinterpret_cast<const T*>(a.x);
+  const T* S = reinterpret_cast<const T*>(a.S);
+  T* G = reinterpret_cast<T*>(a.G);
+  T* mu = reinterpret_cast<T*>(a.mu);
+  constexpr int NR = D == 1 ? 4 : (D == 2 ? 16 : 64);
+  for (int64_t pt = w0; pt < a.t; pt += nw) {
+    int base[D];
+    T w[D][4];
+    bool ok = true;
+#pragma unroll
+    for (int e = 0; e < D; ++e) ok &= keys_weights(grid_coord(x[pt * D + e], a.g, e), a.g.g[e], base[e], w[e]);
+    if (!ok) {
+      for (int c = lane; c < a.ld_g; c += 32) G[pt * a.ld_g + c] = T(0);
+      if (lane == 0) {
+        mu[pt] = (T)NAN;
+        atomicAdd(&a.status->domain_errors, 1ull);
+        dev_flag(a.status, LOVE_ERR_DOMAIN);
+      }
+      continue;
+    }
+    int64_t rows[NR];
+    T ww[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      int r0 = q & 3, r1 = (q >> 2) & 3, r2 = (q >> 4) & 3;
+      int64_t row;
+      T wq;
+      if (D == 1) {
+        row = base[0] - 1 + r0;
+        wq = w[0][r0];
+      } else if (D == 2) {
+        row = (int64_t)(base[0] - 1 + r1) * a.g.stride[0] + (base[1] - 1 + r0);
+        wq = w[0][r1] * w[1][r0];
+      } else {
+        row = (int64_t)(base[0] - 1 + r2) * a.g.stride[0] + (int64_t)(base[1] - 1 + r1) * a.g.stride[1] +
+              (base[2] - 1 + r0);
+        wq = w[0][r2] * w[1][r1] * w[2][r0];
+      }
+      rows[q] = row;
+      ww[q] = wq;
+    }
+    for (int c = lane; c < a.ld_g; c += 32) {
+      T acc = T(0);
+      if (c < a.ks) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc += ww[q] * S[rows[q] * a.ld_s + c];
+      }
+      G[pt * a.ld_g + c] = acc;
+    }
+    if (lane == 0) {
+      T m_ = T(0);
+      if (a.Rc) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) m_ += ww[q] * load_cache_elem<T>(a.Rc, rows[q] * a.ld_c + a.kc, a.cache_dtype);
+      }
+      mu[pt] = m_;
+    }
+  }
+}
+
+// F[j, i] = mu_i + sum_c G[i, c] Z[c, j];  64 x 64 output tile per CTA, 4 x 4 per thread
+template <typename T>
+__global__ void __launch_bounds__(256) k_sample_gemm(const T* __restrict__ G, int ld_g, const T* __restrict__ Z,
+                                                     int s, int ks, const T* __restrict__ mu, int64_t t,
+                                                     T* __restrict__ F) {
+  __shared__ T Gs[16][64 + 1];
+  __shared__ T Zs[16][64];
+  const int64_t i0 = (int64_t)blockIdx.x * 64;
+  const int j0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int c0 = 0; c0 < ks; c0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int idx = threadIdx.x + 256 * q;
+      int ii = idx >> 4, cc = idx & 15;
+      int64_t i = i0 + ii;
+      Gs[cc][ii] = (i < t && c0 + cc < ks) ? G[i * ld_g + c0 + cc] : T(0);
+      int cz = idx >> 6, jj = idx & 63;
+      Zs[cz][jj] = (c0 + cz < ks && j0 + jj < s) ? Z[(int64_t)(c0 + cz) * s + j0 + jj] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc) {
+      T gv[4], zv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) gv[a] = Gs[cc][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) zv[b] = Zs[cc][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(gv[a], zv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int64_t i = i0 + tx + 16 * a;
+    if (i >= t) continue;
+    T m_ = mu[i];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int j = j0 + ty + 16 * b;
+      if (j < s) F[(int64_t)j * t + i] = m_ + acc[a][b];
+    }
+  }
+}
+
+// Philox4x32-10: 10 rounds of (hi0,lo0) = M0 x0, (hi1,lo1) = M1 x2,
+// x <- (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0), key += Weyl constants between rounds.
+__device__ __forceinline__ void philox4x32_10(uint32_t x[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t lo0 = 0xD2511F53u * x[0], hi0 = __umulhi(0xD2511F53u, x[0]);
+    uint32_t lo1 = 0xCD9E8D57u * x[2], hi1 = __umulhi(0xCD9E8D57u, x[2]);
+    uint32_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+    x[0] = y0;
+    x[1] = lo1;
+    x[2] = y2;
+    x[3] = lo0;
+  }
+}
+// element e: block e / 4 of counter (lo, hi, 0, 0), key = seed; u = (r + 1/2) 2^-32;
+// Box-Muller pairs (r0, r1), (r2, r3): (cos, sin) of each
+template <typename T>
+__global__ void k_philox_normals(int64_t count, uint64_t seed, T* __restrict__ out) {
+  int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blk * 4 >= count) return;
+  uint32_t x[4] = {(uint32_t)(uint64_t)blk, (uint32_t)((uint64_t)blk >> 32), 0u, 0u};
+  philox4x32_10(x, (uint32_t)seed, (uint32_t)(seed >> 32));
+  double z[4];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    double u1 = ((double)x[2 * p] + 0.5) * 2.3283064365386963e-10;
+    double u2 = ((double)x[2 * p + 1] + 0.5) * 2.3283064365386963e-10;
+    double rad = sqrt(-2.0 * log(u1));
+    double sn, cn;
+    sincospi(2.0 * u2, &sn, &cn);
+    z[2 * p] = rad * cn;
+    z[2 * p + 1] = rad * sn;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (blk * 4 + q < count) out[blk * 4 + q] = (T)z[q];
+}
+
+struct Buf {
+  const Allocator* al;
+  cudaStream_t s;
+  void* p = nullptr;
+  size_t b = 0;
+  Buf(const Allocator& a, cudaStream_t st) : al(&a), s(st) {}
+  bool get(size_t bytes) {
+    b = bytes;
+    p = al->alloc(bytes, s);
+    return p != nullptr;
+  }
+  ~Buf() {
+    if (p) al->free(p, b, s);
+  }
+  template <typename X> X* as() const { return (X*)p; }
+};
+
+}  // namespace
+
+template <typename T>
+love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uint64_t seed, double tau,
+                          cudaStream_t s) {
+  const GridHost& g = ski->grid;
+  const Allocator& al = ski->alloc;
+  const int64_t m = g.m;
+  const int64_t m_pad = (m + 255) / 256 * 256;
+  Buf Qb(al, s), ab(al, s), okb(al, s);
+  if (!Qb.get(sizeof(double) * m_pad * ks) || !ab.get(sizeof(double) * 4 * (ks + 1)) || !okb.get(sizeof(int)))
+    return LOVE_ERR_OOM;
+  std::vector<double> alpha(ks + 1), beta(ks + 1);
+  int keff = 0;
+  LOVE_TRY(sampler_lanczos<T>(g, ski->fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<double>(), m_pad, alpha.data(),
+                              beta.data(), &keff, c->status, s));
+  if (keff < 1) return LOVE_ERR_NAN;
+  double* ad = ab.as<double>();
+  double* bd = ad + (ks + 1);
+  double* dd = bd + (ks + 1);
+  double* ed = dd + (ks + 1);
+  LOVE_CUDA(cudaMemcpyAsync(ad, alpha.data(), sizeof(double) * keff, cudaMemcpyHostToDevice, s));
+  if (keff > 1) LOVE_CUDA(cudaMemcpyAsync(bd, beta.data(), sizeof(double) * (keff - 1), cudaMemcpyHostToDevice, s));
+  LOVE_COUNT_LAUNCH(); k_chol_tri<<<1, 32, 0, s>>>(ad, bd, keff, dd, ed, okb.as<int>());
+  LOVE_LAUNCH_CHECK();
+  int ok = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&ok, okb.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  const int vec = 16 / (int)sizeof(T);
+  c->ks = keff;
+  c->ld_s = (keff + vec - 1) / vec * vec;
+  c->S = al.alloc(sizeof(T) * (size_t)m * c->ld_s, s);
+  if (!c->S) return LOVE_ERR_OOM;
+  if (ok) {
+    LOVE_COUNT_LAUNCH(); k_root_from_chol<T><<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(Qb.as<double>(), m_pad, m, keff, dd, ed, (T*)c->S, c->ld_s);
+    c->sampler_fallback = 0;
+  } else {
+    Buf A(al, s), V(al, s), B(al, s);
+    const int64_t nn = (int64_t)keff * keff;
+    if (!A.get(sizeof(double) * nn) || !V.get(sizeof(double) * nn) || !B.get(sizeof(double) * nn)) return LOVE_ERR_OOM;
+    LOVE_COUNT_LAUNCH(); k_tri_dense<<<ceil_div(nn, 256), 256, 0, s>>>(ad, bd, keff, A.as<double>());
+    size_t sm = sizeof(double) * 2 * nn;
+    int use_smem = sm <= 200 * 1024 ? 1 : 0;
+    if (use_smem) LOVE_TRY(allow_smem_s(k_jacobi_eig, sm));
+    LOVE_COUNT_LAUNCH(); k_jacobi_eig<<<1, 256, use_smem ? sm : 0, s>>>(A.as<double>(), V.as<double>(), keff, 30, use_smem);
+    LOVE_COUNT_LAUNCH(); k_scale_eigvec<<<ceil_div(nn, 256), 256, 0, s>>>(A.as<double>(), V.as<double>(), keff, B.as<double>());
+    size_t smb = sizeof(T) * nn;
+    LOVE_TRY(allow_smem_s(k_root_from_eig<T>, smb));
+    LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<double>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);
+    LOVE_LAUNCH_CHECK();
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    c->sampler_fallback = 1;
+  }
+  LOVE_LAUNCH_CHECK();
+  return cuda_check(cudaStreamSynchronize(s));
+}
+
+template love_status sampler_build<float>(love_ski*, love_cache*, const float*, int, uint64_t, double, cudaStream_t);
+template love_status sampler_build<double>(love_ski*, love_cache*, const double*, int, uint64_t, double,
+                                           cudaStream_t);
+
+template <typename T>
+static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_count, const void* z, uint64_t seed,
+                               void* out, cudaStream_t s) {
+  const Allocator& al = c->alloc;
+  const int ks = c->ks;
+  const int vec = 16 / (int)sizeof(T);
+  const int ld_g = (ks + vec - 1) / vec * vec;
+  Buf Gb(al, s), mub(al, s), zb(al, s);
+  if (!Gb.get(sizeof(T) * (size_t)t * ld_g) || !mub.get(sizeof(T) * (size_t)t)) return LOVE_ERR_OOM;
+  const T* Z = (const T*)z;
+  if (!Z) {
+    int64_t cnt = (int64_t)ks * s_count;
+    if (!zb.get(sizeof(T) * cnt)) return LOVE_ERR_OOM;
+    int64_t blocks4 = (cnt + 3) / 4;
+    LOVE_COUNT_LAUNCH(); k_philox_normals<T><<<ceil_div(blocks4, 256), 256, 0, s>>>(cnt, seed, zb.as<T>());
+    Z = zb.as<T>();
+  }
+  SampleGatherArgs a{};
+  a.g = c->grid.dev();
+  a.t = t;
+  a.x = x;
+  a.S = c->S;
+  a.ld_s = c->ld_s;
+  a.ks = ks;
+  a.Rc = (c->flags & LOVE_WANT_MEAN) ? c->Rc : nullptr;
+  a.ld_c = c->ld;
+  a.kc = c->k_eff;
+  a.cache_dtype = c->cache_dtype;
+  a.G = Gb.p;
+  a.ld_g = ld_g;
+  a.mu = mub.p;
+  a.status = c->status;
+  int blocks = (int)std::min<int64_t>((t * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  switch (a.g.dim) {
+    case 1: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 1><<<blocks, 256, 0, s>>>(a); break;
+    case 2: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 2><<<blocks, 256, 0, s>>>(a); break;
+    default: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 3><<<blocks, 256, 0, s>>>(a);
+  }
+  dim3 grid((unsigned)((t + 63) / 64), (unsigned)((s_count + 63) / 64));
+  LOVE_COUNT_LAUNCH(); k_sample_gemm<T><<<grid, 256, 0, s>>>(Gb.as<T>(), ld_g, Z, s_count, ks, mub.as<T>(), t, (T*)out);
+  return cuda_check(cudaGetLastError());
+}
+
+love_status sample_launch(love_cache* c, int64_t t, const void* x, int s_count, const void* z, uint64_t seed,
+                          void* out, cudaStream_t s) {
+  if (c->dtype == LOVE_F64) return sample_impl<double>(c, t, x, s_count, z, seed, out, s);
+  return sample_impl<float>(c, t, x, s_count, z, seed, out, s);
+}
+
+}  // namespace love

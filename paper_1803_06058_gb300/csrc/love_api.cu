@@ -1,0 +1,803 @@
+// love_api.cu -- the C ABI declared in include/love.h.
+//
+// Host-side orchestration only: argument checks, handle lifetime, device
+// memory (caller allocator or cudaMallocAsync), and the order of the kernel
+// phases.  Every arithmetic step of the method runs in the kernels of
+// k_sort.cu, k_fft.cu, k_lanczos.cu, k_predict.cu and k_sample.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "love_internal.cuh"
+
+namespace love {
+
+thread_local int g_last_cuda_error = 0;
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace love
+
+using namespace love;
+
+// ---------------------------------------------------------------------------
+void* Allocator::alloc(size_t bytes, cudaStream_t s) const {
+  if (bytes == 0) bytes = 16;
+  if (user) return a.alloc(a.ctx, bytes, s);
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
+    g_last_cuda_error = (int)e;
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void Allocator::free(void* p, size_t bytes, cudaStream_t s) const {
+  if (!p) return;
+  if (user) {
+    a.free(a.ctx, p, bytes ? bytes : 16, s);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+GridDev GridHost::dev() const {
+  GridDev d{};
+  d.dim = dim;
+  d.m = (int)m;
+  for (int e = 0; e < LOVE_MAX_DIM; ++e) {
+    d.g[e] = (int)g[e];
+    d.stride[e] = (int)stride[e];
+    d.lo_d[e] = lo[e];
+    d.h_d[e] = h[e];
+    d.inv_h_d[e] = 1.0 / h[e];
+    d.lo_f[e] = (float)lo[e];
+    d.inv_h_f[e] = (float)(1.0 / h[e]);
+  }
+  return d;
+}
+
+namespace {
+
+inline cudaStream_t cs(love_stream_t s) { return (cudaStream_t)s; }
+
+size_t dtype_size(love_dtype d) { return d == LOVE_F64 ? 8 : (d == LOVE_BF16 ? 2 : 4); }
+
+love_status grid_from_desc(const love_ski_desc* d, GridHost& g) {
+  if (!d || d->dim < 1 || d->dim > LOVE_MAX_DIM) return LOVE_ERR_ARG;
+  if (!(d->outputscale > 0) || !(d->noise > 0)) return LOVE_ERR_ARG;
+  g.dim = d->dim;
+  int64_t m = 1;
+  for (int e = 0; e < LOVE_MAX_DIM; ++e) {
+    if (e < d->dim) {
+      if (d->grid_size[e] < 4 || !(d->grid_hi[e] > d->grid_lo[e]) || !(d->lengthscale[e] > 0)) return LOVE_ERR_ARG;
+      g.g[e] = d->grid_size[e];
+      g.lo[e] = d->grid_lo[e];
+      g.h[e] = (d->grid_hi[e] - d->grid_lo[e]) / (double)(d->grid_size[e] - 1);
+      g.ls[e] = d->lengthscale[e];
+    } else {
+      g.g[e] = 1;
+      g.lo[e] = 0;
+      g.h[e] = 1;
+      g.ls[e] = 1;
+    }
+    m *= g.g[e];
+  }
+  if (m > (int64_t(1) << 30)) return LOVE_ERR_UNSUPPORTED;
+  g.m = m;
+  int64_t st = 1;
+  for (int e = d->dim - 1; e >= 0; --e) {
+    g.stride[e] = st;
+    st *= g.g[e];
+  }
+  for (int e = d->dim; e < LOVE_MAX_DIM; ++e) g.stride[e] = 1;
+  g.sf = d->outputscale;
+  g.noise = d->noise;
+  for (int e = 0; e < d->dim; ++e)
+    for (int q = 0; q < 4; ++q) {
+      double r = q * g.h[e];
+      double ls = g.ls[e];
+      double v = std::exp(-(r * r) / (2 * ls * ls));
+      g.cloc[e][q] = v;
+      g.cloc_dl[e][q] = v * r * r / (ls * ls * ls);
+    }
+  return LOVE_OK;
+}
+
+Allocator make_alloc(const love_allocator* a) {
+  Allocator al;
+  if (a && a->alloc && a->free) {
+    al.a = *a;
+    al.user = true;
+  }
+  return al;
+}
+
+int round_up(int v, int q) { return (v + q - 1) / q * q; }
+
+// CUDA events around the pre-compute phases (reported by love_cache_info)
+struct PhaseEvents {
+  cudaEvent_t e[5] = {};
+  bool ok = true;
+  PhaseEvents() {
+    for (auto& x : e) ok &= cudaEventCreate(&x) == cudaSuccess;
+  }
+  ~PhaseEvents() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  void record(int i, cudaStream_t s) {
+    if (ok) cudaEventRecord(e[i], s);
+  }
+  void elapsed(float* out) {
+    for (int i = 0; i < 4; ++i) {
+      out[i] = 0.f;
+      if (ok) cudaEventElapsedTime(&out[i], e[i], e[i + 1]);
+    }
+  }
+};
+
+void destroy_cache_buffers(love_cache* c, cudaStream_t s) {
+  const Allocator& al = c->alloc;
+  const int64_t m = c->grid.m;
+  al.free(c->Rc, (size_t)m * c->ld * dtype_size(c->cache_dtype), s);
+  al.free(c->S, (size_t)m * c->ld_s * dtype_size(c->dtype), s);
+  al.free(c->P, (size_t)m * c->k_eff * dtype_size(c->dtype), s);
+  al.free(c->KdP, (size_t)c->grid.dim * m * c->ld_g * dtype_size(c->dtype), s);
+  al.free(c->B, (size_t)c->grid.dim * c->k_eff * c->k_eff * dtype_size(c->dtype), s);
+  al.free(c->Minv, (size_t)c->k_eff * c->k_eff * dtype_size(c->dtype), s);
+  al.free(c->status, sizeof(DevStatus), s);
+  delete[] c->alpha;
+  delete[] c->beta;
+  c->Rc = c->S = c->P = c->KdP = c->B = c->Minv = nullptr;
+  c->status = nullptr;
+}
+
+love_cache* new_cache(const GridHost& g, love_dtype dt, love_dtype cdt, unsigned flags, int k, const Allocator& al,
+                      cudaStream_t s) {
+  love_cache* c = new (std::nothrow) love_cache();
+  if (!c) return nullptr;
+  c->grid = g;
+  c->dtype = dt;
+  c->cache_dtype = cdt;
+  c->flags = flags;
+  c->k_eff = k;
+  c->alloc = al;
+  int vec = (int)(16 / dtype_size(cdt));
+  c->ld = round_up(k + 1, vec);
+  c->alpha = new double[k + 1]();
+  c->beta = new double[k + 1]();
+  c->status = (DevStatus*)al.alloc(sizeof(DevStatus), s);
+  c->Rc = al.alloc((size_t)g.m * c->ld * dtype_size(cdt), s);
+  if (!c->status || !c->Rc) {
+    destroy_cache_buffers(c, s);
+    delete c;
+    return nullptr;
+  }
+  cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s);
+  return c;
+}
+
+__global__ void k_import_pack(const double* __restrict__ Rt, int k, const double* __restrict__ a, int64_t m,
+                              int ld, int cdt, void* out) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * ld) return;
+  int64_t r = idx / ld;
+  int c = (int)(idx - r * ld);
+  double v = 0.0;
+  if (c < k) v = Rt[r * k + c];
+  else if (c == k && a) v = a[r];
+  if (cdt == LOVE_BF16) ((__nv_bfloat16*)out)[idx] = __double2bfloat16(v);
+  else if (cdt == LOVE_F64) ((double*)out)[idx] = v;
+  else ((float*)out)[idx] = (float)v;
+}
+// row-major m x k doubles -> column-major m x k of dtype (or row-major with ld)
+__global__ void k_import_colmajor(const double* __restrict__ src, int k, int64_t m, int dbl, void* out) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * k) return;
+  int64_t r = idx / k;
+  int c = (int)(idx - r * k);
+  if (dbl) ((double*)out)[(int64_t)c * m + r] = src[idx];
+  else ((float*)out)[(int64_t)c * m + r] = (float)src[idx];
+}
+__global__ void k_import_rows(const double* __restrict__ src, int k, int64_t m, int ld, int dbl, void* out) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * ld) return;
+  int64_t r = idx / ld;
+  int c = (int)(idx - r * ld);
+  double v = c < k ? src[r * k + c] : 0.0;
+  if (dbl) ((double*)out)[idx] = v;
+  else ((float*)out)[idx] = (float)v;
+}
+
+double bf16_to_double(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* love_status_string(love_status s) {
+  switch (s) {
+    case LOVE_OK: return "ok";
+    case LOVE_ERR_ARG: return "invalid argument";
+    case LOVE_ERR_DOMAIN: return "point outside the interpolable grid (or NaN)";
+    case LOVE_ERR_NOT_PD: return "tridiagonal matrix not positive definite";
+    case LOVE_ERR_NAN: return "NaN or Inf in a reduction";
+    case LOVE_ERR_OOM: return "out of device memory";
+    case LOVE_ERR_CUDA: return "CUDA runtime error";
+    case LOVE_ERR_TIMEOUT: return "bounded device wait expired";
+    case LOVE_ERR_STATE: return "handle lacks what the call needs";
+    case LOVE_ERR_UNSUPPORTED: return "configuration not supported by this build";
+  }
+  return "unknown status";
+}
+
+int love_last_cuda_error(void) { return g_last_cuda_error; }
+uint64_t love_launch_count(void) { return g_launches.load(); }
+const char* love_version(void) { return "love-gb300 1.0 (sm_103a)"; }
+
+love_status ski_destroy(love_ski_t ski) {
+  if (!ski) return LOVE_ERR_ARG;
+  cudaStream_t s = 0;
+  const Allocator& al = ski->alloc;
+  size_t es = dtype_size(ski->dtype);
+  al.free(ski->xs, (size_t)ski->n_pad * ski->grid.dim * es, s);
+  al.free(ski->ys, (size_t)ski->n_pad * es, s);
+  al.free(ski->perm, (size_t)ski->n * 4, s);
+  al.free(ski->cell_start, (size_t)(ski->grid.m + 1) * 4, s);
+  al.free(ski->status, sizeof(DevStatus), s);
+  for (int e = 0; e < ski->grid.dim; ++e) fft_plan_destroy(ski->fft[e], al, s);
+  cudaStreamSynchronize(s);
+  delete ski;
+  return LOVE_OK;
+}
+
+love_status ski_build(const love_ski_desc* desc, const void* x_train, const void* y_train, love_stream_t stream,
+                      love_ski_t* out) {
+  if (!desc || !x_train || !out) return LOVE_ERR_ARG;
+  *out = nullptr;
+  if (desc->n < 1 || desc->n > (int64_t(1) << 31) - 1024) return LOVE_ERR_ARG;
+  if (desc->dtype != LOVE_F32 && desc->dtype != LOVE_F64) return LOVE_ERR_ARG;
+  GridHost g;
+  LOVE_TRY(grid_from_desc(desc, g));
+  cudaStream_t s = cs(stream);
+  love_ski* ski = new (std::nothrow) love_ski();
+  if (!ski) return LOVE_ERR_OOM;
+  ski->grid = g;
+  ski->dtype = desc->dtype;
+  ski->n = desc->n;
+  ski->n_pad = (desc->n + 255) / 256 * 256;
+  ski->alloc = make_alloc(desc->allocator);
+  cudaGetDevice(&ski->device);
+  const Allocator& al = ski->alloc;
+  size_t es = dtype_size(ski->dtype);
+  ski->xs = al.alloc((size_t)ski->n_pad * g.dim * es, s);
+  ski->ys = y_train ? al.alloc((size_t)ski->n_pad * es, s) : nullptr;
+  ski->perm = (int32_t*)al.alloc((size_t)ski->n * 4, s);
+  ski->cell_start = (int32_t*)al.alloc((size_t)(g.m + 1) * 4, s);
+  ski->status = (DevStatus*)al.alloc(sizeof(DevStatus), s);
+  if (!ski->xs || (y_train && !ski->ys) || !ski->perm || !ski->cell_start || !ski->status) {
+    ski_destroy(ski);
+    return LOVE_ERR_OOM;
+  }
+  love_status rc = cuda_check(cudaMemsetAsync(ski->status, 0, sizeof(DevStatus), s));
+  for (int e = 0; e < g.dim && rc == LOVE_OK; ++e) rc = fft_plan_create(ski->fft[e], g, e, al, s);
+  if (rc == LOVE_OK) rc = sort_training_points(ski, x_train, y_train, s);
+  DevStatus st{};
+  if (rc == LOVE_OK) rc = cuda_check(cudaMemcpyAsync(&st, ski->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc == LOVE_OK && st.domain_errors) rc = LOVE_ERR_DOMAIN;
+  if (rc != LOVE_OK) {
+    ski_destroy(ski);
+    return rc;
+  }
+  *out = ski;
+  return LOVE_OK;
+}
+
+love_status ski_mvm(love_ski_t ski, const void* v, void* out, love_stream_t stream) {
+  if (!ski || !v || !out || v == out) return LOVE_ERR_ARG;
+  cudaStream_t s = cs(stream);
+  const Allocator& al = ski->alloc;
+  size_t es = dtype_size(ski->dtype);
+  const GridHost& g = ski->grid;
+  size_t fwb = fft_work_bytes(g, ski->fft, 1, ski->dtype == LOVE_F64);
+  size_t wb = es * (size_t)g.m * 2 + fwb + 256;
+  size_t vb = es * (size_t)ski->n_pad;
+  void* work = al.alloc(wb, s);
+  void* vs = al.alloc(vb, s);
+  void* ys = al.alloc(vb, s);
+  love_status rc = (work && vs && ys) ? LOVE_OK : LOVE_ERR_OOM;
+  if (rc == LOVE_OK) {
+    if (ski->dtype == LOVE_F64) {
+      rc = permute_in<double>((const double*)v, ski->perm, ski->n, ski->n_pad, (double*)vs, s);
+      if (rc == LOVE_OK) rc = ski_mvm_sorted<double>(ski, (const double*)vs, (double*)ys, work, s);
+      if (rc == LOVE_OK) rc = permute_out<double>((const double*)ys, ski->perm, ski->n, (double*)out, s);
+    } else {
+      rc = permute_in<float>((const float*)v, ski->perm, ski->n, ski->n_pad, (float*)vs, s);
+      if (rc == LOVE_OK) rc = ski_mvm_sorted<float>(ski, (const float*)vs, (float*)ys, work, s);
+      if (rc == LOVE_OK) rc = permute_out<float>((const float*)ys, ski->perm, ski->n, (float*)out, s);
+    }
+  }
+  al.free(work, wb, s);
+  al.free(vs, vb, s);
+  al.free(ys, vb, s);
+  return rc;
+}
+
+love_status ski_mvm_kuu(love_ski_t ski, const void* v, void* out, love_stream_t stream) {
+  if (!ski || !v || !out) return LOVE_ERR_ARG;
+  cudaStream_t s = cs(stream);
+  const GridHost& g = ski->grid;
+  size_t fwb = fft_work_bytes(g, ski->fft, 1, ski->dtype == LOVE_F64);
+  void* fw = fwb ? ski->alloc.alloc(fwb, s) : nullptr;
+  if (fwb && !fw) return LOVE_ERR_OOM;
+  love_status rc;
+  if (ski->dtype == LOVE_F64)
+    rc = kuu_apply<double>(g, ski->fft, (const double*)v, (double*)out, 1, g.m, fw, -1, s);
+  else
+    rc = kuu_apply<float>(g, ski->fft, (const float*)v, (float*)out, 1, g.m, fw, -1, s);
+  if (fw) ski->alloc.free(fw, fwb, s);
+  return rc;
+}
+
+love_status love_cache_destroy(love_cache_t c) {
+  if (!c) return LOVE_ERR_ARG;
+  destroy_cache_buffers(c, 0);
+  cudaStreamSynchronize(0);
+  delete c;
+  return LOVE_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o, cudaStream_t s, love_cache** out,
+                                   int* k_eff_out) {
+  const GridHost& g = ski->grid;
+  const Allocator& al = ski->alloc;
+  int k = std::min<int64_t>(o->k, std::min<int64_t>(ski->n, g.m));
+  double tau = o->breakdown_tol > 0 ? o->breakdown_tol : (sizeof(T) == 8 ? 1e-12 : 1e-8);
+  const int64_t ldq = ski->n_pad;
+  size_t qb = sizeof(T) * (size_t)ldq * k;
+  T* Q = (T*)al.alloc(qb, s);
+  if (!Q) return LOVE_ERR_OOM;
+  std::vector<double> alpha(k + 1), beta(k + 1);
+  int keff = 0;
+  PhaseEvents ev;
+  ev.record(0, s);
+  love_status rc = lanczos_run<T>(ski, k, tau, Q, ldq, alpha.data(), beta.data(), &keff, s);
+  ev.record(1, s);
+  if (rc != LOVE_OK) {
+    al.free(Q, qb, s);
+    return rc;
+  }
+  // status from the Lanczos kernels (NaN, timeout)
+  DevStatus dst{};
+  cudaMemcpyAsync(&dst, ski->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (dst.bits & (1u << LOVE_ERR_TIMEOUT)) rc = LOVE_ERR_TIMEOUT;
+  else if (dst.bits & (1u << LOVE_ERR_NAN)) rc = LOVE_ERR_NAN;
+  if (rc == LOVE_OK && keff < 1) rc = LOVE_ERR_NAN;
+  if (rc != LOVE_OK) {
+    cudaMemsetAsync(ski->status, 0, sizeof(DevStatus), s);
+    al.free(Q, qb, s);
+    return rc;
+  }
+  unsigned flags = o->flags;
+  if (!ski->ys) flags &= ~LOVE_WANT_MEAN;
+  love_cache* c = new_cache(g, ski->dtype, o->cache_dtype, flags, keff, al, s);
+  if (!c) {
+    al.free(Q, qb, s);
+    return LOVE_ERR_OOM;
+  }
+  std::copy(alpha.begin(), alpha.begin() + keff, c->alpha);
+  std::copy(beta.begin(), beta.begin() + std::max(keff - 1, 0), c->beta);
+  double* z = nullptr;
+  size_t zb = sizeof(double) * (size_t)ldq;
+  if (flags & LOVE_WANT_MEAN) {
+    z = (double*)al.alloc(zb, s);
+    if (!z) rc = LOVE_ERR_OOM;
+    double tol = o->cg_tol > 0 ? o->cg_tol : (sizeof(T) == 8 ? 1e-12 : 1e-8);
+    int maxit = o->cg_max_iter > 0 ? o->cg_max_iter : 4000;
+    if (rc == LOVE_OK) rc = cg_solve<T>(ski, (const T*)ski->ys, z, tol, maxit, &c->cg_iters, s);
+  }
+  ev.record(2, s);
+  if (rc == LOVE_OK && (flags & LOVE_WANT_GRAD)) {
+    c->P = al.alloc(sizeof(T) * (size_t)g.m * keff, s);
+    if (!c->P) rc = LOVE_ERR_OOM;
+  }
+  T* rt_keep = nullptr;
+  size_t rtb = sizeof(T) * (size_t)g.m * keff;
+  if (rc == LOVE_OK && (flags & LOVE_WANT_SAMPLER)) {
+    rt_keep = (T*)al.alloc(rtb, s);
+    if (!rt_keep) rc = LOVE_ERR_OOM;
+  }
+  if (rc == LOVE_OK) rc = build_cache<T>(ski, c, Q, ldq, z, s, rt_keep);
+  if (rc == LOVE_OK && (flags & LOVE_WANT_GRAD)) rc = backward_tables(c, ski->fft, c->P, keff, s);
+  ev.record(3, s);
+  if (z) al.free(z, zb, s);
+  al.free(Q, qb, s);
+  if (rc == LOVE_OK && (flags & LOVE_WANT_SAMPLER)) {
+    int ks = o->sampler_k > 0 ? o->sampler_k : o->k;
+    ks = std::min<int64_t>(ks, g.m);
+    rc = sampler_build<T>(ski, c, rt_keep, ks, o->sampler_seed, 1e-12, s);
+  }
+  if (rt_keep) al.free(rt_keep, rtb, s);
+  ev.record(4, s);
+  if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc == LOVE_OK) ev.elapsed(c->phase_ms);
+  if (rc != LOVE_OK) {
+    love_cache_destroy(c);
+    return rc;
+  }
+  *out = c;
+  if (k_eff_out) *k_eff_out = keff;
+  return LOVE_OK;
+}
+
+extern "C" {
+
+love_status love_precompute(love_ski_t ski, const love_precompute_opts* opts, love_stream_t stream,
+                            love_cache_t* out, int* k_eff) {
+  if (!ski || !opts || !out) return LOVE_ERR_ARG;
+  *out = nullptr;
+  if (opts->k < 1 || opts->k > LOVE_MAX_K) return LOVE_ERR_ARG;
+  if (ski->dtype == LOVE_F64 && opts->cache_dtype != LOVE_F64) return LOVE_ERR_ARG;
+  if (ski->dtype == LOVE_F32 && opts->cache_dtype == LOVE_F64) return LOVE_ERR_ARG;
+  if (opts->sampler_k > LOVE_MAX_K) return LOVE_ERR_ARG;
+  cudaStream_t s = cs(stream);
+  if (ski->dtype == LOVE_F64) return precompute_impl<double>(ski, opts, s, out, k_eff);
+  return precompute_impl<float>(ski, opts, s, out, k_eff);
+}
+
+love_status love_predict_mean_var(love_cache_t c, int64_t t, const void* x_test, void* mean, void* var,
+                                  love_stream_t stream) {
+  if (!c || t < 0) return LOVE_ERR_ARG;
+  if (t == 0) return LOVE_OK;
+  if (!x_test || !var) return LOVE_ERR_ARG;
+  if (mean && !(c->flags & LOVE_WANT_MEAN)) return LOVE_ERR_STATE;
+  return predict_launch(c, t, x_test, mean, var, cs(stream));
+}
+
+love_status love_sample(love_cache_t c, int64_t t, const void* x_test, int s_count, const void* z, uint64_t seed,
+                        void* out, love_stream_t stream) {
+  if (!c || t < 0 || s_count < 0) return LOVE_ERR_ARG;
+  if (!c->S) return LOVE_ERR_STATE;
+  if (t == 0 || s_count == 0) return LOVE_OK;
+  if (!x_test || !out) return LOVE_ERR_ARG;
+  return sample_launch(c, t, x_test, s_count, z, seed, out, cs(stream));
+}
+
+love_status love_var_backward(love_cache_t c, int64_t t, const void* x_test, const void* grad_var, void* grad_x,
+                              double* grad_lengthscale, double* grad_noise, love_stream_t stream) {
+  if (!c || t < 0) return LOVE_ERR_ARG;
+  if (!(c->flags & LOVE_WANT_GRAD) || !c->KdP) return LOVE_ERR_STATE;
+  if (t > 0 && (!x_test || !grad_var)) return LOVE_ERR_ARG;
+  return backward_launch(c, t, x_test, grad_var, grad_x, grad_lengthscale, grad_noise, cs(stream));
+}
+
+love_status love_cache_info(love_cache_t c, love_cache_info_t* info) {
+  if (!c || !info) return LOVE_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->dim = c->grid.dim;
+  for (int e = 0; e < 3; ++e) info->grid_size[e] = c->grid.g[e];
+  info->m = c->grid.m;
+  info->k_eff = c->k_eff;
+  info->ld = c->ld;
+  info->sampler_k = c->ks;
+  info->cg_iters = c->cg_iters;
+  info->sampler_fallback = c->sampler_fallback;
+  info->dtype = c->dtype;
+  info->cache_dtype = c->cache_dtype;
+  info->flags = c->flags;
+  for (int i = 0; i < 4; ++i) info->phase_ms[i] = c->phase_ms[i];
+  return LOVE_OK;
+}
+
+love_status love_cache_import(const love_ski_desc* desc, int k, love_dtype cache_dtype, unsigned flags,
+                              const double* Rt, const double* a, int ks, const double* S, const double* alpha,
+                              const double* beta, const double* P, love_stream_t stream, love_cache_t* out) {
+  if (!desc || !Rt || !out || k < 1 || k > LOVE_MAX_K || ks < 0 || ks > LOVE_MAX_K) return LOVE_ERR_ARG;
+  if (desc->dtype != LOVE_F32 && desc->dtype != LOVE_F64) return LOVE_ERR_ARG;
+  if (desc->dtype == LOVE_F64 && cache_dtype != LOVE_F64) return LOVE_ERR_ARG;
+  if (desc->dtype == LOVE_F32 && cache_dtype == LOVE_F64) return LOVE_ERR_ARG;
+  if ((flags & LOVE_WANT_GRAD) && (!P || !alpha || !beta)) return LOVE_ERR_ARG;
+  if ((flags & LOVE_WANT_SAMPLER) && (!S || ks < 1)) return LOVE_ERR_ARG;
+  *out = nullptr;
+  GridHost g;
+  LOVE_TRY(grid_from_desc(desc, g));
+  cudaStream_t s = cs(stream);
+  Allocator al = make_alloc(desc->allocator);
+  if (!a) flags &= ~LOVE_WANT_MEAN;
+  love_cache* c = new_cache(g, desc->dtype, cache_dtype, flags, k, al, s);
+  if (!c) return LOVE_ERR_OOM;
+  if (alpha) std::copy(alpha, alpha + k, c->alpha);
+  if (beta && k > 1) std::copy(beta, beta + k - 1, c->beta);
+  const int64_t m = g.m;
+  const bool dbl = desc->dtype == LOVE_F64;
+  love_status rc = LOVE_OK;
+  size_t hb = sizeof(double) * (size_t)m * (size_t)std::max(k, ks) + sizeof(double) * m;
+  double* h = (double*)al.alloc(hb, s);
+  if (!h) rc = LOVE_ERR_OOM;
+  if (rc == LOVE_OK) {
+    rc = cuda_check(cudaMemcpyAsync(h, Rt, sizeof(double) * m * k, cudaMemcpyHostToDevice, s));
+    double* ad = nullptr;
+    if (rc == LOVE_OK && a) {
+      ad = h + (size_t)m * std::max(k, ks);
+      rc = cuda_check(cudaMemcpyAsync(ad, a, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    }
+    if (rc == LOVE_OK) {
+      LOVE_COUNT_LAUNCH(); k_import_pack<<<ceil_div(m * c->ld, 256), 256, 0, s>>>(h, k, ad, m, c->ld, (int)cache_dtype, c->Rc);
+      rc = cuda_check(cudaGetLastError());
+    }
+  }
+  if (rc == LOVE_OK && (flags & LOVE_WANT_SAMPLER)) {
+    c->ks = ks;
+    c->ld_s = round_up(ks, dbl ? 2 : 4);
+    c->S = al.alloc(dtype_size(desc->dtype) * (size_t)m * c->ld_s, s);
+    if (!c->S) rc = LOVE_ERR_OOM;
+    if (rc == LOVE_OK) rc = cuda_check(cudaMemcpyAsync(h, S, sizeof(double) * m * ks, cudaMemcpyHostToDevice, s));
+    if (rc == LOVE_OK) {
+      LOVE_COUNT_LAUNCH(); k_import_rows<<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(h, ks, m, c->ld_s, dbl, c->S);
+      rc = cuda_check(cudaGetLastError());
+    }
+  }
+  if (rc == LOVE_OK && (flags & LOVE_WANT_GRAD)) {
+    c->P = al.alloc(dtype_size(desc->dtype) * (size_t)m * k, s);
+    if (!c->P) rc = LOVE_ERR_OOM;
+    if (rc == LOVE_OK) rc = cuda_check(cudaMemcpyAsync(h, P, sizeof(double) * m * k, cudaMemcpyHostToDevice, s));
+    if (rc == LOVE_OK) {
+      LOVE_COUNT_LAUNCH(); k_import_colmajor<<<ceil_div(m * k, 256), 256, 0, s>>>(h, k, m, dbl, c->P);
+      rc = cuda_check(cudaGetLastError());
+    }
+    if (rc == LOVE_OK) {
+      FftPlan plans[LOVE_MAX_DIM];
+      for (int e = 0; e < g.dim && rc == LOVE_OK; ++e) rc = fft_plan_create(plans[e], g, e, al, s);
+      if (rc == LOVE_OK) rc = backward_tables(c, plans, c->P, k, s);
+      for (int e = 0; e < g.dim; ++e) fft_plan_destroy(plans[e], al, s);
+    }
+  }
+  if (h) al.free(h, hb, s);
+  if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc != LOVE_OK) {
+    love_cache_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LOVE_OK;
+}
+
+love_status love_cache_export(love_cache_t c, double* Rt, double* a, double* S, double* P, double* alpha,
+                              double* beta, love_stream_t stream) {
+  if (!c) return LOVE_ERR_ARG;
+  cudaStream_t s = cs(stream);
+  const int64_t m = c->grid.m;
+  const int k = c->k_eff;
+  if (Rt || a) {
+    size_t es = dtype_size(c->cache_dtype);
+    std::vector<unsigned char> buf((size_t)m * c->ld * es);
+    LOVE_CUDA(cudaMemcpyAsync(buf.data(), c->Rc, buf.size(), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    for (int64_t r = 0; r < m; ++r)
+      for (int q = 0; q <= k; ++q) {
+        size_t idx = (size_t)r * c->ld + q;
+        double v;
+        if (c->cache_dtype == LOVE_F64) v = ((const double*)buf.data())[idx];
+        else if (c->cache_dtype == LOVE_BF16) v = bf16_to_double(((const uint16_t*)buf.data())[idx]);
+        else v = ((const float*)buf.data())[idx];
+        if (q < k && Rt) Rt[r * k + q] = v;
+        if (q == k && a) a[r] = (c->flags & LOVE_WANT_MEAN) ? v : 0.0;
+      }
+  }
+  const bool dbl = c->dtype == LOVE_F64;
+  if (S && c->S) {
+    std::vector<unsigned char> buf((size_t)m * c->ld_s * (dbl ? 8 : 4));
+    LOVE_CUDA(cudaMemcpyAsync(buf.data(), c->S, buf.size(), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    for (int64_t r = 0; r < m; ++r)
+      for (int q = 0; q < c->ks; ++q) {
+        size_t idx = (size_t)r * c->ld_s + q;
+        S[r * c->ks + q] = dbl ? ((const double*)buf.data())[idx] : ((const float*)buf.data())[idx];
+      }
+  }
+  if (P && c->P) {
+    std::vector<unsigned char> buf((size_t)m * k * (dbl ? 8 : 4));
+    LOVE_CUDA(cudaMemcpyAsync(buf.data(), c->P, buf.size(), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    for (int64_t r = 0; r < m; ++r)
+      for (int q = 0; q < k; ++q) {
+        size_t idx = (size_t)q * m + r;
+        P[r * k + q] = dbl ? ((const double*)buf.data())[idx] : ((const float*)buf.data())[idx];
+      }
+  }
+  if (alpha) std::copy(c->alpha, c->alpha + k, alpha);
+  if (beta && k > 1) std::copy(c->beta, c->beta + k - 1, beta);
+  return LOVE_OK;
+}
+
+love_status love_get_device_status(love_cache_t c, int reset, love_device_status_t* st, love_stream_t stream) {
+  if (!c || !st) return LOVE_ERR_ARG;
+  cudaStream_t s = cs(stream);
+  DevStatus d{};
+  LOVE_CUDA(cudaMemcpyAsync(&d, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  if (reset) LOVE_CUDA(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  st->bits = d.bits;
+  st->domain_errors = (int64_t)d.domain_errors;
+  st->clamped = (int64_t)d.clamped;
+  return LOVE_OK;
+}
+
+// ---- checkpoint ---------------------------------------------------------------
+static const char kMagic[8] = {'L', 'O', 'V', 'E', 'C', 'A', 'C', 'H'};
+static const uint32_t kVersion = 1;
+
+struct CacheHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t dim;
+  int64_t g[3];
+  double lo[3], h[3], ls[3];
+  double sf, noise;
+  int32_t dtype, cache_dtype;
+  uint32_t flags;
+  int32_t k_eff, ld, ks, ld_s, ld_g, cg_iters, sampler_fallback;
+  uint64_t bytes_rc, bytes_s, bytes_p, bytes_kdp, bytes_b, bytes_minv;
+};
+
+static love_status write_dev(FILE* f, const void* dptr, size_t bytes, cudaStream_t s) {
+  if (!bytes) return LOVE_OK;
+  std::vector<unsigned char> buf(bytes);
+  LOVE_CUDA(cudaMemcpyAsync(buf.data(), dptr, bytes, cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  return fwrite(buf.data(), 1, bytes, f) == bytes ? LOVE_OK : LOVE_ERR_ARG;
+}
+static love_status read_dev(FILE* f, void** dptr, size_t bytes, const Allocator& al, cudaStream_t s) {
+  if (!bytes) return LOVE_OK;
+  std::vector<unsigned char> buf(bytes);
+  if (fread(buf.data(), 1, bytes, f) != bytes) return LOVE_ERR_ARG;
+  *dptr = al.alloc(bytes, s);
+  if (!*dptr) return LOVE_ERR_OOM;
+  LOVE_CUDA(cudaMemcpyAsync(*dptr, buf.data(), bytes, cudaMemcpyHostToDevice, s));
+  return cuda_check(cudaStreamSynchronize(s));
+}
+
+love_status love_cache_save(love_cache_t c, const char* path, love_stream_t stream) {
+  if (!c || !path) return LOVE_ERR_ARG;
+  cudaStream_t s = cs(stream);
+  CacheHeader hd{};
+  std::memcpy(hd.magic, kMagic, 8);
+  hd.version = kVersion;
+  hd.dim = c->grid.dim;
+  for (int e = 0; e < 3; ++e) {
+    hd.g[e] = c->grid.g[e];
+    hd.lo[e] = c->grid.lo[e];
+    hd.h[e] = c->grid.h[e];
+    hd.ls[e] = c->grid.ls[e];
+  }
+  hd.sf = c->grid.sf;
+  hd.noise = c->grid.noise;
+  hd.dtype = c->dtype;
+  hd.cache_dtype = c->cache_dtype;
+  hd.flags = c->flags;
+  hd.k_eff = c->k_eff;
+  hd.ld = c->ld;
+  hd.ks = c->ks;
+  hd.ld_s = c->ld_s;
+  hd.ld_g = c->ld_g;
+  hd.cg_iters = c->cg_iters;
+  hd.sampler_fallback = c->sampler_fallback;
+  const int64_t m = c->grid.m;
+  size_t es = dtype_size(c->dtype);
+  hd.bytes_rc = (uint64_t)m * c->ld * dtype_size(c->cache_dtype);
+  hd.bytes_s = c->S ? (uint64_t)m * c->ld_s * es : 0;
+  hd.bytes_p = c->P ? (uint64_t)m * c->k_eff * es : 0;
+  hd.bytes_kdp = c->KdP ? (uint64_t)c->grid.dim * m * c->ld_g * es : 0;
+  hd.bytes_b = c->B ? (uint64_t)c->grid.dim * c->k_eff * c->k_eff * es : 0;
+  hd.bytes_minv = c->Minv ? (uint64_t)c->k_eff * c->k_eff * es : 0;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return LOVE_ERR_ARG;
+  love_status rc = fwrite(&hd, sizeof(hd), 1, f) == 1 ? LOVE_OK : LOVE_ERR_ARG;
+  if (rc == LOVE_OK && fwrite(c->alpha, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
+  if (rc == LOVE_OK && fwrite(c->beta, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
+  if (rc == LOVE_OK) rc = write_dev(f, c->Rc, hd.bytes_rc, s);
+  if (rc == LOVE_OK) rc = write_dev(f, c->S, hd.bytes_s, s);
+  if (rc == LOVE_OK) rc = write_dev(f, c->P, hd.bytes_p, s);
+  if (rc == LOVE_OK) rc = write_dev(f, c->KdP, hd.bytes_kdp, s);
+  if (rc == LOVE_OK) rc = write_dev(f, c->B, hd.bytes_b, s);
+  if (rc == LOVE_OK) rc = write_dev(f, c->Minv, hd.bytes_minv, s);
+  std::fclose(f);
+  return rc;
+}
+
+love_status love_cache_load(const char* path, const love_allocator* allocator, love_stream_t stream,
+                            love_cache_t* out) {
+  if (!path || !out) return LOVE_ERR_ARG;
+  *out = nullptr;
+  cudaStream_t s = cs(stream);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return LOVE_ERR_ARG;
+  CacheHeader hd{};
+  if (fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != kVersion ||
+      hd.dim < 1 || hd.dim > 3 || hd.k_eff < 1 || hd.k_eff > LOVE_MAX_K) {
+    std::fclose(f);
+    return LOVE_ERR_ARG;
+  }
+  love_cache* c = new (std::nothrow) love_cache();
+  if (!c) {
+    std::fclose(f);
+    return LOVE_ERR_OOM;
+  }
+  GridHost& g = c->grid;
+  g.dim = hd.dim;
+  g.m = 1;
+  for (int e = 0; e < 3; ++e) {
+    g.g[e] = hd.g[e];
+    g.lo[e] = hd.lo[e];
+    g.h[e] = hd.h[e];
+    g.ls[e] = hd.ls[e];
+    g.m *= g.g[e];
+  }
+  int64_t st = 1;
+  for (int e = g.dim - 1; e >= 0; --e) {
+    g.stride[e] = st;
+    st *= g.g[e];
+  }
+  g.sf = hd.sf;
+  g.noise = hd.noise;
+  for (int e = 0; e < g.dim; ++e)
+    for (int q = 0; q < 4; ++q) {
+      double r = q * g.h[e], ls = g.ls[e];
+      double v = std::exp(-(r * r) / (2 * ls * ls));
+      g.cloc[e][q] = v;
+      g.cloc_dl[e][q] = v * r * r / (ls * ls * ls);
+    }
+  c->dtype = (love_dtype)hd.dtype;
+  c->cache_dtype = (love_dtype)hd.cache_dtype;
+  c->flags = hd.flags;
+  c->k_eff = hd.k_eff;
+  c->ld = hd.ld;
+  c->ks = hd.ks;
+  c->ld_s = hd.ld_s;
+  c->ld_g = hd.ld_g;
+  c->cg_iters = hd.cg_iters;
+  c->sampler_fallback = hd.sampler_fallback;
+  c->alloc = make_alloc(allocator);
+  c->alpha = new double[c->k_eff + 1]();
+  c->beta = new double[c->k_eff + 1]();
+  love_status rc = LOVE_OK;
+  if (fread(c->alpha, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
+  if (rc == LOVE_OK && fread(c->beta, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
+  if (rc == LOVE_OK) rc = read_dev(f, &c->Rc, hd.bytes_rc, c->alloc, s);
+  if (rc == LOVE_OK) rc = read_dev(f, &c->S, hd.bytes_s, c->alloc, s);
+  if (rc == LOVE_OK) rc = read_dev(f, &c->P, hd.bytes_p, c->alloc, s);
+  if (rc == LOVE_OK) rc = read_dev(f, &c->KdP, hd.bytes_kdp, c->alloc, s);
+  if (rc == LOVE_OK) rc = read_dev(f, &c->B, hd.bytes_b, c->alloc, s);
+  if (rc == LOVE_OK) rc = read_dev(f, &c->Minv, hd.bytes_minv, c->alloc, s);
+  std::fclose(f);
+  if (rc == LOVE_OK) {
+    c->status = (DevStatus*)c->alloc.alloc(sizeof(DevStatus), s);
+    if (!c->status) rc = LOVE_ERR_OOM;
+    else rc = cuda_check(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+  }
+  if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc != LOVE_OK) {
+    love_cache_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return LOVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+// love_internal.cuh -- shared definitions of the GB300 LOVE library.
+//
+// Device-side building blocks used by every kernel file:
+//   * double-float ("df") arithmetic: a value hi + lo of two floats, built from
+//     the error-free transformations TwoSum (Knuth) and TwoProduct via FMA.
+//     GB300 runs FP64 at a small fraction of its FP32 rate, so sums whose
+//     cancellation needs more than 24 bits (reorthogonalisation dots, the
+//     predictive variance p - |v|^2) are accumulated in df (~48-bit) instead
+//     of native doubles (Dot2 of Ogita, Rump & Oishi 2005).
+//   * Keys cubic-convolution weights (Sec. 2.3; a = -1/2).
+//   * bounded mbarrier waits and 1-D bulk async copies (TMA) in inline PTX.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/love.h"
+
+#define LOVE_MAX_DIM 3
+#define LOVE_MAX_K 200
+
+// ---------------------------------------------------------------------------
+// device status word (one per handle)
+struct DevStatus {
+  unsigned int bits;
+  unsigned int pad;
+  unsigned long long domain_errors;
+  unsigned long long clamped;
+};
+
+__device__ __forceinline__ void dev_flag(DevStatus* st, love_status s) {
+  if (st) atomicOr(&st->bits, 1u << (unsigned)s);
+}
+
+// ---------------------------------------------------------------------------
+// grid description passed by value to kernels
+struct GridDev {
+  int dim;
+  int g[LOVE_MAX_DIM];          // points per dimension
+  int stride[LOVE_MAX_DIM];     // linear-index stride of each dimension
+  float lo_f[LOVE_MAX_DIM];
+  float inv_h_f[LOVE_MAX_DIM];
+  double lo_d[LOVE_MAX_DIM];
+  double inv_h_d[LOVE_MAX_DIM];
+  double h_d[LOVE_MAX_DIM];
+  int m;
+};
+
+// grid coordinate s = (x - lo)/h in the arithmetic of T.  The same function
+// is used to bucket training points and to evaluate their weights, so the
+// cell of a point and its stencil always agree.
+__device__ __forceinline__ float grid_coord(float x, const GridDev& g, int e) {
+  return (x - g.lo_f[e]) * g.inv_h_f[e];
+}
+__device__ __forceinline__ double grid_coord(double x, const GridDev& g, int e) {
+  return (x - g.lo_d[e]) * g.inv_h_d[e];
+}
+
+// Keys kernel u(s) with a = -1/2:
+//   |s| <= 1 : 3/2 |s|^3 - 5/2 |s|^2 + 1
+//   1 < |s| < 2 : -1/2 |s|^3 + 5/2 |s|^2 - 4 |s| + 2
+template <typename T>
+__device__ __forceinline__ T keys_u(T s) {
+  T a = s < T(0) ? -s : s;
+  if (a <= T(1)) return (T(1.5) * a - T(2.5)) * a * a + T(1);
+  if (a < T(2)) return ((T(-0.5) * a + T(2.5)) * a - T(4)) * a + T(2);
+  return T(0);
+}
+// derivative u'(s) (odd)
+template <typename T>
+__device__ __forceinline__ T keys_du(T s) {
+  T a = s < T(0) ? -s : s;
+  T r;
+  if (a <= T(1)) r = (T(4.5) * a - T(5)) * a;
+  else if (a < T(2)) r = (T(-1.5) * a + T(5)) * a - T(4);
+  else r = T(0);
+  return s < T(0) ? -r : r;
+}
+
+// base index and the 4 weights of one coordinate: nodes i-1..i+2,
+// w_r = u(f + 1 - r), f = s - i.  Returns false if the stencil leaves [0, g).
+template <typename T>
+__device__ __forceinline__ bool keys_weights(T s, int g, int& base, T w[4]) {
+  if (!(s >= T(1)) || !(s < T(g - 2))) {  // also rejects NaN
+    base = 1;
+    w[0] = w[1] = w[2] = w[3] = T(0);
+    return false;
+  }
+  int i = (int)floor(s);
+  if (i > g - 3) i = g - 3;
+  T f = s - T(i);
+  base = i;
+  w[0] = keys_u(f + T(1));
+  w[1] = keys_u(f);
+  w[2] = keys_u(T(1) - f);
+  w[3] = keys_u(T(2) - f);
+  return true;
+}
+template <typename T>
+__device__ __forceinline__ void keys_dweights(T s, int base, T inv_h, T dw[4]) {
+  T f = s - T(base);
+  dw[0] = keys_du(f + T(1)) * inv_h;
+  dw[1] = keys_du(f) * inv_h;
+  dw[2] = keys_du(f - T(1)) * inv_h;
+  dw[3] = keys_du(f - T(2)) * inv_h;
+}
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic (value = hi + lo, |lo| <= ulp(hi)/2)
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float err = (a - (s - bb)) + (b - bb);
+  return {s, err};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  df t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, p.lo);
+  p.lo = fmaf(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_from_double(double x) {
+  float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// Dot2 accumulator: sum of exact products a*b (Ogita, Rump, Oishi 2005)
+struct DotAccF {
+  float s, c;
+  __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    float p = a * b;
+    float pe = fmaf(a, b, -p);
+    float t = s + p;
+    float z = t - s;
+    float err = (s - (t - z)) + (p - z);
+    s = t;
+    c += pe + err;
+  }
+  __device__ __forceinline__ void add(float p) {
+    float t = s + p;
+    float z = t - s;
+    c += (s - (t - z)) + (p - z);
+    s = t;
+  }
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    float t = s + s2;
+    float z = t - s;
+    float err = (s - (t - z)) + (s2 - z);
+    s = t;
+    c += c2 + err;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+struct DotAccD {
+  double s;
+  __device__ __forceinline__ void zero() { s = 0.0; }
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void add(double p) { s += p; }
+  __device__ __forceinline__ void merge(double s2, double c2) { s += s2 + c2; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <typename T> struct DotAcc;
+template <> struct DotAcc<float> { using type = DotAccF; };
+template <> struct DotAcc<double> { using type = DotAccD; };
+
+// warp-level merge of a DotAcc (deterministic butterfly)
+__device__ __forceinline__ void warp_merge(DotAccF& a, unsigned mask = 0xffffffffu, int width = 32) {
+  for (int o = width / 2; o > 0; o >>= 1) {
+    float s2 = __shfl_xor_sync(mask, a.s, o, width);
+    float c2 = __shfl_xor_sync(mask, a.c, o, width);
+    a.merge(s2, c2);
+  }
+}
+__device__ __forceinline__ void warp_merge(DotAccD& a, unsigned mask = 0xffffffffu, int width = 32) {
+  for (int o = width / 2; o > 0; o >>= 1) a.s += __shfl_xor_sync(mask, a.s, o, width);
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk async copy (TMA, 1-D form) helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of `bar`, giving up after ~1 s.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = global_timer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side handle definitions
+struct FftPlan {
+  int64_t g = 0;       // Toeplitz size along this mode
+  int64_t N = 0;       // circulant length (power of two, >= 2g - 1)
+  int N1 = 0, N2 = 0;  // four-step split (N1 = N, N2 = 1: single-CTA path)
+  void* lam_f = nullptr;  // N floats: spectrum / N (outputscale folded into mode 0)
+  void* lam_d = nullptr;  // N doubles
+  void* tw_f = nullptr;   // N float2: exp(-2 pi i j / N)
+  void* tw_d = nullptr;   // N double2
+  void* lamdl_f = nullptr;  // spectrum of dT/dl (for gradients), / N
+  void* lamdl_d = nullptr;
+};
+
+struct Allocator {
+  love_allocator a{};
+  bool user = false;
+  void* alloc(size_t bytes, cudaStream_t s) const;
+  void free(void* p, size_t bytes, cudaStream_t s) const;
+};
+
+struct GridHost {
+  int dim = 1;
+  int64_t g[LOVE_MAX_DIM] = {1, 1, 1};
+  int64_t stride[LOVE_MAX_DIM] = {1, 1, 1};
+  int64_t m = 1;
+  double lo[LOVE_MAX_DIM] = {0, 0, 0};
+  double h[LOVE_MAX_DIM] = {1, 1, 1};
+  double ls[LOVE_MAX_DIM] = {1, 1, 1};
+  double sf = 1.0;
+  double noise = 1.0;
+  double cloc[LOVE_MAX_DIM][4] = {};     // T_e[0..3] (first Toeplitz entries)
+  double cloc_dl[LOVE_MAX_DIM][4] = {};  // dT_e/dl_e [0..3]
+  GridDev dev() const;
+};
+
+struct love_ski {
+  GridHost grid;
+  love_dtype dtype = LOVE_F32;
+  int64_t n = 0, n_pad = 0;
+  Allocator alloc;
+  int device = 0;
+  void* xs = nullptr;          // n_pad x dim, sorted by cell (dtype)
+  void* ys = nullptr;          // n_pad (dtype) or null
+  int32_t* perm = nullptr;     // sorted position -> caller index (n)
+  int32_t* cell_start = nullptr;  // m + 1
+  FftPlan fft[LOVE_MAX_DIM];
+  DevStatus* status = nullptr;
+};
+
+struct love_cache {
+  GridHost grid;
+  love_dtype dtype = LOVE_F32, cache_dtype = LOVE_F32;
+  unsigned flags = 0;
+  int k_eff = 0, ld = 0;       // Rc: m x ld, columns [0,k) = Rt, column k = a
+  Allocator alloc;
+  void* Rc = nullptr;
+  int ks = 0, ld_s = 0;        // S: m x ld_s (dtype), columns [0, ks)
+  void* S = nullptr;
+  int ld_g = 0;                // backward tables: KdP_e: m x ld_g per dimension
+  void* KdP = nullptr;         // dim x m x ld_g (dtype): (dK/dl_e) P
+  void* B = nullptr;           // dim x k x k (float/double): P^T (dK/dl_e) P
+  void* Minv = nullptr;        // k x k: L^{-1} L^{-T}
+  double* alpha = nullptr;     // host copies
+  double* beta = nullptr;
+  void* P = nullptr;           // m x k_eff column-major (dtype), kept for export
+  int cg_iters = 0;
+  int sampler_fallback = 0;
+  float phase_ms[4] = {0, 0, 0, 0};
+  DevStatus* status = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the kernel .cu files)
+namespace love {
+
+// k_sort.cu
+love_status sort_training_points(love_ski* ski, const void* x_in, const void* y_in, cudaStream_t s);
+
+// k_fft.cu
+love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocator& al, cudaStream_t s);
+void fft_plan_destroy(FftPlan& p, const Allocator& al, cudaStream_t s);
+// out = K_UU v (all modes) for `ncol` columns (column stride ldc elements); work
+// must hold fft_work_elems() complex values.  deriv_dim >= 0 selects dK/dl_e.
+size_t fft_work_bytes(const GridHost& g, const FftPlan* plans, int ncol, bool dbl);
+template <typename T>
+love_status kuu_apply(const GridHost& g, const FftPlan* plans, const T* v, T* out, int ncol,
+                      int64_t ldc, void* work, int deriv_dim, cudaStream_t s);
+
+// k_lanczos.cu
+struct LanczosWork;
+template <typename T>
+love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, double* alpha_h,
+                        double* beta_h, int* k_eff, cudaStream_t s);
+template <typename T>
+love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaStream_t s);
+template <typename T>
+love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* out, int64_t ldo,
+                          cudaStream_t s);
+template <typename T>
+love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_iter, int* iters,
+                     cudaStream_t s);
+template <typename T>
+love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, const double* zmean,
+                        cudaStream_t s, T* keep_rt);
+// sampler Lanczos on M = K_UU - Rt Rt^T (FP64); Rt: m x k column-major (ldr)
+template <typename T>
+love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
+                            int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
+                            double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s);
+// k_sample.cu: S = Q' L' (or the eigen fallback), stored in the cache
+template <typename T>
+love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uint64_t seed, double tau,
+                          cudaStream_t s);
+
+template <typename T>
+love_status permute_in(const T* v, const int32_t* perm, int64_t n, int64_t n_pad, T* out, cudaStream_t s);
+template <typename T>
+love_status permute_out(const T* v, const int32_t* perm, int64_t n, T* out, cudaStream_t s);
+
+// k_predict.cu
+love_status predict_launch(love_cache* c, int64_t t, const void* x, void* mean, void* var,
+                           cudaStream_t s);
+love_status backward_launch(love_cache* c, int64_t t, const void* x, const void* gv, void* gx,
+                            double* gl, double* gn, cudaStream_t s);
+love_status backward_tables(love_cache* c, const FftPlan* plans, const void* P, int k,
+                            cudaStream_t s);
+
+// k_sample.cu
+love_status sample_launch(love_cache* c, int64_t t, const void* x, int s_count, const void* z,
+                          uint64_t seed, void* out, cudaStream_t s);
+
+// api helpers
+extern thread_local int g_last_cuda_error;
+// kernels launched by this library in this process (reported by love_launch_count)
+void count_launch();
+inline love_status cuda_check(cudaError_t e) {
+  if (e == cudaSuccess) return LOVE_OK;
+  g_last_cuda_error = (int)e;
+  return LOVE_ERR_CUDA;
+}
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+int num_sms();
+
+}  // namespace love
+
+#define LOVE_TRY(...)                      \
+  do {                                     \
+    love_status _st = (__VA_ARGS__);       \
+    if (_st != LOVE_OK) return _st;        \
+  } while (0)
+#define LOVE_CUDA(...) LOVE_TRY(love::cuda_check(__VA_ARGS__))
+#define LOVE_LAUNCH_CHECK() LOVE_CUDA(cudaGetLastError())
+#define LOVE_COUNT_LAUNCH() love::count_launch()

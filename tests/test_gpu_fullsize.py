@@ -1,0 +1,51 @@
+"""Full-size parity on the 1-D, n = 1e6, m = 1e4, k = 100, FP32 workload, in the
+launch configuration bench.py times: the GPU cache and all 1e6 predictive
+variances are checked by properties that hold at any size (finite, 0 <= var <= p,
+k_eff = k), and 2,000 sampled test points against the FP64 oracle LOVE run on
+the same data at the same k (|d var| / p <= 1e-6, the FP32 tolerance)."""
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def love():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1803_06058_gb300 as pkg
+    return pkg
+
+
+def test_c2_fullsize_variances(love):
+    from oracle import grid as og
+    from oracle import love as ol
+    from oracle import ski as os_
+    wl = workloads.C2
+    x = wl.x_train()
+    y = wl.y_train(x)
+    xs = wl.x_test()
+    ski = love.ski_build(torch.tensor(x, dtype=torch.float32, device="cuda"),
+                         torch.tensor(y, dtype=torch.float32, device="cuda"), wl.grid_size,
+                         wl.grid_lo, wl.grid_hi, wl.lengthscale, wl.outputscale, wl.noise)
+    cache = love.love_precompute(ski, k=wl.k, want_mean=True)
+    assert cache.info()["k_eff"] == wl.k
+    mean, var = love.love_predict_mean_var(cache, torch.tensor(xs, dtype=torch.float32, device="cuda"))
+    v = var.double().cpu().numpy()
+    grid = og.grid_from_workload(wl)
+    p = ol.prior(grid, xs)
+    assert np.all(np.isfinite(v)) and np.all(np.isfinite(mean.cpu().numpy()))
+    assert np.all(v >= 0) and np.all(v <= p * (1 + 1e-6))
+    assert cache.device_status()["domain_errors"] == 0
+    # oracle on the same data, same k, FP64
+    oc = ol.precompute(os_.SKI(grid, x, wl.noise, y), k=wl.k, want_mean=False)
+    idx = np.random.default_rng(0).choice(xs.shape[0], 2000, replace=False)
+    _, v_ref = ol.predict(oc, xs[idx])
+    err = np.abs(v[idx] - v_ref) / p[idx]
+    rel = np.abs(v[idx] - v_ref) / v_ref
+    print(f"C2 |dvar|/p max {err.max():.3e} median {np.median(err):.3e}; "
+          f"relative median {np.median(rel):.3e} max {rel.max():.3e}; var/p median {np.median(v_ref / p[idx]):.3e}")
+    assert err.max() <= 1e-6
