@@ -124,7 +124,7 @@ typedef struct {
   love_dtype cache_dtype;  /* F32, BF16 (with an F32 ski) or F64 (F64 ski)     */
   unsigned flags;
   double breakdown_tol;    /* stop when beta_j <= tol * max|alpha|; <=0: 1e-12 (F64) / 1e-8 (F32) */
-  double cg_tol;           /* relative residual of the FP64 CG; <=0: 1e-12 (F64 ski) / 1e-8 (F32 ski) */
+  double cg_tol;           /* relative residual of the FP64 CG; <=0: 1e-12 (F64 ski) / 1e-6 (F32 ski) */
   int cg_max_iter;         /* <=0: 4000                                        */
   int sampler_k;           /* Lanczos steps for S; <=0: k                      */
   uint64_t sampler_seed;   /* SplitMix64 seed of the Rademacher probe          */

@@ -289,8 +289,13 @@ constexpr int SMALL_MAX_N = 4096;
 
 // FFTs per CTA in the four-step kernels: at most `cap` complex values per CTA
 // and at most 16 transforms
-inline int four_logF(int L, int cap) {
-  int F = std::max(1, std::min(16, cap / L));
+// Transforms per CTA in the four-step kernels: at most `cap` complex values
+// per CTA and at most 16 transforms, but few enough that the launch has
+// >= 2 CTAs per SM (FP64 throughput per SM is low on this part, so the
+// transforms must be spread over the whole GPU).  `count` = transforms in the launch.
+inline int four_logF(int L, int cap, int64_t count) {
+  int64_t want = count / (2 * (int64_t)num_sms());
+  int F = (int)std::max<int64_t>(1, std::min<int64_t>({16, (int64_t)(cap / L), want}));
   int l = 0;
   while ((2 << l) <= F) ++l;
   return l;
@@ -303,11 +308,15 @@ love_status allow_smem(K kernel, size_t bytes) {
 }
 
 template <typename R>
-int small_logF(int N) {
-  // total complex elements per CTA: 4096 (FP32, 32 KB) / 2048 (FP64, 32 KB)
+int small_logF(int N, int64_t total) {
+  // total complex elements per CTA: 4096 (FP32, 32 KB) / 2048 (FP64, 32 KB),
+  // and at least 2 CTAs per SM when there are enough fibres
   int cap = sizeof(R) == 4 ? 4096 : 2048;
-  int F = std::max(1, cap / N);
-  return ilog2(F);
+  int64_t want = std::max<int64_t>(1, total / (2 * (int64_t)num_sms()));
+  int F = (int)std::max<int64_t>(1, std::min<int64_t>(cap / N, want));
+  int l = 0;
+  while ((2 << l) <= F) ++l;
+  return l;
 }
 
 // One mode of K_UU applied to FP32 or FP64 data; the transform itself always
@@ -324,7 +333,7 @@ love_status toeplitz_mode(const FftPlan& p, const IO* in, IO* out, ModeGeom mg, 
   const int N = (int)p.N;
   const int64_t total = mg.nfib * ncol;
   if (p.N2 == 1) {
-    int logF = small_logF<R>(N);
+    int logF = small_logF<R>(N, total);
     int F = 1 << logF;
     size_t sm = (size_t)N * F * sizeof(C);
     int threads = std::min(512, std::max(64, (N * F) / 4));
@@ -336,9 +345,9 @@ love_status toeplitz_mode(const FftPlan& p, const IO* in, IO* out, ModeGeom mg, 
   const int N1 = p.N1, N2 = p.N2;
   C* wk = (C*)work;
   const int cap = 2048;
-  int logFA = four_logF(N2, cap);
+  int logFA = four_logF(N2, cap, (int64_t)N1 * total);
   int FA = 1 << logFA;
-  int logFB = four_logF(N1, cap);
+  int logFB = four_logF(N1, cap, (int64_t)N2 * total);
   int FB = 1 << logFB;
   dim3 ga(N1 / FA, (unsigned)total), gb(N2 / FB, (unsigned)total);
   size_t sma = (size_t)N2 * FA * sizeof(C), smb = (size_t)N1 * FB * sizeof(C);
@@ -408,8 +417,8 @@ love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocato
       // four-step forward with a real input: A (reads real parts) then B (forward only)
       LOVE_COUNT_LAUNCH(); k_real_part<<<nb, 256, 0, s>>>(col, re, N);
       ModeGeom mg{N, 1, 1, N};
-      int logFA = four_logF(p.N2, 2048);
-      int logFB = four_logF(p.N1, 2048);
+      int logFA = four_logF(p.N2, 2048, p.N1);
+      int logFB = four_logF(p.N1, 2048, p.N2);
       dim3 ga(p.N1 >> logFA, 1), gb(p.N2 >> logFB, 1);
       LOVE_COUNT_LAUNCH(); k_four_a<double, double><<<ga, 256, (size_t)p.N2 * (1 << logFA) * sizeof(double2), s>>>(
           re, wk, mg, (int)N, p.N1, p.N2, ilog2(p.N2), logFA, (const double2*)p.tw_d);

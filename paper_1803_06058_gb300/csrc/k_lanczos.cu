@@ -26,6 +26,9 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "love_internal.cuh"
 
 namespace love {
@@ -194,8 +197,12 @@ __device__ __forceinline__ void node_index(int64_t node, const GridDev& g, int* 
 // the sum is accumulated in double-float (Dot2) and rounded once.
 template <typename T, int D, typename V = T>
 __global__ void k_scatter(GridDev g, const T* __restrict__ xs, const int* __restrict__ cell_start,
-                          const V* __restrict__ v, const double* __restrict__ scal, V scale, V* __restrict__ u) {
+                          const V* __restrict__ v, const double* __restrict__ scal, V scale, V* __restrict__ u,
+                          const V* __restrict__ v2, const double* __restrict__ beta2, const int* __restrict__ skip) {
+  // with v2: scatters v + beta2 v2 (the CG direction r + beta p, formed on the fly)
   using Acc = typename AccOf<V>::type;
+  if (skip && *skip) return;
+  const V b2 = v2 ? (V)(*beta2) : V(0);
   const int lane = threadIdx.x & 31;
   const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -209,7 +216,9 @@ __global__ void k_scatter(GridDev g, const T* __restrict__ xs, const int* __rest
     acc.zero();
     for (int f = lane; f < rg.total; f += 32) {
       int p = rg.point(f);
-      acc.add_prod((V)node_weight<T, D>(xs + (int64_t)p * D, g, nd), v[p]);
+      V val = v[p];
+      if (v2) val += b2 * v2[p];
+      acc.add_prod((V)node_weight<T, D>(xs + (int64_t)p * D, g, nd), val);
     }
     warp_merge(acc);
     if (lane == 0) u[node] = (V)(acc.value() * sc);
@@ -320,8 +329,20 @@ __device__ bool last_cta_reduce(const double2* __restrict__ partial, int stride,
 // Lanczos tile kernels
 enum { MODE_GATHER_DOT = 0, MODE_UPDATE_DOT = 1, MODE_UPDATE_NORM = 2, MODE_DOT = 3 };
 
+// 2-D tiled bulk tensor copy (TMA) of a box of Q into shared memory
+__device__ __forceinline__ void tma_load_2d(void* dst_smem, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
 template <typename T>
 struct TileArgs {
+  CUtensorMap qmap;   // Q as a 2-D tensor {rows = n_pad, cols = kcols}, box {TILE_R, bc}
+  int kpad;           // columns of the shared-memory tile (kcols rounded up to bc)
+  int bc;             // columns per TMA box
   GridDev g;
   int64_t n, n_pad;
   int j;
@@ -339,7 +360,7 @@ struct TileArgs {
 };
 
 template <typename T, int D, int MODE, int KPW>
-__global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(TileArgs<T> a) {
+__global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(const __grid_constant__ TileArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LanczosState* st = a.st;
@@ -347,8 +368,8 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(TileArgs<T> a) {
   const int j = a.j;
   const int ncols = j + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  T* Qs = reinterpret_cast<T*>(smem_raw);                              // [stages][kcols][R]
-  T* ys = Qs + (size_t)a.stages * a.kcols * TILE_R;                     // [R]
+  T* Qs = reinterpret_cast<T*>(smem_raw);                              // [stages][kpad][R]
+  T* ys = Qs + (size_t)a.stages * a.kpad * TILE_R;                      // [R]
   T* cf = ys + TILE_R;                                                 // [kcols]
   uint64_t* bar = reinterpret_cast<uint64_t*>(
       (reinterpret_cast<uintptr_t>(cf + a.kcols) + 15) & ~uintptr_t(15));  // [stages]
@@ -365,12 +386,13 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(TileArgs<T> a) {
     fence_mbar_init();
   }
   __syncthreads();
-  const uint32_t col_bytes = TILE_R * sizeof(T);
+  const int nbox = (ncols + a.bc - 1) / a.bc;
+  const uint32_t box_bytes = TILE_R * sizeof(T) * (uint32_t)a.bc;
   auto issue = [&](int64_t tile, int s) {
-    mbar_arrive_expect_tx(&bar[s], col_bytes * (uint32_t)ncols);
-    const T* src = a.Q + tile * TILE_R;
-    T* dst = Qs + (size_t)s * a.kcols * TILE_R;
-    for (int i = 0; i < ncols; ++i) bulk_g2s(dst + (size_t)i * TILE_R, src + (int64_t)i * a.ldq, col_bytes, &bar[s]);
+    mbar_arrive_expect_tx(&bar[s], box_bytes * (uint32_t)nbox);
+    T* dst = Qs + (size_t)s * a.kpad * TILE_R;
+    for (int b = 0; b < nbox; ++b)
+      tma_load_2d(dst + (size_t)b * a.bc * TILE_R, &a.qmap, (int)(tile * TILE_R), b * a.bc, &bar[s]);
   };
   if (tid == 0) {
     int64_t t0 = blockIdx.x;
@@ -396,7 +418,7 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(TileArgs<T> a) {
       st->done = 1;
       return;
     }
-    T* Qt = Qs + (size_t)s * a.kcols * TILE_R;
+    T* Qt = Qs + (size_t)s * a.kpad * TILE_R;
     const int64_t p = tile * TILE_R + tid;
     // ---- phase A: one row per thread
     if (MODE == MODE_GATHER_DOT || MODE == MODE_DOT) {
@@ -442,9 +464,14 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(TileArgs<T> a) {
       for (int s2 = 0; s2 < KPW; ++s2) {
         const int i = warp + NWARP * s2;
         if (i < ncols) {
+          // FP32 partial over this lane's 8 rows, folded into the double-float sum:
+          // the partials are ~sqrt(8/n) of the total, so their rounding stays
+          // far below the final rounding
           const T* qc = Qt + (size_t)i * TILE_R;
+          T part = T(0);
 #pragma unroll
-          for (int r = 0; r < TILE_R / 32; ++r) acc[s2].add_prod(qc[lane + 32 * r], yr[r]);
+          for (int r = 0; r < TILE_R / 32; ++r) part = fma(qc[lane + 32 * r], yr[r], part);
+          acc[s2].add(part);
         }
       }
     }
@@ -545,24 +572,28 @@ __global__ void k_state_init(LanczosState* st, int kmax, double tau) {
 // vectors and all reductions are FP64 whatever the coordinate type T (the
 // interpolation weights stay in T, as in the Lanczos MVMs): an FP32 CG stalls
 // on this ill-conditioned system (cond(K^) ~ 1e7 on the n = 1e6 workload).
-// Ap = W^T u + s^2 p ; pAp = p . Ap
+// p = r + beta p (the new direction, written back); Ap = W^T u + s^2 p; pAp = p . Ap
+// (u = K_UU W p was scattered from r + beta p on the fly)
 template <typename T, int D>
 __global__ void k_cg_gather_dot(GridDev g, const T* __restrict__ xs, int64_t n, int64_t n_pad,
-                                const double* __restrict__ u, double noise, const double* __restrict__ pv,
-                                double* __restrict__ Ap, double2* partial, LanczosState* st) {
+                                const double* __restrict__ u, double noise, const double* __restrict__ r,
+                                double* __restrict__ pv, double* __restrict__ Ap, double2* partial, LanczosState* st) {
   __shared__ DotAccD red[32];
   if (st->cg_done) return;
+  const double be = st->cg_beta;
   DotAccD a;
   a.zero();
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
-    double r = 0.0;
+    const double pn = r[p] + be * pv[p];
+    pv[p] = pn;
+    double q = 0.0;
     if (p < n) {
       Stencil<T, D> stc;
       stc.compute(xs + p * D, g);
-      r = stc.apply(u, g) + noise * pv[p];
+      q = stc.apply(u, g) + noise * pn;
     }
-    Ap[p] = r;
-    a.add_prod(pv[p], r);
+    Ap[p] = q;
+    a.add_prod(pn, q);
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
@@ -600,12 +631,6 @@ __global__ void k_cg_update(int64_t n_pad, double* __restrict__ x, double* __res
     }
   }
 }
-__global__ void k_cg_pupdate(int64_t n_pad, double* __restrict__ pv, const double* __restrict__ r, LanczosState* st) {
-  if (st->cg_done) return;
-  const double be = st->cg_beta;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x)
-    pv[p] = r[p] + be * pv[p];
-}
 template <typename T>
 __global__ void k_cg_init(int64_t n_pad, const T* __restrict__ b, double* __restrict__ x, double* __restrict__ r,
                           double* __restrict__ pv, double2* partial, LanczosState* st, double tol) {
@@ -616,7 +641,7 @@ __global__ void k_cg_init(int64_t n_pad, const T* __restrict__ b, double* __rest
     double v = (double)b[p];
     x[p] = 0.0;
     r[p] = v;
-    pv[p] = v;
+    pv[p] = 0.0;  // first direction r + 0 p = r
     a.add_prod(v, v);
   }
   block_merge(a, red);
@@ -627,8 +652,169 @@ __global__ void k_cg_init(int64_t n_pad, const T* __restrict__ b, double* __rest
     st->rr0 = st->norm2;
     st->tol2 = tol * tol * st->norm2;
     st->cg_iters = 0;
+    st->cg_beta = 0.0;
     st->cg_done = st->norm2 == 0.0 ? 1 : 0;
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same CG for the FP32 path in double-float: x, r, p, Ap are (hi, lo) float
+// pairs (~48-bit), every operation runs on the FP32 pipes (GB300's FP64 rate
+// is a small fraction of FP32), and K_UU still goes through the FP64 FFT on
+// the m-sized grid vectors.
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  p.lo = fmaf(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ void acc_add_dfprod(DotAccF& acc, df a, df b) {
+  acc.add_prod(a.hi, b.hi);
+  acc.c += fmaf(a.hi, b.lo, a.lo * b.hi);
+}
+
+// u[node] = sum over sorted points of w_p(node) (r_p + beta p_p), FP64 result
+template <int D>
+__global__ void k_scatter_df(GridDev g, const float* __restrict__ xs, const int* __restrict__ cell_start,
+                             const df* __restrict__ r, const df* __restrict__ pv, const LanczosState* st,
+                             double* __restrict__ u) {
+  if (st->cg_done) return;
+  const df be = df_from_double(st->cg_beta);
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t node = wg; node < g.m; node += nw) {
+    int nd[D];
+    node_index<D>(node, g, nd);
+    NodeRanges<D> rg;
+    rg.build(g, nd, cell_start, lane);
+    DotAccF acc;
+    acc.zero();
+    for (int f = lane; f < rg.total; f += 32) {
+      int p = rg.point(f);
+      df val = df_add(r[p], df_mul(be, pv[p]));
+      float w = node_weight<float, D>(xs + (int64_t)p * D, g, nd);
+      acc.add_prod(w, val.hi);
+      acc.c += w * val.lo;
+    }
+    warp_merge(acc);
+    if (lane == 0) u[node] = acc.value();
+  }
+}
+__global__ void k_double_to_df(int64_t m, const double* __restrict__ a, df* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = df_from_double(a[i]);
+}
+// p = r + beta p (written back); Ap = W^T u + s^2 p; pAp = p . Ap
+template <int D>
+__global__ void k_cgdf_gather_dot(GridDev g, const float* __restrict__ xs, int64_t n, int64_t n_pad,
+                                  const df* __restrict__ u, double noise, const df* __restrict__ r,
+                                  df* __restrict__ pv, df* __restrict__ Ap, double2* partial, LanczosState* st) {
+  __shared__ DotAccF red[32];
+  if (st->cg_done) return;
+  const df be = df_from_double(st->cg_beta);
+  const df nz = df_from_double(noise);
+  DotAccF a;
+  a.zero();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
+    const df pn = df_add(r[p], df_mul(be, pv[p]));
+    pv[p] = pn;
+    df q = {0.f, 0.f};
+    if (p < n) {
+      Stencil<float, D> stc;
+      stc.compute(xs + p * D, g);
+      // sum over the 4^D stencil nodes of w * u (df)
+      if (D == 1) {
+#pragma unroll
+        for (int r0 = 0; r0 < 4; ++r0) q = df_add(q, df_mul_f(u[stc.base[0] - 1 + r0], stc.w[0][r0]));
+      } else if (D == 2) {
+#pragma unroll
+        for (int r0 = 0; r0 < 4; ++r0)
+#pragma unroll
+          for (int r1 = 0; r1 < 4; ++r1) {
+            int64_t node = (int64_t)(stc.base[0] - 1 + r0) * g.stride[0] + (stc.base[1] - 1 + r1);
+            q = df_add(q, df_mul_f(u[node], stc.w[0][r0] * stc.w[1][r1]));
+          }
+      } else {
+#pragma unroll
+        for (int r0 = 0; r0 < 4; ++r0)
+#pragma unroll
+          for (int r1 = 0; r1 < 4; ++r1)
+#pragma unroll
+            for (int r2 = 0; r2 < 4; ++r2) {
+              int64_t node = (int64_t)(stc.base[0] - 1 + r0) * g.stride[0] +
+                             (int64_t)(stc.base[1] - 1 + r1) * g.stride[1] + (stc.base[2] - 1 + r2);
+              q = df_add(q, df_mul_f(u[node], stc.w[0][r0] * stc.w[1][r1] * stc.w[2][r2]));
+            }
+      }
+      q = df_add(q, df_mul(nz, pn));
+    }
+    Ap[p] = q;
+    acc_add_dfprod(a, pn, q);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->pap, &st->counter2);
+  if (last && threadIdx.x == 0) st->cg_alpha = st->rr / st->pap;
+}
+// x += a p ; r -= a Ap ; rr' = r.r
+__global__ void k_cgdf_update(int64_t n_pad, df* __restrict__ x, df* __restrict__ r, const df* __restrict__ pv,
+                              const df* __restrict__ Ap, double2* partial, LanczosState* st, int max_iter,
+                              DevStatus* status) {
+  __shared__ DotAccF red[32];
+  if (st->cg_done) return;
+  const df al = df_from_double(st->cg_alpha);
+  const df mal = df_neg(al);
+  DotAccF a;
+  a.zero();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
+    x[p] = df_add(x[p], df_mul(al, pv[p]));
+    df rv = df_add(r[p], df_mul(mal, Ap[p]));
+    r[p] = rv;
+    acc_add_dfprod(a, rv, rv);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->norm2, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    double rrn = st->norm2;
+    st->cg_beta = rrn / st->rr;
+    st->rr = rrn;
+    st->cg_iters += 1;
+    if (!isfinite(rrn)) {
+      dev_flag(status, LOVE_ERR_NAN);
+      st->cg_done = 1;
+    } else if (rrn <= st->tol2 || st->cg_iters >= max_iter) {
+      st->cg_done = 1;
+    }
+  }
+}
+__global__ void k_cgdf_init(int64_t n_pad, const float* __restrict__ b, df* __restrict__ x, df* __restrict__ r,
+                            df* __restrict__ pv, double2* partial, LanczosState* st, double tol) {
+  __shared__ DotAccF red[32];
+  DotAccF a;
+  a.zero();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += (int64_t)gridDim.x * blockDim.x) {
+    float v = b[p];
+    x[p] = {0.f, 0.f};
+    r[p] = {v, 0.f};
+    pv[p] = {0.f, 0.f};
+    a.add_prod(v, v);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->norm2, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    st->rr = st->norm2;
+    st->rr0 = st->norm2;
+    st->tol2 = tol * tol * st->norm2;
+    st->cg_iters = 0;
+    st->cg_beta = 0.0;
+    st->cg_done = st->norm2 == 0.0 ? 1 : 0;
+  }
+}
+__global__ void k_df_to_double(int64_t n, const df* __restrict__ a, double* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = df_to_double(a[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -730,20 +916,22 @@ struct DevBuf {
 };
 
 template <typename T, int D, typename V>
-love_status scatter_launch(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s) {
+love_status scatter_launch(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s,
+                           const V* v2, const double* beta2, const int* skip) {
   GridDev g = ski->grid.dev();
   int64_t warps = g.m;
   int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
-  LOVE_COUNT_LAUNCH(); k_scatter<T, D, V><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, v, scal, scale, u);
+  LOVE_COUNT_LAUNCH(); k_scatter<T, D, V><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, v, scal, scale, u, v2, beta2, skip);
   return cuda_check(cudaGetLastError());
 }
-// u = W v with coordinates of type T (the ski dtype) and values of type V
+// u = W v (or W (v + beta2 v2)) with coordinates of type T (the ski dtype) and values of type V
 template <typename T, typename V = T>
-love_status scatter_any(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s) {
+love_status scatter_any(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s,
+                        const V* v2 = nullptr, const double* beta2 = nullptr, const int* skip = nullptr) {
   switch (ski->grid.dim) {
-    case 1: return scatter_launch<T, 1, V>(ski, v, scal, scale, u, s);
-    case 2: return scatter_launch<T, 2, V>(ski, v, scal, scale, u, s);
-    default: return scatter_launch<T, 3, V>(ski, v, scal, scale, u, s);
+    case 1: return scatter_launch<T, 1, V>(ski, v, scal, scale, u, s, v2, beta2, skip);
+    case 2: return scatter_launch<T, 2, V>(ski, v, scal, scale, u, s, v2, beta2, skip);
+    default: return scatter_launch<T, 3, V>(ski, v, scal, scale, u, s, v2, beta2, skip);
   }
 }
 template <typename T>
@@ -783,6 +971,31 @@ love_status tile_any(int dim, TileArgs<T> a, int grid, size_t smem, cudaStream_t
     case 2: return tile_launch<T, 2, MODE>(a, grid, smem, s);
     default: return tile_launch<T, 3, MODE>(a, grid, smem, s);
   }
+}
+
+// Q as a 2-D tensor for TMA: rows (inner, n_pad) x columns (kcols), box
+// {TILE_R rows, bc columns}; columns past kcols read as zeros
+inline int box_cols(size_t elem) { return elem == 4 ? 8 : 4; }
+template <typename T>
+love_status make_qmap(T* Q, int64_t ldq, int kcols, int bc, CUtensorMap* out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !encode) {
+      encode = nullptr;
+      return e != cudaSuccess ? cuda_check(e) : LOVE_ERR_UNSUPPORTED;
+    }
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)ldq, (cuuint64_t)kcols};
+  cuuint64_t strides[1] = {(cuuint64_t)ldq * sizeof(T)};
+  cuuint32_t box[2] = {(cuuint32_t)TILE_R, (cuuint32_t)bc};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(out, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                      (void*)Q, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LOVE_OK : LOVE_ERR_CUDA;
 }
 
 inline size_t tile_smem(int stages, int kcols, size_t elem) {
@@ -826,9 +1039,11 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
   const GridHost& gh = ski->grid;
   const int dim = gh.dim;
   if (k < 1 || k > LOVE_MAX_K) return LOVE_ERR_ARG;
-  const int stages = tile_stages(k, sizeof(T));
+  const int bc = box_cols(sizeof(T));
+  const int kpad = (k + bc - 1) / bc * bc;
+  const int stages = tile_stages(kpad, sizeof(T));
   if (stages == 0) return LOVE_ERR_UNSUPPORTED;
-  const size_t smem = tile_smem(stages, k, sizeof(T));
+  const size_t smem = tile_smem(stages, kpad, sizeof(T));
   const int64_t ntiles = ski->n_pad / TILE_R;
   const int grid = (int)std::min<int64_t>(ntiles, num_sms());
   DevBuf stb(ski->alloc, s), part(ski->alloc, s), u(ski->alloc, s), y(ski->alloc, s), fw(ski->alloc, s);
@@ -858,6 +1073,9 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
   ta.n = ski->n;
   ta.n_pad = ski->n_pad;
   ta.kcols = k;
+  ta.kpad = kpad;
+  ta.bc = bc;
+  LOVE_TRY(make_qmap<T>(Q, ldq, k, bc, &ta.qmap));
   ta.stages = stages;
   ta.xs = (const T*)ski->xs;
   ta.u = u2;
@@ -898,8 +1116,63 @@ love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* o
   return cuda_check(cudaGetLastError());
 }
 
+// FP32 ski: double-float CG; the solution is returned as FP64 in x
+love_status cg_solve_df(love_ski* ski, const float* b, double* x, double tol, int max_iter, int* iters,
+                        cudaStream_t s) {
+  const GridHost& gh = ski->grid;
+  const GridDev g = gh.dev();
+  const int64_t np = ski->n_pad;
+  DevBuf stb(ski->alloc, s), part(ski->alloc, s), xb(ski->alloc, s), r(ski->alloc, s), pv(ski->alloc, s),
+      Ap(ski->alloc, s), u(ski->alloc, s), udf(ski->alloc, s), fw(ski->alloc, s);
+  size_t fwb = fft_work_bytes(gh, ski->fft, 1, true);
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * 1024) || !xb.get(sizeof(df) * np) ||
+      !r.get(sizeof(df) * np) || !pv.get(sizeof(df) * np) || !Ap.get(sizeof(df) * np) ||
+      !u.get(sizeof(double) * gh.m * 2) || !udf.get(sizeof(df) * gh.m) || !fw.get(std::max<size_t>(fwb, 16)))
+    return LOVE_ERR_OOM;
+  LanczosState* st = stb.as<LanczosState>();
+  double* u1 = u.as<double>();
+  double* u2 = u1 + gh.m;
+  const int blocks = std::min(1024, ceil_div(np, 256));
+  const int sblocks = (int)std::min<int64_t>((g.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, 1, 0.0);
+  LOVE_COUNT_LAUNCH(); k_cgdf_init<<<blocks, 256, 0, s>>>(np, b, xb.as<df>(), r.as<df>(), pv.as<df>(), part.as<double2>(), st, tol);
+  LOVE_LAUNCH_CHECK();
+  int it = 0;
+  const int chunk = 32;
+  while (it < max_iter) {
+    for (int c = 0; c < chunk && it < max_iter; ++c, ++it) {
+      switch (g.dim) {
+        case 1: LOVE_COUNT_LAUNCH(); k_scatter_df<1><<<sblocks, 256, 0, s>>>(g, (const float*)ski->xs, ski->cell_start, r.as<df>(), pv.as<df>(), st, u1); break;
+        case 2: LOVE_COUNT_LAUNCH(); k_scatter_df<2><<<sblocks, 256, 0, s>>>(g, (const float*)ski->xs, ski->cell_start, r.as<df>(), pv.as<df>(), st, u1); break;
+        default: LOVE_COUNT_LAUNCH(); k_scatter_df<3><<<sblocks, 256, 0, s>>>(g, (const float*)ski->xs, ski->cell_start, r.as<df>(), pv.as<df>(), st, u1);
+      }
+      LOVE_TRY(kuu_apply<double>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
+      LOVE_COUNT_LAUNCH(); k_double_to_df<<<ceil_div(gh.m, 256), 256, 0, s>>>(gh.m, u2, udf.as<df>());
+      switch (g.dim) {
+        case 1: LOVE_COUNT_LAUNCH(); k_cgdf_gather_dot<1><<<blocks, 256, 0, s>>>(g, (const float*)ski->xs, ski->n, np, udf.as<df>(), gh.noise, r.as<df>(), pv.as<df>(), Ap.as<df>(), part.as<double2>(), st); break;
+        case 2: LOVE_COUNT_LAUNCH(); k_cgdf_gather_dot<2><<<blocks, 256, 0, s>>>(g, (const float*)ski->xs, ski->n, np, udf.as<df>(), gh.noise, r.as<df>(), pv.as<df>(), Ap.as<df>(), part.as<double2>(), st); break;
+        default: LOVE_COUNT_LAUNCH(); k_cgdf_gather_dot<3><<<blocks, 256, 0, s>>>(g, (const float*)ski->xs, ski->n, np, udf.as<df>(), gh.noise, r.as<df>(), pv.as<df>(), Ap.as<df>(), part.as<double2>(), st);
+      }
+      LOVE_COUNT_LAUNCH(); k_cgdf_update<<<blocks, 256, 0, s>>>(np, xb.as<df>(), r.as<df>(), pv.as<df>(), Ap.as<df>(), part.as<double2>(), st, max_iter, ski->status);
+      LOVE_LAUNCH_CHECK();
+    }
+    int done = 0;
+    LOVE_CUDA(cudaMemcpyAsync(&done, &st->cg_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    if (done) break;
+  }
+  LOVE_COUNT_LAUNCH(); k_df_to_double<<<ceil_div(np, 256), 256, 0, s>>>(np, xb.as<df>(), x);
+  LOVE_LAUNCH_CHECK();
+  int n_it = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&n_it, &st->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  if (iters) *iters = n_it;
+  return LOVE_OK;
+}
+
 template <typename T>
 love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_iter, int* iters, cudaStream_t s) {
+  if (sizeof(T) == 4) return cg_solve_df(ski, (const float*)b, x, tol, max_iter, iters, s);
   const GridHost& gh = ski->grid;
   const GridDev g = gh.dev();
   const int64_t np = ski->n_pad;
@@ -921,16 +1194,16 @@ love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_i
   const int chunk = 32;
   while (it < max_iter) {
     for (int c = 0; c < chunk && it < max_iter; ++c, ++it) {
-      LOVE_TRY(scatter_any<T, double>(ski, pv.as<double>(), nullptr, 1.0, u1, s));
+      LOVE_TRY(scatter_any<T, double>(ski, r.as<double>(), nullptr, 1.0, u1, s, pv.as<double>(), &st->cg_beta,
+                                      &st->cg_done));
       LOVE_TRY(kuu_apply<double>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
       switch (g.dim) {
-        case 1: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 1><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, pv.as<double>(), Ap.as<double>(), part.as<double2>(), st); break;
-        case 2: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 2><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, pv.as<double>(), Ap.as<double>(), part.as<double2>(), st); break;
-        default: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 3><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, pv.as<double>(), Ap.as<double>(), part.as<double2>(), st);
+        case 1: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 1><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, r.as<double>(), pv.as<double>(), Ap.as<double>(), part.as<double2>(), st); break;
+        case 2: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 2><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, r.as<double>(), pv.as<double>(), Ap.as<double>(), part.as<double2>(), st); break;
+        default: LOVE_COUNT_LAUNCH(); k_cg_gather_dot<T, 3><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->n, np, u2, gh.noise, r.as<double>(), pv.as<double>(), Ap.as<double>(), part.as<double2>(), st);
       }
       LOVE_COUNT_LAUNCH(); k_cg_update<<<blocks, 256, 0, s>>>(np, x, r.as<double>(), pv.as<double>(), Ap.as<double>(), part.as<double2>(), st, max_iter,
                                            ski->status);
-      LOVE_COUNT_LAUNCH(); k_cg_pupdate<<<blocks, 256, 0, s>>>(np, pv.as<double>(), r.as<double>(), st);
       LOVE_LAUNCH_CHECK();
     }
     int done = 0;
@@ -1109,9 +1382,11 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
                             double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s) {
   const int64_t m = gh.m, m_pad = ldq;
   if (ks < 1 || ks > LOVE_MAX_K || m_pad % TILE_R) return LOVE_ERR_ARG;
-  const int stages = tile_stages(ks, sizeof(double));
+  const int bc = box_cols(sizeof(double));
+  const int kpad = (ks + bc - 1) / bc * bc;
+  const int stages = tile_stages(kpad, sizeof(double));
   if (stages == 0) return LOVE_ERR_UNSUPPORTED;
-  const size_t smem = tile_smem(stages, ks, sizeof(double));
+  const size_t smem = tile_smem(stages, kpad, sizeof(double));
   const int grid = (int)std::min<int64_t>(m_pad / TILE_R, num_sms());
   DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s);
   size_t fwb = fft_work_bytes(gh, fft, 1, true);
@@ -1128,6 +1403,9 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
   ta.n = m;
   ta.n_pad = m_pad;
   ta.kcols = ks;
+  ta.kpad = kpad;
+  ta.bc = bc;
+  LOVE_TRY(make_qmap<double>(Q, ldq, ks, bc, &ta.qmap));
   ta.stages = stages;
   ta.Q = Q;
   ta.ldq = ldq;

@@ -74,30 +74,40 @@ __global__ void k_tri_dense(const double* alpha, const double* beta, int n, doub
   A[idx] = v;
 }
 
-// Cyclic Jacobi eigenvalue iteration on a symmetric n x n matrix, one CTA.
-// Each rotation J (c, s at (p, q)) with tan(phi) = t the smaller root of
-// t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq), annihilates a_pq:
-// A <- J^T A J, V <- V J.  Sweeps until the off-diagonal mass is below
-// 1e-28 of the total (or max_sweeps).  A, V in shared memory when they fit.
-__global__ void k_jacobi_eig(double* __restrict__ Ag, double* __restrict__ Vg, int n, int max_sweeps, int use_smem) {
+// Parallel Jacobi eigenvalue iteration on a symmetric n x n matrix, one CTA,
+// in FP32 shared memory (Golub & Van Loan, Sec. 8.5: cyclic Jacobi with the
+// round-robin ordering, so each step applies n/2 rotations on disjoint index
+// pairs at once).  Each rotation (c, s at (p, q)) uses tan(phi) = t, the smaller
+// root of t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq), which
+// annihilates a_pq: A <- J^T A J, V <- V J.  Sweeps stop when the off-diagonal
+// mass is below 1e-13 of the total.  FP32 is enough here: eigenvalues below
+// ~1e-7 of the largest are clamped to zero anyway, and FP64 on this part runs
+// at a small fraction of FP32.  Writes lam (n) and V (n x n, eigenvectors in
+// columns) as doubles.  Shared memory: 2 np^2 + 2 np floats, np = n rounded up to even.
+__global__ void k_jacobi_par(const double* __restrict__ Ain, int n, int max_sweeps, double* __restrict__ lam,
+                             double* __restrict__ Vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* A = use_smem ? reinterpret_cast<double*>(smem_raw) : Ag;
-  double* V = use_smem ? A + (size_t)n * n : Vg;
-  __shared__ double rot[2];
-  __shared__ int skip;
-  __shared__ double red[2][32];
+  const int np = n + (n & 1);
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* V = A + (size_t)np * np;
+  float* cs = V + (size_t)np * np;   // [np/2][2]
+  int* pr = reinterpret_cast<int*>(cs + np);  // [np/2][2]
+  __shared__ float red[2][32];
+  __shared__ int stop;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int64_t i = tid; i < (int64_t)n * n; i += nt) {
-    if (use_smem) A[i] = Ag[i];
-    V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  for (int i = tid; i < np * np; i += nt) {
+    int r = i / np, c = i % np;
+    A[i] = (r < n && c < n) ? (float)Ain[(int64_t)r * n + c] : 0.f;
+    V[i] = (r == c) ? 1.f : 0.f;
   }
   __syncthreads();
+  const int half = np / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int64_t i = tid; i < (int64_t)n * n; i += nt) {
-      double a = A[i];
-      tot += a * a;
-      if (i / n != i % n) off += a * a;
+    float off = 0.f, tot = 0.f;
+    for (int i = tid; i < np * np; i += nt) {
+      float v = A[i];
+      tot += v * v;
+      if (i / np != i % np) off += v * v;
     }
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_xor_sync(0xffffffffu, off, o);
@@ -109,65 +119,72 @@ __global__ void k_jacobi_eig(double* __restrict__ Ag, double* __restrict__ Vg, i
     }
     __syncthreads();
     if (tid == 0) {
-      double a = 0.0, b = 0.0;
+      float a = 0.f, b = 0.f;
       for (int w = 0; w < (nt + 31) / 32; ++w) {
         a += red[0][w];
         b += red[1][w];
       }
-      skip = (a <= 1e-28 * b) ? 1 : 0;
+      stop = (a <= 1e-13f * b) ? 1 : 0;
     }
     __syncthreads();
-    if (skip) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        if (tid == 0) {
-          double apq = A[(int64_t)p * n + q];
-          double app = A[(int64_t)p * n + p], aqq = A[(int64_t)q * n + q];
-          if (fabs(apq) <= 1e-300 || fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq))) {
-            skip = 1;
-          } else {
-            skip = 0;
-            double theta = (aqq - app) / (2.0 * apq);
-            double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            double c = 1.0 / sqrt(t * t + 1.0);
-            rot[0] = c;
-            rot[1] = t * c;
-          }
+    if (stop) break;
+    for (int step = 0; step < np - 1; ++step) {
+      // round robin: position 0 holds index 0, positions 1..np-1 rotate by `step`
+      for (int i = tid; i < half; i += nt) {
+        int ja = i, jb = np - 1 - i;
+        int a = ja == 0 ? 0 : 1 + (ja - 1 + step) % (np - 1);
+        int b = 1 + (jb - 1 + step) % (np - 1);
+        int p = a < b ? a : b, q = a < b ? b : a;
+        float apq = A[p * np + q], app = A[p * np + p], aqq = A[q * np + q];
+        float c = 1.f, sn = 0.f;
+        if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-8f * sqrtf(fabsf(app * aqq))) {
+          float theta = (aqq - app) / (2.f * apq);
+          float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+          c = rsqrtf(t * t + 1.f);
+          sn = t * c;
         }
-        __syncthreads();
-        if (skip) continue;
-        const double c = rot[0], s = rot[1];
-        for (int i = tid; i < n; i += nt) {  // A <- A J (columns p, q)
-          double aip = A[(int64_t)i * n + p], aiq = A[(int64_t)i * n + q];
-          A[(int64_t)i * n + p] = c * aip - s * aiq;
-          A[(int64_t)i * n + q] = s * aip + c * aiq;
-        }
-        __syncthreads();
-        for (int j = tid; j < n; j += nt) {  // A <- J^T A (rows p, q); V <- V J
-          double apj = A[(int64_t)p * n + j], aqj = A[(int64_t)q * n + j];
-          A[(int64_t)p * n + j] = c * apj - s * aqj;
-          A[(int64_t)q * n + j] = s * apj + c * aqj;
-          double vjp = V[(int64_t)j * n + p], vjq = V[(int64_t)j * n + q];
-          V[(int64_t)j * n + p] = c * vjp - s * vjq;
-          V[(int64_t)j * n + q] = s * vjp + c * vjq;
-        }
-        __syncthreads();
+        pr[2 * i] = p;
+        pr[2 * i + 1] = q;
+        cs[2 * i] = c;
+        cs[2 * i + 1] = sn;
       }
-  }
-  if (use_smem)
-    for (int64_t i = tid; i < (int64_t)n * n; i += nt) {
-      Ag[i] = A[i];
-      Vg[i] = V[i];
+      __syncthreads();
+      for (int w = tid; w < half * np; w += nt) {  // columns p, q of A and V
+        int i = w / np, r = w % np;
+        int p = pr[2 * i], q = pr[2 * i + 1];
+        float c = cs[2 * i], sn = cs[2 * i + 1];
+        if (sn == 0.f) continue;
+        float arp = A[r * np + p], arq = A[r * np + q];
+        A[r * np + p] = c * arp - sn * arq;
+        A[r * np + q] = sn * arp + c * arq;
+        float vrp = V[r * np + p], vrq = V[r * np + q];
+        V[r * np + p] = c * vrp - sn * vrq;
+        V[r * np + q] = sn * vrp + c * vrq;
+      }
+      __syncthreads();
+      for (int w = tid; w < half * np; w += nt) {  // rows p, q of A
+        int i = w / np, cidx = w % np;
+        int p = pr[2 * i], q = pr[2 * i + 1];
+        float c = cs[2 * i], sn = cs[2 * i + 1];
+        if (sn == 0.f) continue;
+        float apc = A[p * np + cidx], aqc = A[q * np + cidx];
+        A[p * np + cidx] = c * apc - sn * aqc;
+        A[q * np + cidx] = sn * apc + c * aqc;
+      }
+      __syncthreads();
     }
+  }
+  for (int i = tid; i < n; i += nt) lam[i] = (double)A[i * np + i];
+  for (int i = tid; i < n * n; i += nt) Vout[i] = (double)V[(i / n) * np + (i % n)];
 }
 
-// B[j, c] = V[j, c] sqrt(max(lam_c, 0)),  lam_c = A[c, c]
-__global__ void k_scale_eigvec(const double* A, const double* V, int n, double* B) {
+// B[j, c] = V[j, c] sqrt(max(lam_c, 0))
+__global__ void k_scale_eig(const double* lam, const double* V, int n, double* B) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n) return;
   int c = (int)(idx % n);
-  double lam = A[(int64_t)c * n + c];
-  B[idx] = V[idx] * sqrt(lam > 0.0 ? lam : 0.0);
+  double l = lam[c];
+  B[idx] = V[idx] * sqrt(l > 0.0 ? l : 0.0);
 }
 
 // S[r, c] = sum_j Q'[r, j] B[j, c]  (arithmetic in T; S row-major ld_s)
@@ -432,11 +449,16 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
     const int64_t nn = (int64_t)keff * keff;
     if (!A.get(sizeof(double) * nn) || !V.get(sizeof(double) * nn) || !B.get(sizeof(double) * nn)) return LOVE_ERR_OOM;
     LOVE_COUNT_LAUNCH(); k_tri_dense<<<ceil_div(nn, 256), 256, 0, s>>>(ad, bd, keff, A.as<double>());
-    size_t sm = sizeof(double) * 2 * nn;
-    int use_smem = sm <= 200 * 1024 ? 1 : 0;
-    if (use_smem) LOVE_TRY(allow_smem_s(k_jacobi_eig, sm));
-    LOVE_COUNT_LAUNCH(); k_jacobi_eig<<<1, 256, use_smem ? sm : 0, s>>>(A.as<double>(), V.as<double>(), keff, 30, use_smem);
-    LOVE_COUNT_LAUNCH(); k_scale_eigvec<<<ceil_div(nn, 256), 256, 0, s>>>(A.as<double>(), V.as<double>(), keff, B.as<double>());
+    const int np = keff + (keff & 1);
+    size_t sm = sizeof(float) * (2 * (size_t)np * np + 2 * np);
+    if (sm > 220 * 1024) return LOVE_ERR_UNSUPPORTED;   // k' > ~165
+    LOVE_TRY(allow_smem_s(k_jacobi_par, sm));
+    double* lam = B.as<double>();                        // first n entries of B as scratch
+    Buf L(al, s);
+    if (!L.get(sizeof(double) * keff)) return LOVE_ERR_OOM;
+    LOVE_COUNT_LAUNCH(); k_jacobi_par<<<1, 1024, sm, s>>>(A.as<double>(), keff, 40, L.as<double>(), V.as<double>());
+    LOVE_COUNT_LAUNCH(); k_scale_eig<<<ceil_div(nn, 256), 256, 0, s>>>(L.as<double>(), V.as<double>(), keff, B.as<double>());
+    (void)lam;
     size_t smb = sizeof(T) * nn;
     LOVE_TRY(allow_smem_s(k_root_from_eig<T>, smb));
     LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<double>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);

@@ -408,7 +408,7 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   if (flags & LOVE_WANT_MEAN) {
     z = (double*)al.alloc(zb, s);
     if (!z) rc = LOVE_ERR_OOM;
-    double tol = o->cg_tol > 0 ? o->cg_tol : (sizeof(T) == 8 ? 1e-12 : 1e-8);
+    double tol = o->cg_tol > 0 ? o->cg_tol : (sizeof(T) == 8 ? 1e-12 : 1e-6);
     int maxit = o->cg_max_iter > 0 ? o->cg_max_iter : 4000;
     if (rc == LOVE_OK) rc = cg_solve<T>(ski, (const T*)ski->ys, z, tol, maxit, &c->cg_iters, s);
   }
