@@ -235,6 +235,25 @@ typedef struct {
 LOVE_API love_status love_get_device_status(love_cache_t cache, int reset, love_device_status_t* st,
                                    love_stream_t stream);
 
+/* ski_mvm_kuu_noalloc -- out = K_UU v, like ski_mvm_kuu, for callers that may
+ * not allocate device memory.  The paper has no counterpart; it exists for
+ * callers such as code being captured into a CUDA graph whose replays must
+ * not allocate, real-time loops that forbid allocator calls, or host
+ * frameworks that have already reserved all device memory.  ski_mvm_kuu takes
+ * its FFT work area from the handle's allocator; this entry point instead uses
+ * a fixed file-scope device array of 4 MiB, present on every GPU that loads the
+ * library until the process exits, and calls no allocator (no cudaMalloc,
+ * cudaFree or allocating library routine).  It accepts grids whose longest
+ * mode with more than 2048 points needs at most 4 MiB of FFT work (a 1-D grid
+ * of up to 131,072 points); larger grids return LOVE_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (every call overwrites the part it reads, so nothing needs
+ * clearing); calls whose work overlaps on the GPU, on different streams or
+ * from different threads, race on it.  v, out: m device arrays (dtype). */
+LOVE_API love_status ski_mvm_kuu_noalloc(love_ski_t ski, const void* v, void* out, love_stream_t stream);
+
 /* Host-side helpers. */
 LOVE_API const char* love_status_string(love_status s);
 LOVE_API int love_last_cuda_error(void);            /* last cudaError_t seen by the library */

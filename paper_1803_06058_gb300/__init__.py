@@ -168,6 +168,17 @@ def ski_mvm_kuu(ski: Ski, v: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
+def ski_mvm_kuu_noalloc(ski: Ski, v: torch.Tensor, out: Optional[torch.Tensor] = None,
+                        stream=None) -> torch.Tensor:
+    """K_UU v through the entry point that allocates nothing (its FFT scratch is
+    a fixed device array inside the library); pass `out` to keep this call
+    allocation-free on the Python side as well."""
+    if out is None:
+        out = torch.empty_like(v)
+    check("ski_mvm_kuu_noalloc", lib().ski_mvm_kuu_noalloc(ski.handle, _ptr(v), _ptr(out), _stream(stream)))
+    return out
+
+
 def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool = True,
                     want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
                     breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,

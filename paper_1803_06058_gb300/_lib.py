@@ -60,6 +60,7 @@ SIGNATURES = {
     "ski_destroy": (C.c_int, [VP]),
     "ski_mvm": (C.c_int, [VP, VP, VP, VP]),
     "ski_mvm_kuu": (C.c_int, [VP, VP, VP, VP]),
+    "ski_mvm_kuu_noalloc": (C.c_int, [VP, VP, VP, VP]),
     "love_precompute": (C.c_int, [VP, C.POINTER(love_precompute_opts), VP, C.POINTER(VP),
                                   C.POINTER(C.c_int)]),
     "love_cache_destroy": (C.c_int, [VP]),
