@@ -53,11 +53,18 @@ def exact_pushthrough(ski: SKI, x: np.ndarray, prior_mode: str = "ski", C=None):
     var = prior(grid, x, prior_mode) - np.einsum("tm,tm->t", WC, Ws.T.toarray())
     mean = None
     if ski.y is not None:
-        Kd = grid.dense_kuu()
-        G = (ski.W @ ski.W.T).toarray()
-        a = Kd @ np.linalg.solve(G @ Kd + ski.noise * np.eye(grid.m), ski.W @ ski.y)
-        mean = Ws.T @ a
+        mean = Ws.T @ mean_weights_pushthrough(ski)
     return mean, var
+
+
+def mean_weights_pushthrough(ski: SKI) -> np.ndarray:
+    """a = K_UU W (W^T K_UU W + s^2 I)^{-1} y = K_UU (G K_UU + s^2 I)^{-1} W y,
+    G = W W^T (push-through identity), by one dense m x m solve; the predictive
+    mean is w*^T a (eq. pred_mean_ski)."""
+    grid = ski.grid
+    Kd = grid.dense_kuu()
+    G = (ski.W @ ski.W.T).tocsr()
+    return Kd @ np.linalg.solve(np.asarray(G @ Kd) + ski.noise * np.eye(grid.m), ski.W @ ski.y)
 
 
 def exact_cg(ski: SKI, x: np.ndarray, prior_mode: str = "ski", tol: float = 1e-12,

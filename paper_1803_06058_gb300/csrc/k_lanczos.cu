@@ -8,18 +8,20 @@
 // (in exact arithmetic c holds the three-term coefficients alpha_j, beta_{j-1}
 // and zeros, so pass 1 is the Lanczos recurrence plus reorthogonalisation).
 //
-// One step is five launches, all stream-ordered with every scalar kept on the
+// One step is six launches, all stream-ordered with every scalar kept on the
 // device (graph-capturable, no host synchronisation):
-//   scatter    u = W q_j            warp per grid node, gather over the
+//   scatter     u = W q_j           warp per grid node, gather over the
 //                                   cell-sorted training points (deterministic)
-//   K_UU       u = K_UU u           FFT Toeplitz / Kronecker (k_fft.cu)
-//   gather+dot y = W^T u + s^2 q_j; c = Q_j^T y
-//   update+dot y -= Q_j c;  c' = Q_j^T y
+//   K_UU        u = K_UU u          FFT Toeplitz / Kronecker (k_fft.cu)
+//   gather      y = W^T u + s^2 q_j (q_j normalised in place)
+//   dot         c = Q_j^T y
+//   update+dot  y -= Q_j c;  c' = Q_j^T y
 //   update+norm y -= Q_j c';  beta = |y|;  q_{j+1} = y (scaled on next use)
-// The last three stream row tiles of Q_j (256 rows x (j+1) columns) through a
-// double-buffered shared-memory ring filled by bulk async copies (TMA, 1-D
-// form, one copy per column segment, completion on an mbarrier); Q_j is read
-// three times per step.  Dot products accumulate in double-float per thread
+// The last three stream row tiles of [Q_j | y] (128 rows x (j + 1) columns
+// of Q, plus y) through a 2- to 8-stage shared-memory ring filled by TMA
+// (2-D tensor boxes of Q, a 1-D bulk copy of y; completion on an mbarrier),
+// two CTAs per SM, so Q_j is read three times per step and nothing else of
+// the step touches HBM.  Dot products accumulate in double-float per thread
 // and per CTA, and CTA partials are combined by the last CTA to finish, in a
 // fixed order (deterministic, no floating-point atomics).
 #include <algorithm>
@@ -55,8 +57,9 @@ struct LanczosState {
 
 namespace {
 
-constexpr int TILE_R = 256;     // rows per tile = threads per CTA
-constexpr int NWARP = TILE_R / 32;
+constexpr int TILE_R = 128;     // rows per reorthogonalisation tile
+constexpr int TILE_T = 256;     // threads per tile CTA (two per row in the update)
+constexpr int NWARP = TILE_T / 32;
 
 template <typename T> struct AccOf;
 template <> struct AccOf<float> { using type = DotAccF; };
@@ -327,7 +330,7 @@ __device__ bool last_cta_reduce(const double2* __restrict__ partial, int stride,
 
 // ---------------------------------------------------------------------------
 // Lanczos tile kernels
-enum { MODE_GATHER_DOT = 0, MODE_UPDATE_DOT = 1, MODE_UPDATE_NORM = 2, MODE_DOT = 3 };
+enum { MODE_DOT = 0, MODE_UPDATE_DOT = 1, MODE_UPDATE_NORM = 2 };
 
 // 2-D tiled bulk tensor copy (TMA) of a box of Q into shared memory
 __device__ __forceinline__ void tma_load_2d(void* dst_smem, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
@@ -340,27 +343,34 @@ __device__ __forceinline__ void tma_load_2d(void* dst_smem, const CUtensorMap* m
 
 template <typename T>
 struct TileArgs {
-  CUtensorMap qmap;   // Q as a 2-D tensor {rows = n_pad, cols = kcols}, box {TILE_R, bc}
-  int kpad;           // columns of the shared-memory tile (kcols rounded up to bc)
+  CUtensorMap qmap;   // Q as a 2-D tensor {rows = ldq, cols = kcols}, box {TILE_R, bc}
   int bc;             // columns per TMA box
-  GridDev g;
-  int64_t n, n_pad;
+  int kpad;           // Q columns of one ring stage: j + 1 rounded up to bc
+  int stages;         // ring depth
+  int64_t n_pad;      // rows (a multiple of TILE_R)
   int j;
-  int kcols;          // allocated columns of Q (and of the smem tile)
-  int stages;
-  const T* xs;
-  const T* u;         // GATHER: K_UU W q_j
-  T noise;
+  int kcols;          // allocated columns of Q
   T* Q;
   int64_t ldq;
-  T* y;
+  T* y;               // [n_pad], 16-byte aligned
   double2* partial;   // [gridDim][kcols + 1]
   LanczosState* st;
   DevStatus* status;
 };
 
-template <typename T, int D, int MODE, int KPW>
-__global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(const __grid_constant__ TileArgs<T> a) {
+// One reorthogonalisation sweep over the row tiles of [Q_j | y].  Per tile,
+// TILE_R rows of columns 0..j of Q (2-D TMA boxes of bc columns) and of y (a
+// 1-D bulk copy) land in one stage of a shared-memory ring, so every step
+// below reads shared memory only:
+//   DOT          c = Q_j^T y                       (alpha_j = c_j)
+//   UPDATE_DOT   y -= Q_j c;   c' = Q_j^T y
+//   UPDATE_NORM  y -= Q_j c';  beta_j = |y|;  q_{j+1} = y (scaled on next use)
+// The update gives each row two threads (the two halves of the columns, two
+// independent FMA chains each); the dots give warp w the columns w, w + 8, ...
+// with each lane owning TILE_R / 32 rows.  Two CTAs share an SM so that one
+// computes while the other waits for its ring.
+template <typename T, int MODE, int KPW>
+__global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constant__ TileArgs<T> a) {
   using Acc = typename AccOf<T>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LanczosState* st = a.st;
@@ -368,18 +378,18 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(const __grid_constan
   const int j = a.j;
   const int ncols = j + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  T* Qs = reinterpret_cast<T*>(smem_raw);                              // [stages][kpad][R]
-  T* ys = Qs + (size_t)a.stages * a.kpad * TILE_R;                      // [R]
-  T* cf = ys + TILE_R;                                                 // [kcols]
+  const size_t stage_elems = (size_t)(a.kpad + 1) * TILE_R;               // Q columns, then y
+  T* ring = reinterpret_cast<T*>(smem_raw);                                // [stages][kpad + 1][TILE_R]
+  T* cf = ring + (size_t)a.stages * stage_elems;                           // [kcols]
+  T* hp = cf + a.kcols;                                                     // [TILE_R]
   uint64_t* bar = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(cf + a.kcols) + 15) & ~uintptr_t(15));  // [stages]
+      (reinterpret_cast<uintptr_t>(hp + TILE_R) + 15) & ~uintptr_t(15));    // [stages]
   __shared__ Acc red[NWARP];
 
   if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
     const double* c = MODE == MODE_UPDATE_DOT ? st->coef : st->coef2;
-    for (int i = tid; i < ncols; i += TILE_R) cf[i] = (T)c[i];
+    for (int i = tid; i < ncols; i += TILE_T) cf[i] = (T)c[i];
   }
-  const T scal_j = (MODE == MODE_GATHER_DOT) ? (T)st->scal[j] : T(1);
   const int64_t ntiles = a.n_pad / TILE_R;
   if (tid == 0) {
     for (int s = 0; s < a.stages; ++s) mbar_init(&bar[s], 1);
@@ -387,17 +397,18 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(const __grid_constan
   }
   __syncthreads();
   const int nbox = (ncols + a.bc - 1) / a.bc;
-  const uint32_t box_bytes = TILE_R * sizeof(T) * (uint32_t)a.bc;
+  const uint32_t col_bytes = TILE_R * (uint32_t)sizeof(T);
+  const uint32_t tx = col_bytes * (uint32_t)(nbox * a.bc + 1);
   auto issue = [&](int64_t tile, int s) {
-    mbar_arrive_expect_tx(&bar[s], box_bytes * (uint32_t)nbox);
-    T* dst = Qs + (size_t)s * a.kpad * TILE_R;
+    mbar_arrive_expect_tx(&bar[s], tx);
+    T* dst = ring + (size_t)s * stage_elems;
     for (int b = 0; b < nbox; ++b)
       tma_load_2d(dst + (size_t)b * a.bc * TILE_R, &a.qmap, (int)(tile * TILE_R), b * a.bc, &bar[s]);
+    bulk_g2s(dst + (size_t)a.kpad * TILE_R, a.y + tile * TILE_R, col_bytes, &bar[s]);
   };
   if (tid == 0) {
-    int64_t t0 = blockIdx.x;
     for (int s = 0; s < a.stages; ++s) {
-      int64_t t = t0 + (int64_t)s * gridDim.x;
+      int64_t t = blockIdx.x + (int64_t)s * gridDim.x;
       if (t < ntiles) issue(t, s);
     }
   }
@@ -418,55 +429,52 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(const __grid_constan
       st->done = 1;
       return;
     }
-    T* Qt = Qs + (size_t)s * a.kpad * TILE_R;
-    const int64_t p = tile * TILE_R + tid;
-    // ---- phase A: one row per thread
-    if (MODE == MODE_GATHER_DOT || MODE == MODE_DOT) {
-      T q = Qt[(size_t)j * TILE_R + tid] * scal_j;
-      T yv;
-      if (MODE == MODE_GATHER_DOT) {
-        yv = T(0);
-        if (p < a.n) {
-          Stencil<T, D> stc;
-          stc.compute(a.xs + p * D, a.g);
-          yv = stc.apply(a.u, a.g) + a.noise * q;
-        } else {
-          q = T(0);
-        }
-        a.y[p] = yv;
-        a.Q[(int64_t)j * a.ldq + p] = q;
-      } else {
-        yv = a.y[p];
+    T* Qt = ring + (size_t)s * stage_elems;
+    T* yt = Qt + (size_t)a.kpad * TILE_R;
+    // ---- update: y -= Q_j c, two threads per row
+    if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
+      const int r = tid & (TILE_R - 1), h = tid / TILE_R;
+      const int mid = (ncols + 1) >> 1;
+      const int i1 = h ? ncols : mid;
+      T s0 = T(0), s1 = T(0);
+      int i = h ? mid : 0;
+      for (; i + 1 < i1; i += 2) {
+        s0 = fma(Qt[(size_t)i * TILE_R + r], cf[i], s0);
+        s1 = fma(Qt[(size_t)(i + 1) * TILE_R + r], cf[i + 1], s1);
       }
-      Qt[(size_t)j * TILE_R + tid] = q;
-      ys[tid] = yv;
-    } else {
-      T yv = a.y[p];
-      for (int i = ncols - 1; i >= 0; --i) yv = fma(-Qt[(size_t)i * TILE_R + tid], cf[i], yv);
-      if (MODE == MODE_UPDATE_DOT) {
-        a.y[p] = yv;
-        ys[tid] = yv;
-      } else {
-        if (j + 1 < a.kcols)
-          a.Q[(int64_t)(j + 1) * a.ldq + p] = yv;
-        else
+      if (i < i1) s0 = fma(Qt[(size_t)i * TILE_R + r], cf[i], s0);
+      const T part = s0 + s1;
+      if (h) hp[r] = part;
+      __syncthreads();
+      if (!h) {
+        const T yv = yt[r] - (part + hp[r]);
+        const int64_t p = tile * TILE_R + r;
+        if (MODE == MODE_UPDATE_DOT) {
           a.y[p] = yv;
-        nacc.add_prod(yv, yv);
+          yt[r] = yv;
+          fence_proxy_async();
+        } else {
+          if (j + 1 < a.kcols)
+            a.Q[(int64_t)(j + 1) * a.ldq + p] = yv;
+          else
+            a.y[p] = yv;
+          nacc.add_prod(yv, yv);
+        }
       }
+      if (MODE == MODE_UPDATE_DOT) __syncthreads();
     }
-    __syncthreads();
-    // ---- phase B: column dots, warp w owns columns w, w + 8, ...
+    // ---- column dots: warp w owns columns w, w + NWARP, ...
     if (MODE != MODE_UPDATE_NORM) {
       T yr[TILE_R / 32];
 #pragma unroll
-      for (int r = 0; r < TILE_R / 32; ++r) yr[r] = ys[lane + 32 * r];
+      for (int r = 0; r < TILE_R / 32; ++r) yr[r] = yt[lane + 32 * r];
 #pragma unroll
       for (int s2 = 0; s2 < KPW; ++s2) {
         const int i = warp + NWARP * s2;
         if (i < ncols) {
-          // FP32 partial over this lane's 8 rows, folded into the double-float sum:
-          // the partials are ~sqrt(8/n) of the total, so their rounding stays
-          // far below the final rounding
+          // a partial over this lane's TILE_R / 32 rows, folded into the
+          // double-float sum: the partials are ~sqrt(TILE_R / 32 / n) of the
+          // total, so their rounding stays far below the final rounding
           const T* qc = Qt + (size_t)i * TILE_R;
           T part = T(0);
 #pragma unroll
@@ -501,7 +509,7 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(const __grid_constan
   double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
   bool last = last_cta_reduce<Acc>(a.partial, pstride, MODE == MODE_UPDATE_NORM ? 1 : ncols, result, &st->counter);
   if (!last || tid != 0) return;
-  if (MODE == MODE_GATHER_DOT || MODE == MODE_DOT) {
+  if (MODE == MODE_DOT) {
     double al = st->coef[j];
     st->alpha[j] = al;
     if (!isfinite(al)) {
@@ -526,6 +534,28 @@ __global__ void __launch_bounds__(TILE_R, 1) k_lanczos_tile(const __grid_constan
     } else {
       st->scal[j + 1] = 1.0 / b;
     }
+  }
+}
+
+// Lanczos product y = W^T u + s^2 q_j (u = K_UU W q_j), normalising q_j in
+// place: Q[:, j] *= scal_j.  Rows past n are zero.  No-op after breakdown.
+template <typename T, int D>
+__global__ void k_lanczos_gather(GridDev g, const T* __restrict__ xs, int64_t n, int64_t n_pad,
+                                 const T* __restrict__ u, T noise, T* __restrict__ qj, T* __restrict__ y,
+                                 const LanczosState* st, int j) {
+  if (st->done) return;
+  const T scal = (T)st->scal[j];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pad;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    T q = T(0), r = T(0);
+    if (p < n) {
+      q = qj[p] * scal;
+      Stencil<T, D> stc;
+      stc.compute(xs + p * D, g);
+      r = stc.apply(u, g) + noise * q;
+    }
+    qj[p] = q;
+    y[p] = r;
   }
 }
 
@@ -946,16 +976,41 @@ love_status gather_any(love_ski* ski, const T* u, T a, T b, const T* v, T* out, 
   return cuda_check(cudaGetLastError());
 }
 
-template <typename T, int D, int MODE>
-love_status tile_launch(TileArgs<T> a, int grid, size_t smem, cudaStream_t s) {
-  const int kc = a.kcols;
-#define LOVE_TILE_CASE(KPW)                                                         \
-  if (kc <= NWARP * KPW) {                                                          \
-    auto kern = k_lanczos_tile<T, D, MODE, KPW>;                                    \
-    LOVE_TRY(allow_smem(kern, smem));                                               \
-    LOVE_COUNT_LAUNCH(); kern<<<grid, TILE_R, smem, s>>>(a);                                             \
-    return cuda_check(cudaGetLastError());                                          \
+// Ring geometry per launch: a stage holds the j + 1 live columns (rounded up
+// to the box width) plus the y column; as many stages (2..8) as fit a budget
+// that leaves room for two CTAs per SM.
+inline size_t tile_smem(int stages, int kpad, int kcols, size_t elem) {
+  return (size_t)stages * (kpad + 1) * TILE_R * elem + (size_t)kcols * elem + TILE_R * elem + 16 + 8 * stages;
+}
+inline int tile_stages(int kpad, int kcols, size_t elem) {
+  const size_t budget = 104 * 1024, cap = 225 * 1024;
+  int st = (int)std::min<size_t>(8, budget / ((size_t)(kpad + 1) * TILE_R * elem));
+  st = std::max(st, 2);
+  while (st > 1 && tile_smem(st, kpad, kcols, elem) > cap) --st;
+  return tile_smem(st, kpad, kcols, elem) <= cap ? st : 0;
+}
+constexpr int TILE_CTAS_PER_SM = 2;
+
+template <typename T, int MODE>
+love_status tile_run(TileArgs<T> a, cudaStream_t s) {
+  const int ncols = a.j + 1;
+  a.kpad = (ncols + a.bc - 1) / a.bc * a.bc;
+  a.stages = tile_stages(a.kpad, a.kcols, sizeof(T));
+  if (a.stages == 0) return LOVE_ERR_UNSUPPORTED;
+  const size_t smem = tile_smem(a.stages, a.kpad, a.kcols, sizeof(T));
+  const int64_t ntiles = a.n_pad / TILE_R;
+#define LOVE_TILE_CASE(KPW)                                                                    \
+  if (ncols <= NWARP * KPW) {                                                                  \
+    auto kern = k_lanczos_tile<T, MODE, KPW>;                                                  \
+    LOVE_TRY(allow_smem(kern, smem));                                                          \
+    int per_sm = 0;                                                                            \
+    LOVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE_T, smem));     \
+    per_sm = std::min(std::max(per_sm, 1), TILE_CTAS_PER_SM);                                  \
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms());              \
+    LOVE_COUNT_LAUNCH(); kern<<<grid, TILE_T, smem, s>>>(a);                                   \
+    return cuda_check(cudaGetLastError());                                                     \
   }
+  LOVE_TILE_CASE(1)
   LOVE_TILE_CASE(2)
   LOVE_TILE_CASE(4)
   LOVE_TILE_CASE(8)
@@ -964,13 +1019,20 @@ love_status tile_launch(TileArgs<T> a, int grid, size_t smem, cudaStream_t s) {
 #undef LOVE_TILE_CASE
   return LOVE_ERR_UNSUPPORTED;
 }
-template <typename T, int MODE>
-love_status tile_any(int dim, TileArgs<T> a, int grid, size_t smem, cudaStream_t s) {
-  switch (dim) {
-    case 1: return tile_launch<T, 1, MODE>(a, grid, smem, s);
-    case 2: return tile_launch<T, 2, MODE>(a, grid, smem, s);
-    default: return tile_launch<T, 3, MODE>(a, grid, smem, s);
+
+template <typename T>
+love_status lanczos_gather_any(love_ski* ski, const T* u, T* qj, T* y, const LanczosState* st, int j,
+                               cudaStream_t s) {
+  const GridDev g = ski->grid.dev();
+  const int blocks = (int)std::min<int64_t>(ceil_div(ski->n_pad, 256), (int64_t)num_sms() * 8);
+  const T* xs = (const T*)ski->xs;
+  const T nz = (T)ski->grid.noise;
+  switch (g.dim) {
+    case 1: LOVE_COUNT_LAUNCH(); k_lanczos_gather<T, 1><<<blocks, 256, 0, s>>>(g, xs, ski->n, ski->n_pad, u, nz, qj, y, st, j); break;
+    case 2: LOVE_COUNT_LAUNCH(); k_lanczos_gather<T, 2><<<blocks, 256, 0, s>>>(g, xs, ski->n, ski->n_pad, u, nz, qj, y, st, j); break;
+    default: LOVE_COUNT_LAUNCH(); k_lanczos_gather<T, 3><<<blocks, 256, 0, s>>>(g, xs, ski->n, ski->n_pad, u, nz, qj, y, st, j);
   }
+  return cuda_check(cudaGetLastError());
 }
 
 // Q as a 2-D tensor for TMA: rows (inner, n_pad) x columns (kcols), box
@@ -996,16 +1058,6 @@ love_status make_qmap(T* Q, int64_t ldq, int kcols, int bc, CUtensorMap* out) {
                       (void*)Q, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? LOVE_OK : LOVE_ERR_CUDA;
-}
-
-inline size_t tile_smem(int stages, int kcols, size_t elem) {
-  return (size_t)stages * kcols * TILE_R * elem + TILE_R * elem + kcols * elem + 64;
-}
-inline int tile_stages(int kcols, size_t elem) {
-  const size_t cap = 225 * 1024;
-  if (tile_smem(2, kcols, elem) <= cap) return 2;
-  if (tile_smem(1, kcols, elem) <= cap) return 1;
-  return 0;
 }
 
 }  // namespace
@@ -1040,15 +1092,11 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
   const int dim = gh.dim;
   if (k < 1 || k > LOVE_MAX_K) return LOVE_ERR_ARG;
   const int bc = box_cols(sizeof(T));
-  const int kpad = (k + bc - 1) / bc * bc;
-  const int stages = tile_stages(kpad, sizeof(T));
-  if (stages == 0) return LOVE_ERR_UNSUPPORTED;
-  const size_t smem = tile_smem(stages, kpad, sizeof(T));
-  const int64_t ntiles = ski->n_pad / TILE_R;
-  const int grid = (int)std::min<int64_t>(ntiles, num_sms());
+  if (ski->n_pad % TILE_R) return LOVE_ERR_ARG;
+  const int max_grid = std::max(TILE_CTAS_PER_SM * num_sms(), 1024);
   DevBuf stb(ski->alloc, s), part(ski->alloc, s), u(ski->alloc, s), y(ski->alloc, s), fw(ski->alloc, s);
   size_t fwb = fft_work_bytes(gh, ski->fft, 1, sizeof(T) == 8);
-  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)std::max(grid, 1024) * (k + 1)) ||
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)max_grid * (k + 1)) ||
       !u.get(sizeof(T) * gh.m * 2) || !y.get(sizeof(T) * ski->n_pad) || !fw.get(std::max<size_t>(fwb, 16)))
     return LOVE_ERR_OOM;
   LanczosState* st = stb.as<LanczosState>();
@@ -1069,17 +1117,10 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
     LOVE_LAUNCH_CHECK();
   }
   TileArgs<T> ta{};
-  ta.g = g;
-  ta.n = ski->n;
   ta.n_pad = ski->n_pad;
   ta.kcols = k;
-  ta.kpad = kpad;
   ta.bc = bc;
   LOVE_TRY(make_qmap<T>(Q, ldq, k, bc, &ta.qmap));
-  ta.stages = stages;
-  ta.xs = (const T*)ski->xs;
-  ta.u = u2;
-  ta.noise = (T)gh.noise;
   ta.Q = Q;
   ta.ldq = ldq;
   ta.y = y.as<T>();
@@ -1090,10 +1131,12 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
     // u = W q_j (q_j stored unnormalised, scaled by scal[j])
     LOVE_TRY(scatter_any<T>(ski, Q + (int64_t)j * ldq, st->scal + j, T(1), u1, s));
     LOVE_TRY(kuu_apply<T>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
+    // y = W^T u + s^2 q_j (q_j normalised in place)
+    LOVE_TRY(lanczos_gather_any<T>(ski, u2, Q + (int64_t)j * ldq, y.as<T>(), st, j, s));
     ta.j = j;
-    LOVE_TRY(tile_any<T, MODE_GATHER_DOT>(dim, ta, grid, smem, s));
-    LOVE_TRY(tile_any<T, MODE_UPDATE_DOT>(dim, ta, grid, smem, s));
-    LOVE_TRY(tile_any<T, MODE_UPDATE_NORM>(dim, ta, grid, smem, s));
+    LOVE_TRY(tile_run<T, MODE_DOT>(ta, s));
+    LOVE_TRY(tile_run<T, MODE_UPDATE_DOT>(ta, s));
+    LOVE_TRY(tile_run<T, MODE_UPDATE_NORM>(ta, s));
   }
   int keff = 0;
   LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1218,10 +1261,294 @@ love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_i
   return LOVE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Mean cache on the grid (d <= 2).  W is m x n here (u = W v scatters points
+// to nodes) and G = W W^T is the m x m Gram matrix of the interpolation
+// weights, banded with 7^d diagonals.  The push-through identity
+//   W (W^T K W + s^2 I)^-1 = (G K + s^2 I)^-1 W
+// turns the mean weights a = K_UU W K^^-1 y (Sec. 3, predictive mean) into
+//   a = K z,   A z = W y,   A = G K + s^2 I,
+// an m-sized system.  A is self-adjoint and positive definite in the inner
+// product <u, v>_K = u^T K v (K A = K G K + s^2 K), with eigenvalues >= s^2,
+// so CG runs in that inner product: s = K r and q = K p are carried by
+// recurrence, leaving one K product (FFT) per iteration and no n-sized work.
+// Stopping rule: CG minimises E = <e, A e>_K over the Krylov space (e the
+// error of z), and |W^T (a_i - a)|^2 = e^T K G K e <= E <= <r, r>_K / s^2, so
+//   rho = r^T K r <= tol^2 s^2 |y|^2
+// bounds the error of the fitted values at the training points by tol |y|,
+// the same guarantee the rule |y - K^ x| <= tol |y| gives CG on K^ x = y
+// (there W^T (a_i - a) = (K^ - s^2 I) K^^-1 r, a contraction of r).
+namespace {
+
+template <int D> struct Band { static constexpr int B = D == 1 ? 7 : 49; };
+
+// G[o][node] = sum_p w_p(node) w_p(node + off(o)), offsets -3..3 per dimension;
+// warp per node over the cell-sorted points, FP64 accumulation
+template <typename T, int D>
+__global__ void k_gram_band(GridDev g, const T* __restrict__ xs, const int* __restrict__ cell_start,
+                            double* __restrict__ G) {
+  constexpr int B = Band<D>::B;
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t node = wg; node < g.m; node += nw) {
+    int nd[D];
+    node_index<D>(node, g, nd);
+    NodeRanges<D> rg;
+    rg.build(g, nd, cell_start, lane);
+    double acc[B];
+#pragma unroll
+    for (int o = 0; o < B; ++o) acc[o] = 0.0;
+    for (int f = lane; f < rg.total; f += 32) {
+      const int p = rg.point(f);
+      T wd[D][7];
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        T sc = grid_coord(xs[(int64_t)p * D + e], g, e);
+        int i = (int)floor(sc);
+        if (i > g.g[e] - 3) i = g.g[e] - 3;
+        T fr = sc - T(i);
+#pragma unroll
+        for (int o = 0; o < 7; ++o) wd[e][o] = keys_u(fr + T(1) - T(nd[e] + o - 3 - (i - 1)));
+      }
+      if constexpr (D == 1) {
+#pragma unroll
+        for (int o = 0; o < 7; ++o) acc[o] = fma((double)wd[0][3], (double)wd[0][o], acc[o]);
+      } else {
+        const T wu = wd[0][3] * wd[D - 1][3];
+#pragma unroll
+        for (int o0 = 0; o0 < 7; ++o0)
+#pragma unroll
+          for (int o1 = 0; o1 < 7; ++o1)
+            acc[o0 * 7 + o1] = fma((double)wu, (double)(wd[0][o0] * wd[D - 1][o1]), acc[o0 * 7 + o1]);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < B; ++o) {
+      double v = acc[o];
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+      if (lane == 0) G[(int64_t)o * g.m + node] = v;
+    }
+  }
+}
+
+// t = G q + s^2 p (= A p);  pi = q . t (= <p, A p>_K)
+template <int D>
+__global__ void k_mcg_band(GridDev g, const double* __restrict__ G, const double* __restrict__ q,
+                           const double* __restrict__ pv, double noise, double* __restrict__ t, double2* partial,
+                           LanczosState* st, int max_iter, DevStatus* status) {
+  constexpr int B = Band<D>::B;
+  __shared__ DotAccD red[32];
+  if (st->cg_done) return;
+  DotAccD api;
+  api.zero();
+  for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < g.m;
+       node += (int64_t)gridDim.x * blockDim.x) {
+    int nd[D];
+    node_index<D>(node, g, nd);
+    double gq = 0.0;
+#pragma unroll
+    for (int o = 0; o < B; ++o) {
+      const int o0 = D == 1 ? o : o / 7, o1 = o % 7;
+      const int a0 = nd[0] + o0 - 3;
+      const int a1 = D == 1 ? 0 : nd[D - 1] + o1 - 3;
+      bool in = a0 >= 0 && a0 < g.g[0];
+      if (D == 2) in = in && a1 >= 0 && a1 < g.g[1];
+      if (in) {
+        const int64_t nb = D == 1 ? a0 : (int64_t)a0 * g.stride[0] + a1;
+        gq = fma(G[(int64_t)o * g.m + node], q[nb], gq);
+      }
+    }
+    const double tv = gq + noise * pv[node];
+    t[node] = tv;
+    api.add_prod(q[node], tv);
+  }
+  block_merge(api, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, api);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->pap, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    const double pi = st->pap;
+    if (!isfinite(pi)) {
+      dev_flag(status, LOVE_ERR_NAN);
+      st->cg_done = 1;
+    } else if (pi <= 0.0 || st->cg_iters >= max_iter) {
+      st->cg_done = 1;
+    } else {
+      st->cg_alpha = st->rr / pi;
+    }
+  }
+}
+
+// w += a q;  r -= a t;  s -= a K t;  rho' = r . s
+__global__ void k_mcg_update(int64_t m, double* __restrict__ w, double* __restrict__ r, double* __restrict__ sv,
+                             const double* __restrict__ q, const double* __restrict__ t,
+                             const double* __restrict__ Kt, double2* partial, LanczosState* st, DevStatus* status) {
+  __shared__ DotAccD red[32];
+  if (st->cg_done) return;
+  const double al = st->cg_alpha;
+  DotAccD a;
+  a.zero();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    w[i] = fma(al, q[i], w[i]);
+    const double rv = fma(-al, t[i], r[i]);
+    const double sn = fma(-al, Kt[i], sv[i]);
+    r[i] = rv;
+    sv[i] = sn;
+    a.add_prod(rv, sn);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    const double rho = st->norm2;
+    st->cg_beta = rho / st->rr;
+    st->rr = rho;
+    st->cg_iters += 1;
+    if (!isfinite(rho)) {
+      dev_flag(status, LOVE_ERR_NAN);
+      st->cg_done = 1;
+    } else if (rho <= st->tol2) {
+      st->cg_done = 1;
+    }
+  }
+}
+
+// p = r + beta p;  q = s + beta q
+__global__ void k_mcg_dir(int64_t m, double* __restrict__ pv, double* __restrict__ q, const double* __restrict__ r,
+                          const double* __restrict__ sv, const LanczosState* st) {
+  if (st->cg_done) return;
+  const double be = st->cg_beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    pv[i] = fma(be, pv[i], r[i]);
+    q[i] = fma(be, q[i], sv[i]);
+  }
+}
+
+// |y|^2 -> the stopping threshold tol^2 s^2 |y|^2
+template <typename T>
+__global__ void k_mcg_ynorm(int64_t n, const T* __restrict__ y, double* __restrict__ yd, double tol, double noise,
+                            double2* partial, LanczosState* st) {
+  __shared__ DotAccD red[32];
+  DotAccD a;
+  a.zero();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)y[i];
+    if (yd) yd[i] = v;
+    a.add_prod(v, v);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    st->rr0 = st->norm2;
+    st->tol2 = tol * tol * st->norm2 * noise;
+    st->cg_iters = 0;
+    st->cg_beta = 0.0;
+    st->cg_done = st->norm2 == 0.0 ? 1 : 0;
+  }
+}
+
+// r = b, p = b, q = s = K b, w = 0;  rho = r . s
+__global__ void k_mcg_start(int64_t m, const double* __restrict__ b, const double* __restrict__ Kb,
+                            double* __restrict__ r, double* __restrict__ pv, double* __restrict__ sv,
+                            double* __restrict__ q, double* __restrict__ w, double2* partial, LanczosState* st) {
+  __shared__ DotAccD red[32];
+  DotAccD a;
+  a.zero();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    r[i] = b[i];
+    pv[i] = b[i];
+    sv[i] = Kb[i];
+    q[i] = Kb[i];
+    w[i] = 0.0;
+    a.add_prod(b[i], Kb[i]);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  if (last && threadIdx.x == 0) {
+    st->rr = st->norm2;
+    if (!(st->norm2 > st->tol2)) st->cg_done = 1;
+  }
+}
+
+}  // namespace
+
+bool mean_grid_cg_supported(const love_ski* ski) { return ski->grid.dim <= 2; }
+
+template <typename T>
+love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s) {
+  const GridHost& gh = ski->grid;
+  const GridDev g = gh.dev();
+  const int dim = gh.dim;
+  if (dim > 2) return LOVE_ERR_UNSUPPORTED;
+  const int64_t m = gh.m, n = ski->n;
+  const int B = dim == 1 ? 7 : 49;
+  DevBuf stb(ski->alloc, s), part(ski->alloc, s), Gb(ski->alloc, s), vec(ski->alloc, s), yb(ski->alloc, s),
+      fw(ski->alloc, s);
+  size_t fwb = fft_work_bytes(gh, ski->fft, 1, true);
+  const bool conv = sizeof(T) != sizeof(double);
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * 2048) || !Gb.get(sizeof(double) * B * m) ||
+      !vec.get(sizeof(double) * 7 * m) || (conv && !yb.get(sizeof(double) * std::max<int64_t>(n, 1))) ||
+      !fw.get(std::max<size_t>(fwb, 16)))
+    return LOVE_ERR_OOM;
+  LanczosState* st = stb.as<LanczosState>();
+  double* v = vec.as<double>();
+  double *b = v, *r = v + m, *pv = v + 2 * m, *sv = v + 3 * m, *q = v + 4 * m, *t = v + 5 * m, *Kt = v + 6 * m;
+  double* w = a;  // a = K z accumulates in place
+  double2* pp = part.as<double2>();
+  const int sblocks = (int)std::min<int64_t>((m * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  const int mblocks = (int)std::min<int64_t>(ceil_div(m, 256), 1024);
+  const int nblocks = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(n, 1), 256), 1024);
+  LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, 1, 0.0);
+  // G = W W^T
+  if (dim == 1) {
+    LOVE_COUNT_LAUNCH(); k_gram_band<T, 1><<<sblocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Gb.as<double>());
+  } else {
+    LOVE_COUNT_LAUNCH(); k_gram_band<T, 2><<<sblocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Gb.as<double>());
+  }
+  // b = W y (FP64), |y|^2
+  const double* yd = conv ? yb.as<double>() : (const double*)ski->ys;
+  LOVE_COUNT_LAUNCH();
+  k_mcg_ynorm<T><<<nblocks, 256, 0, s>>>(n, (const T*)ski->ys, conv ? yb.as<double>() : nullptr, tol, gh.noise, pp, st);
+  LOVE_LAUNCH_CHECK();
+  LOVE_TRY(scatter_any<T, double>(ski, yd, nullptr, 1.0, b, s));
+  LOVE_TRY(kuu_apply<double>(gh, ski->fft, b, Kt, 1, m, fw.p, -1, s));
+  LOVE_COUNT_LAUNCH(); k_mcg_start<<<mblocks, 256, 0, s>>>(m, b, Kt, r, pv, sv, q, w, pp, st);
+  LOVE_LAUNCH_CHECK();
+  int it = 0;
+  const int chunk = 64;
+  while (it <= max_iter) {
+    for (int c = 0; c < chunk && it <= max_iter; ++c, ++it) {
+      if (dim == 1) {
+        LOVE_COUNT_LAUNCH(); k_mcg_band<1><<<mblocks, 256, 0, s>>>(g, Gb.as<double>(), q, pv, gh.noise, t, pp, st, max_iter, ski->status);
+      } else {
+        LOVE_COUNT_LAUNCH(); k_mcg_band<2><<<mblocks, 256, 0, s>>>(g, Gb.as<double>(), q, pv, gh.noise, t, pp, st, max_iter, ski->status);
+      }
+      LOVE_TRY(kuu_apply<double>(gh, ski->fft, t, Kt, 1, m, fw.p, -1, s));
+      LOVE_COUNT_LAUNCH(); k_mcg_update<<<mblocks, 256, 0, s>>>(m, w, r, sv, q, t, Kt, pp, st, ski->status);
+      LOVE_COUNT_LAUNCH(); k_mcg_dir<<<mblocks, 256, 0, s>>>(m, pv, q, r, sv, st);
+      LOVE_LAUNCH_CHECK();
+    }
+    int done = 0;
+    LOVE_CUDA(cudaMemcpyAsync(&done, &st->cg_done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    if (done) break;
+  }
+  int n_it = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&n_it, &st->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  if (iters) *iters = n_it;
+  return LOVE_OK;
+}
+template love_status mean_grid_cg<float>(love_ski*, double, int, double*, int*, cudaStream_t);
+template love_status mean_grid_cg<double>(love_ski*, double, int, double*, int*, cudaStream_t);
+
 // cache build: Rt = K_UU W Q L^{-T}; a = K_UU W z; packed rows [Rt | a | 0]
 template <typename T>
 love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, const double* zmean, cudaStream_t s,
-                        T* keep_rt) {
+                        T* keep_rt, const double* amean) {
   const GridHost& gh = ski->grid;
   const int64_t m = gh.m;
   const int k = c->k_eff;
@@ -1256,8 +1583,8 @@ love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, c
   int blocks = ceil_div(m, 256);
   LOVE_COUNT_LAUNCH(); k_lt_solve<T><<<blocks, 256, 0, s>>>(R0.as<T>(), m, m, k, dptr, eptr, RT, m);
   LOVE_LAUNCH_CHECK();
-  const double* aptr = nullptr;
-  if (zmean) {
+  const double* aptr = amean;
+  if (zmean && !amean) {
     // a = K_UU W z (eq. pred_mean_ski) in FP64
     double* a1 = av.as<double>();
     size_t fwb2 = fft_work_bytes(gh, ski->fft, 1, true);
@@ -1297,9 +1624,9 @@ template love_status scatter_multi<double>(love_ski*, const double*, int64_t, in
 template love_status cg_solve<float>(love_ski*, const float*, double*, double, int, int*, cudaStream_t);
 template love_status cg_solve<double>(love_ski*, const double*, double*, double, int, int*, cudaStream_t);
 template love_status build_cache<float>(love_ski*, love_cache*, const float*, int64_t, const double*, cudaStream_t,
-                                        float*);
+                                        float*, const double*);
 template love_status build_cache<double>(love_ski*, love_cache*, const double*, int64_t, const double*,
-                                         cudaStream_t, double*);
+                                         cudaStream_t, double*, const double*);
 
 // permutation helpers used by the API (caller order <-> cell-sorted order)
 template <typename T>
@@ -1383,14 +1710,10 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
   const int64_t m = gh.m, m_pad = ldq;
   if (ks < 1 || ks > LOVE_MAX_K || m_pad % TILE_R) return LOVE_ERR_ARG;
   const int bc = box_cols(sizeof(double));
-  const int kpad = (ks + bc - 1) / bc * bc;
-  const int stages = tile_stages(kpad, sizeof(double));
-  if (stages == 0) return LOVE_ERR_UNSUPPORTED;
-  const size_t smem = tile_smem(stages, kpad, sizeof(double));
-  const int grid = (int)std::min<int64_t>(m_pad / TILE_R, num_sms());
+  const int max_grid = std::max(TILE_CTAS_PER_SM * num_sms(), 1024);
   DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s);
   size_t fwb = fft_work_bytes(gh, fft, 1, true);
-  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)std::max(grid, 1024) * (ks + 1)) ||
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)max_grid * (ks + 1)) ||
       !kq.get(sizeof(double) * m) || !y.get(sizeof(double) * m_pad) || !tv.get(sizeof(double) * (k + 1)) ||
       !fw.get(std::max<size_t>(fwb, 16)))
     return LOVE_ERR_OOM;
@@ -1399,14 +1722,10 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
   LOVE_COUNT_LAUNCH(); k_rademacher<<<ceil_div(m_pad, 256), 256, 0, s>>>(m, m_pad, seed, Q, st);
   LOVE_LAUNCH_CHECK();
   TileArgs<double> ta{};
-  ta.g = gh.dev();
-  ta.n = m;
   ta.n_pad = m_pad;
   ta.kcols = ks;
-  ta.kpad = kpad;
   ta.bc = bc;
   LOVE_TRY(make_qmap<double>(Q, ldq, ks, bc, &ta.qmap));
-  ta.stages = stages;
   ta.Q = Q;
   ta.ldq = ldq;
   ta.y = y.as<double>();
@@ -1422,9 +1741,9 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
     LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T><<<ceil_div(m_pad, 256), 256, 0, s>>>(Rt, ldr, m, m_pad, k, tv.as<double>(), kq.as<double>(), y.as<double>(), st);
     LOVE_LAUNCH_CHECK();
     ta.j = j;
-    LOVE_TRY(tile_launch<double, 1, MODE_DOT>(ta, grid, smem, s));
-    LOVE_TRY(tile_launch<double, 1, MODE_UPDATE_DOT>(ta, grid, smem, s));
-    LOVE_TRY(tile_launch<double, 1, MODE_UPDATE_NORM>(ta, grid, smem, s));
+    LOVE_TRY(tile_run<double, MODE_DOT>(ta, s));
+    LOVE_TRY(tile_run<double, MODE_UPDATE_DOT>(ta, s));
+    LOVE_TRY(tile_run<double, MODE_UPDATE_NORM>(ta, s));
   }
   int keff = 0;
   LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));

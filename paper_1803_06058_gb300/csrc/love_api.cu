@@ -403,14 +403,22 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   }
   std::copy(alpha.begin(), alpha.begin() + keff, c->alpha);
   std::copy(beta.begin(), beta.begin() + std::max(keff - 1, 0), c->beta);
-  double* z = nullptr;
-  size_t zb = sizeof(double) * (size_t)ldq;
+  double* z = nullptr;       // K^^-1 y (n-space CG) ...
+  double* am = nullptr;      // ... or the mean weights directly (grid CG)
+  const bool grid_cg = mean_grid_cg_supported(ski);
+  size_t zb = sizeof(double) * (grid_cg ? (size_t)g.m : (size_t)ldq);
   if (flags & LOVE_WANT_MEAN) {
-    z = (double*)al.alloc(zb, s);
-    if (!z) rc = LOVE_ERR_OOM;
+    double* buf = (double*)al.alloc(zb, s);
+    if (!buf) rc = LOVE_ERR_OOM;
     double tol = o->cg_tol > 0 ? o->cg_tol : (sizeof(T) == 8 ? 1e-12 : 1e-6);
     int maxit = o->cg_max_iter > 0 ? o->cg_max_iter : 4000;
-    if (rc == LOVE_OK) rc = cg_solve<T>(ski, (const T*)ski->ys, z, tol, maxit, &c->cg_iters, s);
+    if (grid_cg) {
+      am = buf;
+      if (rc == LOVE_OK) rc = mean_grid_cg<T>(ski, tol, maxit, am, &c->cg_iters, s);
+    } else {
+      z = buf;
+      if (rc == LOVE_OK) rc = cg_solve<T>(ski, (const T*)ski->ys, z, tol, maxit, &c->cg_iters, s);
+    }
   }
   ev.record(2, s);
   if (rc == LOVE_OK && (flags & LOVE_WANT_GRAD)) {
@@ -423,10 +431,11 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     rt_keep = (T*)al.alloc(rtb, s);
     if (!rt_keep) rc = LOVE_ERR_OOM;
   }
-  if (rc == LOVE_OK) rc = build_cache<T>(ski, c, Q, ldq, z, s, rt_keep);
+  if (rc == LOVE_OK) rc = build_cache<T>(ski, c, Q, ldq, z, s, rt_keep, am);
   if (rc == LOVE_OK && (flags & LOVE_WANT_GRAD)) rc = backward_tables(c, ski->fft, c->P, keff, s);
   ev.record(3, s);
   if (z) al.free(z, zb, s);
+  if (am) al.free(am, zb, s);
   al.free(Q, qb, s);
   if (rc == LOVE_OK && (flags & LOVE_WANT_SAMPLER)) {
     int ks = o->sampler_k > 0 ? o->sampler_k : o->k;

@@ -350,9 +350,15 @@ love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* o
 template <typename T>
 love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_iter, int* iters,
                      cudaStream_t s);
+// mean weights a = K_UU W K^^-1 y (m-vector, FP64) by CG on the grid system
+// (G K_UU + s^2 I) z = W y with G = W W^T; dimensions 1 and 2
+bool mean_grid_cg_supported(const love_ski* ski);
+template <typename T>
+love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s);
+// zmean: K^^-1 y (n-vector, cell-sorted) or amean: the mean weights themselves
 template <typename T>
 love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, const double* zmean,
-                        cudaStream_t s, T* keep_rt);
+                        cudaStream_t s, T* keep_rt, const double* amean = nullptr);
 // sampler Lanczos on M = K_UU - Rt Rt^T (FP64); Rt: m x k column-major (ldr)
 template <typename T>
 love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
@@ -369,6 +375,18 @@ template <typename T>
 love_status permute_out(const T* v, const int32_t* perm, int64_t n, T* out, cudaStream_t s);
 
 // k_predict.cu
+// batched predict: one entry per GP (an opaque descriptor of predict_desc_bytes()),
+// row chunks that never straddle two GPs, one persistent launch
+struct PredChunk {
+  int gp, pad;
+  int64_t begin, end;  // rows [begin, end) of GP gp (GP-local indices)
+};
+size_t predict_desc_bytes();
+void predict_fill_desc(const love_cache* c, void* dst);
+int predict_lane_candidates(int dim, int* out);
+love_status predict_batched_launch(const void* descs, const int64_t* toff, const PredChunk* chunks, int nchunks,
+                                   int dim, love_dtype dtype, love_dtype cache_dtype, int lanes, int ctas_per_sm,
+                                   const void* x, void* mean, void* var, cudaStream_t s);
 love_status predict_launch(love_cache* c, int64_t t, const void* x, void* mean, void* var,
                            cudaStream_t s);
 love_status backward_launch(love_cache* c, int64_t t, const void* x, const void* gv, void* gx,
@@ -379,6 +397,10 @@ love_status backward_tables(love_cache* c, const FftPlan* plans, const void* P, 
 // k_sample.cu
 love_status sample_launch(love_cache* c, int64_t t, const void* x, int s_count, const void* z,
                           uint64_t seed, void* out, cudaStream_t s);
+// the same with caller work space (Philox normals, no allocation)
+size_t sample_ws_bytes(const love_cache* c, int64_t t, int s_count);
+love_status sample_launch_ws(love_cache* c, int64_t t, const void* x, int s_count, uint64_t seed, void* out,
+                             void* ws, cudaStream_t s);
 
 // api helpers
 extern thread_local int g_last_cuda_error;

@@ -49,3 +49,35 @@ def test_c2_fullsize_variances(love):
     print(f"C2 |dvar|/p max {err.max():.3e} median {np.median(err):.3e}; "
           f"relative median {np.median(rel):.3e} max {rel.max():.3e}; var/p median {np.median(v_ref / p[idx]):.3e}")
     assert err.max() <= 1e-6
+
+
+def test_c2_fullsize_mean(love):
+    """Predictive mean of the full-size workload (Sec. 3, eq. pred_mean_ski)
+    against the oracle's exact SKI mean by the push-through identity (one dense
+    m x m solve, m = 1e4) at 2,000 sampled test points: |d mu| <= 1e-4 std(y),
+    the FP32 mean tolerance; the CG stopping rule bounds the error of the
+    fitted values at the training points by 1e-6 |y|."""
+    from oracle import exact as oe
+    from oracle import grid as og
+    from oracle import ski as os_
+    wl = workloads.C2
+    x = wl.x_train()
+    y = wl.y_train(x)
+    ski = love.ski_build(torch.tensor(x, dtype=torch.float32, device="cuda"),
+                         torch.tensor(y, dtype=torch.float32, device="cuda"), wl.grid_size,
+                         wl.grid_lo, wl.grid_hi, wl.lengthscale, wl.outputscale, wl.noise)
+    cache = love.love_precompute(ski, k=8, want_mean=True)
+    inf = cache.info()
+    assert 0 < inf["cg_iters"] < 4000
+    xs = wl.x_test()
+    idx = np.random.default_rng(1).choice(xs.shape[0], 2000, replace=False)
+    xs = np.asarray(xs[idx], np.float32).astype(np.float64)
+    mu, _ = love.love_predict_mean_var(cache, torch.tensor(xs, dtype=torch.float32, device="cuda"))
+    grid = og.grid_from_workload(wl)
+    xr = np.asarray(x, np.float32).astype(np.float64)
+    yr = np.asarray(y, np.float32).astype(np.float64)
+    a = oe.mean_weights_pushthrough(os_.SKI(grid, xr, wl.noise, yr))
+    mu_ref = grid.W(xs).T @ a
+    err = np.abs(mu.double().cpu().numpy() - mu_ref) / np.std(yr)
+    print(f"C2 mean: cg_iters {inf['cg_iters']}, |d mu|/std(y) max {err.max():.3e} median {np.median(err):.3e}")
+    assert err.max() <= 1e-4
