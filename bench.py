@@ -359,8 +359,186 @@ def run_gpu(args):
     return 0
 
 
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def _timed(fn, reps, flush=None):
+    """median CUDA-event time (ms) of fn() over reps runs (L2 flushed before each)."""
+    import torch
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = _ev(), _ev()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return statistics.median(out)
+
+
+def run_secondary(args):
+    """Secondary workloads (one JSON line each, not the headline): the 3-D
+    precision split (FP32 vs BF16 cache), the 2-D gradient workload, and the
+    256-GP batched serving form against 256 sequential single-GP calls."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1803_06058_gb300 as love
+    import workloads
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    peak, peak_kind = _peaks()
+    reps = max(args.steps, 3)
+    lib = love.lib()
+    l0 = lib.love_launch_count()
+    w0 = time.perf_counter()
+    base = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": reps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+
+    def ski_of(wl):
+        x = torch.tensor(wl.x_train(), dtype=torch.float32, device=dev)
+        y = torch.tensor(wl.y_train(), dtype=torch.float32, device=dev)
+        return love.ski_build(x, y, wl.grid_size, wl.grid_lo, wl.grid_hi, wl.lengthscale, wl.outputscale,
+                              wl.noise)
+
+    if args.workload == "c3":
+        wl = workloads.C3
+        ski = ski_of(wl)
+        xs = torch.tensor(wl.x_test(), dtype=torch.float32, device=dev)
+        res = {}
+        var = {}
+        for cd in ("f32", "bf16"):
+            for _ in range(args.warmup):
+                love.love_precompute(ski, k=wl.k, cache_dtype=cd, want_mean=False)
+            pre = _timed(lambda: love.love_precompute(ski, k=wl.k, cache_dtype=cd, want_mean=False), reps, flush)
+            cache = love.love_precompute(ski, k=wl.k, cache_dtype=cd, want_mean=False)
+            inf = cache.info()
+            out_v = torch.empty(wl.t, dtype=torch.float32, device=dev)
+            for _ in range(args.warmup):
+                love.love_predict_mean_var(cache, xs, want_mean=False, out_var=out_v)
+            ms = _timed(lambda: love.love_predict_mean_var(cache, xs, want_mean=False, out_var=out_v), reps, flush)
+            bpp = 3 * 4 + 4 + 64 * (inf["k_eff"] + 1) * (2 if cd == "bf16" else 4)
+            var[cd] = out_v.double()
+            clamped = cache.device_status()["clamped"]
+            res[cd] = {"predict_ms": ms, "vars_per_s": wl.t / (ms * 1e-3), "precompute_ms": pre,
+                       "lanczos_ms": inf["phase_ms"][0], "cache_build_ms": inf["phase_ms"][2],
+                       "k_eff": inf["k_eff"], "bytes_per_point": bpp,
+                       "roofline": {"bound": "hbm", "achieved": bpp * wl.t / (ms * 1e-3) / 1e9, "peak": peak,
+                                    "unit": "GB/s", "frac": bpp * wl.t / (ms * 1e-3) / 1e9 / peak,
+                                    "peak_kind": peak_kind},
+                       "clamped_at_zero": int(clamped)}
+        p = float(wl.outputscale)
+        d = (var["bf16"] - var["f32"]).abs() / p
+        res["bf16_vs_f32"] = {"max_abs_dvar_over_p": float(d.max()), "median_abs_dvar_over_p": float(d.median())}
+        line = dict(base, workload="c3", value=res["f32"]["vars_per_s"], dtype="f32",
+                    ms_per_step=res["f32"]["predict_ms"],
+                    config={"workload": wl.name, "n": wl.n, "m": wl.m, "k": wl.k, "t": wl.t,
+                            "l2": "flushed before every timed call (256 MB write)"},
+                    per_cache_dtype=res)
+    elif args.workload == "c4":
+        wl = workloads.C4
+        ski = ski_of(wl)
+        xs = torch.tensor(wl.x_test(), dtype=torch.float32, device=dev)
+        g = torch.ones(wl.t, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            love.love_precompute(ski, k=wl.k, want_mean=False, want_grad=True)
+        pre = _timed(lambda: love.love_precompute(ski, k=wl.k, want_mean=False, want_grad=True), reps, flush)
+        cache = love.love_precompute(ski, k=wl.k, want_mean=False, want_grad=True)
+        inf = cache.info()
+        fwd = _timed(lambda: love.love_predict_mean_var(cache, xs, want_mean=False), reps, flush)
+        gx = torch.empty((wl.t, 2), dtype=torch.float32, device=dev)
+        bx = _timed(lambda: lib.love_var_backward(cache.handle, wl.t, love._ptr(xs), love._ptr(g), love._ptr(gx),
+                                                  None, None, love._stream()), reps, flush)
+        bh = _timed(lambda: love.love_var_backward(cache, xs, g), reps, flush)
+        line = dict(base, workload="c4", value=wl.t / (fwd * 1e-3), dtype="f32", ms_per_step=fwd + bh,
+                    config={"workload": wl.name, "n": wl.n, "m": wl.m, "k": wl.k, "t": wl.t,
+                            "l2": "flushed before every timed call (256 MB write)"},
+                    precompute_ms=pre, precompute_split_ms=dict(zip(["lanczos", "mean_cg", "cache_build", "sampler"],
+                                                                    inf["phase_ms"])),
+                    forward_ms=fwd, backward_x_ms=bx, backward_x_and_hyper_ms=bh,
+                    backward_points_per_s=wl.t / (bh * 1e-3))
+    else:
+        bw = workloads.C5
+        members = bw.members()
+        skis = [ski_of(m) for m in members]
+        torch.cuda.synchronize()
+        t_sizes = [m.t for m in members]
+        x_all = torch.cat([torch.tensor(m.x_test(), dtype=torch.float32) for m in members]).to(dev)
+        T = x_all.shape[0]
+        kw = dict(k=bw.k, cache_dtype="bf16", want_mean=True, want_sampler=True)
+        # sequential single-GP pre-computes
+        a, b = _ev(), _ev()
+        a.record()
+        seq_caches = [love.love_precompute(sk, **kw) for sk in skis]
+        b.record()
+        torch.cuda.synchronize()
+        seq_pre = a.elapsed_time(b)
+        a, b = _ev(), _ev()
+        a.record()
+        caches, keff = love.love_precompute_batched(skis, **kw)
+        b.record()
+        torch.cuda.synchronize()
+        bat_pre = a.elapsed_time(b)
+        del seq_caches
+        batch = love.love_batch_create(caches, t_sizes)
+        mean = torch.empty(T, device=dev)
+        var = torch.empty(T, device=dev)
+        smp = torch.empty(bw.s * T, device=dev)
+        offs = [0]
+        for t in t_sizes:
+            offs.append(offs[-1] + t)
+
+        def seq_serve():
+            for i, c in enumerate(caches):
+                xi = x_all[offs[i]:offs[i + 1]]
+                love.love_predict_mean_var(c, xi, out_mean=mean[offs[i]:offs[i + 1]], out_var=var[offs[i]:offs[i + 1]])
+                love.love_sample(c, xi, bw.s, seed=7 + i)
+
+        def seq_predict():
+            for i, c in enumerate(caches):
+                xi = x_all[offs[i]:offs[i + 1]]
+                love.love_predict_mean_var(c, xi, out_mean=mean[offs[i]:offs[i + 1]], out_var=var[offs[i]:offs[i + 1]])
+
+        for _ in range(args.warmup):
+            seq_serve()
+            love.love_batch_serve(batch, x_all, mean, var, s=bw.s, seed=7, samples=smp, use_graph=True)
+        t_seq_pred = _timed(seq_predict, reps, flush)
+        t_bat_pred = _timed(lambda: love.love_predict_batched(batch, x_all, out_mean=mean, out_var=var), reps, flush)
+        t_seq = _timed(seq_serve, reps, flush)
+        t_eager = _timed(lambda: love.love_batch_serve(batch, x_all, mean, var, s=bw.s, seed=7, samples=smp,
+                                                       use_graph=False), reps, flush)
+        t_graph = _timed(lambda: love.love_batch_serve(batch, x_all, mean, var, s=bw.s, seed=7, samples=smp,
+                                                       use_graph=True), reps, flush)
+        bpp = 4 + 8 + 4 * (bw.k + 1) * 2
+        line = dict(base, workload="c5", value=T / (t_bat_pred * 1e-3), dtype="f32 (bf16 cache)",
+                    ms_per_step=t_graph,
+                    config={"workload": bw.name, "gps": len(members), "sum_n": int(sum(m.n for m in members)),
+                            "sum_m": int(sum(m.m for m in members)), "k": bw.k, "t_per_gp": bw.t, "s": bw.s,
+                            "cache_dtype": "bf16", "l2": "flushed before every timed call (256 MB write)"},
+                    precompute_ms={"sequential": seq_pre, "batched": bat_pre, "speedup": seq_pre / bat_pre},
+                    predict_ms={"sequential": t_seq_pred, "batched_one_launch": t_bat_pred,
+                                "speedup": t_seq_pred / t_bat_pred},
+                    predict_sample_ms={"sequential": t_seq, "batched_eager": t_eager, "batched_graph": t_graph,
+                                       "speedup_graph": t_seq / t_graph},
+                    autotune=batch.info(),
+                    roofline={"bound": "hbm", "achieved": bpp * T / (t_bat_pred * 1e-3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": bpp * T / (t_bat_pred * 1e-3) / 1e9 / peak,
+                              "peak_kind": peak_kind, "bytes_per_point": bpp})
+    line["gpu_launches"] = int(lib.love_launch_count() - l0)
+    line["wall_s"] = time.perf_counter() - w0
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 (default): the headline line; c3/c4/c5: secondary workload lines")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -369,6 +547,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c2":
+        return run_secondary(args)
     return run_gpu(args)
 
 

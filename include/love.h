@@ -154,6 +154,16 @@ LOVE_API love_status love_cache_destroy(love_cache_t cache);
 LOVE_API love_status love_predict_mean_var(love_cache_t cache, int64_t t, const void* x_test,
                                   void* mean, void* var, love_stream_t stream);
 
+/* love_predict_var_root -- predictive variance from the posterior root S of
+ * Sec. 3.3 (S S^T ~ K_UU - Rt Rt^T, the sampler cache): var = |S^T w*|^2 at
+ * each of t test points.  A sum of squares, so no cancellation against the
+ * prior (relative accuracy where p - |Rt^T w*|^2 loses it), but a rank-k_s
+ * truncation of the posterior covariance (exact at Krylov exhaustion).
+ * Requires LOVE_WANT_SAMPLER, else LOVE_ERR_STATE.  x_test: t x dim device
+ * array; var: t device array; both in the ski dtype.  t = 0 is a no-op. */
+LOVE_API love_status love_predict_var_root(love_cache_t cache, int64_t t, const void* x_test, void* var,
+                                           love_stream_t stream);
+
 /* love_sample -- s posterior samples at t test points (Sec. 3.3, eq. sample):
  * out[j, i] = mean_i + (W*^T S z)_{i j}, out an s x t device array (sample-major,
  * ski dtype).  z: k_s x s device array of standard normals (row-major, float for
@@ -253,6 +263,72 @@ LOVE_API love_status love_get_device_status(love_cache_t cache, int reset, love_
  * clearing); calls whose work overlaps on the GPU, on different streams or
  * from different threads, race on it.  v, out: m device arrays (dtype). */
 LOVE_API love_status ski_mvm_kuu_noalloc(love_ski_t ski, const void* v, void* out, love_stream_t stream);
+
+/* ---- Batches of independent GPs ------------------------------------------
+ * Not in the paper: a serving form of the same method for B independent
+ * KISS-GPs of uneven n, m and test-set size.  Each GP's results are those of
+ * the single-GP calls on its own handles (up to summation order). */
+
+/* love_precompute_batched -- love_precompute for skis[0..B) with shared opts.
+ * Up to `workers` pre-computes run at the same time (0 -> 8; at most 32), each
+ * on a stream of a pool the library owns, ordered after the work already
+ * queued on `stream`; the call returns when all are done (like
+ * love_precompute, it synchronises).  caches[b] receives GP b's handle and
+ * k_eff[b] (may be NULL) its Lanczos steps.  On failure every cache this call
+ * created is destroyed, caches[] is all NULL and the status of the lowest
+ * failing b is returned. */
+LOVE_API love_status love_precompute_batched(int B, const love_ski_t* skis, const love_precompute_opts* opts,
+                                             int workers, love_stream_t stream, love_cache_t* caches,
+                                             int* k_eff);
+
+typedef struct love_batch* love_batch_t;
+
+/* love_batch_create -- serve caches[0..B) together.  t_off: HOST array of
+ * B + 1 non-decreasing row offsets, t_off[0] = 0; rows t_off[b] ..
+ * t_off[b+1] - 1 of the concatenated test inputs belong to GP b.  All caches
+ * share dim, data dtype and cache dtype and must outlive the batch.  Uploads a
+ * descriptor table (one entry per GP, plus a list of row chunks that never
+ * straddle two GPs) and autotunes the launch shape of love_predict_batched
+ * (lanes per test point, CTAs per SM) by timing the candidates on synthetic
+ * in-domain points of the same sizes; synchronises `stream`.  Freed with
+ * love_batch_destroy. */
+LOVE_API love_status love_batch_create(int B, const love_cache_t* caches, const int64_t* t_off,
+                                       love_stream_t stream, love_batch_t* out);
+LOVE_API love_status love_batch_destroy(love_batch_t batch);
+
+/* love_predict_batched -- love_predict_mean_var for every GP of the batch in
+ * one kernel launch (a persistent grid walks the chunk list).  x: t_off[B] x
+ * dim device array; mean (NULL, or every cache has LOVE_WANT_MEAN) and var:
+ * t_off[B] device arrays; all in the data dtype.  No allocation, no
+ * synchronisation: it may be captured into a CUDA graph. */
+LOVE_API love_status love_predict_batched(love_batch_t batch, const void* x, void* mean, void* var,
+                                          love_stream_t stream);
+
+/* love_sample_batched -- love_sample for every GP: s samples per GP at its own
+ * rows of x, normals drawn on the device (Philox4x32-10, GP b uses seed + b).
+ * out: GP b's s x t_b sample-major block starts at element s * t_off[b].  Every
+ * cache needs LOVE_WANT_SAMPLER.  Work space comes from the batch (allocated
+ * on the first call for a given s, before any capture). */
+LOVE_API love_status love_sample_batched(love_batch_t batch, const void* x, int s, uint64_t seed, void* out,
+                                         love_stream_t stream);
+
+/* love_batch_serve -- love_predict_batched then (if s > 0) love_sample_batched
+ * on one stream.  With use_graph != 0 the launches are captured into a CUDA
+ * graph the first time a given (x, mean, var, s, seed, samples) is seen (after
+ * one eager call that sets up the work space) and the graph is replayed on
+ * later calls with the same arguments. */
+LOVE_API love_status love_batch_serve(love_batch_t batch, const void* x, void* mean, void* var, int s,
+                                      uint64_t seed, void* samples, int use_graph, love_stream_t stream);
+
+/* Launch shape chosen by the autotuner and the candidates' times (host). */
+typedef struct {
+  int lanes_per_point;      /* threads cooperating on one test point */
+  int ctas_per_sm;          /* persistent grid = ctas_per_sm x SMs (capped by chunks) */
+  int n_candidates;
+  float candidate_ms[16];   /* in the order lanes {small..large} x ctas {4, 8, 16} */
+  int64_t chunks;
+} love_batch_info_t;
+LOVE_API love_status love_batch_info(love_batch_t batch, love_batch_info_t* info);
 
 /* Host-side helpers. */
 LOVE_API const char* love_status_string(love_status s);

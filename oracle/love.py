@@ -137,6 +137,14 @@ def sampler_precompute(cache: LoveCache, k: int, seed: int, tau: float = 1e-12):
     return S, fallback
 
 
+def predict_root(cache: LoveCache, x: np.ndarray) -> np.ndarray:
+    """Predictive variance from the posterior root of Sec. 3.3 (S S^T ~ K_UU - C):
+    var(x*) = |S^T w*|^2, a sum of squares (no cancellation), exact at Krylov
+    exhaustion, a rank-k' truncation of the posterior covariance otherwise."""
+    G = cache.grid.W(x).T @ cache.S              # t x k'
+    return np.einsum("tk,tk->t", G, G)
+
+
 def sample(cache: LoveCache, x: np.ndarray, Z: np.ndarray) -> np.ndarray:
     """Samples F (s x t): F[j, i] = mu_i + (W*^T S Z)[i, j]  (eq. sample)."""
     Ws = cache.grid.W(x)

@@ -200,6 +200,126 @@ def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool =
     return Cache(h, ski.dtype, ski.dim)
 
 
+def _opts(dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,
+          cg_max_iter, sampler_k, sampler_seed):
+    o = _lib.love_precompute_opts()
+    o.k = k
+    o.cache_dtype = dtype if cache_dtype is None else _DT[cache_dtype]
+    o.flags = ((WANT_MEAN if want_mean else 0) | (WANT_SAMPLER if want_sampler else 0)
+               | (WANT_GRAD if want_grad else 0) | (PRIOR_EXACT if prior_exact else 0))
+    o.breakdown_tol = breakdown_tol
+    o.cg_tol = cg_tol
+    o.cg_max_iter = cg_max_iter
+    o.sampler_k = sampler_k
+    o.sampler_seed = sampler_seed
+    return o
+
+
+def love_precompute_batched(skis: Sequence[Ski], k: int, cache_dtype: str = None, want_mean: bool = True,
+                            want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
+                            breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
+                            sampler_k: int = 0, sampler_seed: int = 0, workers: int = 0, stream=None):
+    """love_precompute for every ski (shared options), run concurrently; returns (caches, k_eff)."""
+    B = len(skis)
+    if B == 0:
+        return [], []
+    o = _opts(skis[0].dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol,
+              cg_tol, cg_max_iter, sampler_k, sampler_seed)
+    hs = (C.c_void_p * B)(*[s.handle for s in skis])
+    out = (C.c_void_p * B)()
+    keff = (C.c_int * B)()
+    check("love_precompute_batched", lib().love_precompute_batched(B, hs, C.byref(o), workers, _stream(stream),
+                                                                   out, keff))
+    return [Cache(C.c_void_p(out[b]), skis[b].dtype, skis[b].dim) for b in range(B)], list(keff)
+
+
+class Batch:
+    """Caches served together (handle of love_batch_create); keeps the caches alive."""
+
+    def __init__(self, handle, caches, t_sizes):
+        self.handle = handle
+        self.caches = list(caches)
+        self.t_sizes = list(t_sizes)
+        self.dtype = caches[0].dtype
+        self.dim = caches[0].dim
+
+    def info(self) -> dict:
+        inf = _lib.love_batch_info_t()
+        check("love_batch_info", lib().love_batch_info(self.handle, C.byref(inf)))
+        return {"lanes_per_point": inf.lanes_per_point, "ctas_per_sm": inf.ctas_per_sm,
+                "candidate_ms": list(inf.candidate_ms)[:inf.n_candidates], "chunks": inf.chunks}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib._lib is not None:
+            _lib._lib.love_batch_destroy(self.handle)
+            self.handle = None
+
+
+def love_batch_create(caches: Sequence[Cache], t_sizes: Sequence[int], stream=None) -> Batch:
+    B = len(caches)
+    off = [0]
+    for t in t_sizes:
+        off.append(off[-1] + int(t))
+    hs = (C.c_void_p * B)(*[c.handle for c in caches])
+    to = (C.c_int64 * (B + 1))(*off)
+    h = C.c_void_p()
+    check("love_batch_create", lib().love_batch_create(B, hs, to, _stream(stream), C.byref(h)))
+    return Batch(h, caches, t_sizes)
+
+
+def love_predict_batched(batch: Batch, x_test: torch.Tensor, want_mean: bool = True, stream=None,
+                         out_mean=None, out_var=None):
+    """x_test: the concatenated test points of all GPs (sum t_b, dim)."""
+    dt = _TORCH[batch.dtype]
+    x_test = _as_points(x_test, batch.dim, dt)
+    T = x_test.shape[0]
+    if T != sum(batch.t_sizes):
+        raise ValueError("x_test rows must equal the batch's total test points")
+    var = out_var if out_var is not None else torch.empty(T, dtype=dt, device=x_test.device)
+    mean = None
+    if want_mean:
+        mean = out_mean if out_mean is not None else torch.empty(T, dtype=dt, device=x_test.device)
+    check("love_predict_batched", lib().love_predict_batched(batch.handle, _ptr(x_test), _ptr(mean), _ptr(var),
+                                                             _stream(stream)))
+    return mean, var
+
+
+def love_sample_batched(batch: Batch, x_test: torch.Tensor, s: int, seed: int = 0, stream=None, out=None):
+    """s samples per GP; returns a flat tensor: GP b's s x t_b block starts at s * t_off[b]."""
+    dt = _TORCH[batch.dtype]
+    x_test = _as_points(x_test, batch.dim, dt)
+    T = x_test.shape[0]
+    if T != sum(batch.t_sizes):
+        raise ValueError("x_test rows must equal the batch's total test points")
+    out = out if out is not None else torch.empty(s * T, dtype=dt, device=x_test.device)
+    check("love_sample_batched", lib().love_sample_batched(batch.handle, _ptr(x_test), s, seed, _ptr(out),
+                                                           _stream(stream)))
+    return out
+
+
+def love_batch_serve(batch: Batch, x_test: torch.Tensor, mean: Optional[torch.Tensor], var: torch.Tensor,
+                     s: int = 0, seed: int = 0, samples: Optional[torch.Tensor] = None, use_graph: bool = True,
+                     stream=None):
+    """Predict (and sample) the whole batch into caller buffers; with use_graph the launches
+    are captured into one CUDA graph on first use and replayed afterwards."""
+    dt = _TORCH[batch.dtype]
+    x_test = _as_points(x_test, batch.dim, dt)
+    check("love_batch_serve", lib().love_batch_serve(batch.handle, _ptr(x_test), _ptr(mean), _ptr(var), s, seed,
+                                                     _ptr(samples), int(use_graph), _stream(stream)))
+
+
+def batch_split(batch: Batch, flat: torch.Tensor, s: int = 0):
+    """Views of a batched output per GP: (t_b,) for predict outputs, (s, t_b) for samples."""
+    res, off = [], 0
+    for t in batch.t_sizes:
+        if s:
+            res.append(flat[off * s:(off + t) * s].view(s, t))
+        else:
+            res.append(flat[off:off + t])
+        off += t
+    return res
+
+
 def love_predict_mean_var(cache: Cache, x_test: torch.Tensor, want_mean: bool = True,
                           stream=None, out_mean=None, out_var=None):
     dt = _TORCH[cache.dtype]
@@ -213,6 +333,17 @@ def love_predict_mean_var(cache: Cache, x_test: torch.Tensor, want_mean: bool = 
           lib().love_predict_mean_var(cache.handle, t, _ptr(x_test), _ptr(mean), _ptr(var),
                                       _stream(stream)))
     return mean, var
+
+
+def love_predict_var_root(cache: Cache, x_test: torch.Tensor, stream=None, out_var=None) -> torch.Tensor:
+    """Variance from the posterior root: |S^T w*|^2 (needs want_sampler)."""
+    dt = _TORCH[cache.dtype]
+    x_test = _as_points(x_test, cache.dim, dt)
+    t = x_test.shape[0]
+    var = out_var if out_var is not None else torch.empty(t, dtype=dt, device=x_test.device)
+    check("love_predict_var_root", lib().love_predict_var_root(cache.handle, t, _ptr(x_test), _ptr(var),
+                                                               _stream(stream)))
+    return var
 
 
 def love_sample(cache: Cache, x_test: torch.Tensor, s: int, z: Optional[torch.Tensor] = None,

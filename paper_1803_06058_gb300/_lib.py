@@ -51,6 +51,11 @@ class love_device_status_t(C.Structure):
     _fields_ = [("bits", C.c_uint32), ("domain_errors", C.c_int64), ("clamped", C.c_int64)]
 
 
+class love_batch_info_t(C.Structure):
+    _fields_ = [("lanes_per_point", C.c_int), ("ctas_per_sm", C.c_int), ("n_candidates", C.c_int),
+                ("candidate_ms", C.c_float * 16), ("chunks", C.c_int64)]
+
+
 VP = C.c_void_p
 DP = C.POINTER(C.c_double)
 
@@ -66,6 +71,7 @@ SIGNATURES = {
     "love_cache_destroy": (C.c_int, [VP]),
     "love_predict_mean_var": (C.c_int, [VP, C.c_int64, VP, VP, VP, VP]),
     "love_sample": (C.c_int, [VP, C.c_int64, VP, C.c_int, VP, C.c_uint64, VP, VP]),
+    "love_predict_var_root": (C.c_int, [VP, C.c_int64, VP, VP, VP]),
     "love_var_backward": (C.c_int, [VP, C.c_int64, VP, VP, VP, DP, DP, VP]),
     "love_cache_info": (C.c_int, [VP, C.POINTER(love_cache_info_t)]),
     "love_cache_import": (C.c_int, [C.POINTER(love_ski_desc), C.c_int, C.c_int, C.c_uint, DP, DP,
@@ -74,6 +80,14 @@ SIGNATURES = {
     "love_cache_save": (C.c_int, [VP, C.c_char_p, VP]),
     "love_cache_load": (C.c_int, [C.c_char_p, C.POINTER(love_allocator), VP, C.POINTER(VP)]),
     "love_get_device_status": (C.c_int, [VP, C.c_int, C.POINTER(love_device_status_t), VP]),
+    "love_precompute_batched": (C.c_int, [C.c_int, C.POINTER(VP), C.POINTER(love_precompute_opts), C.c_int, VP,
+                                          C.POINTER(VP), C.POINTER(C.c_int)]),
+    "love_batch_create": (C.c_int, [C.c_int, C.POINTER(VP), C.POINTER(C.c_int64), VP, C.POINTER(VP)]),
+    "love_batch_destroy": (C.c_int, [VP]),
+    "love_predict_batched": (C.c_int, [VP, VP, VP, VP, VP]),
+    "love_sample_batched": (C.c_int, [VP, VP, C.c_int, C.c_uint64, VP, VP]),
+    "love_batch_serve": (C.c_int, [VP, VP, VP, VP, C.c_int, C.c_uint64, VP, C.c_int, VP]),
+    "love_batch_info": (C.c_int, [VP, C.POINTER(love_batch_info_t)]),
     "love_status_string": (C.c_char_p, [C.c_int]),
     "love_last_cuda_error": (C.c_int, []),
     "love_launch_count": (C.c_uint64, []),

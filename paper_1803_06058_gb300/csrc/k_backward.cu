@@ -256,20 +256,41 @@ __global__ void __launch_bounds__(BWD_WARPS * 32) k_var_backward(BwdArgs a) {
         s_vdv[e].add_prod(v[j], dv[e][j]);
         s_uv[e].add_prod(u[e][j], v[j]);
       }
-      // row c of B_e and Minv against v
-      Acc bm[D], mm;
-      mm.zero();
+      // row c of B_e and Minv against v.  Both matrices are symmetric, so row c
+      // is read as column c (lanes read consecutive addresses); four
+      // independent accumulators per product keep the chains short.
+      Acc bm[D][4], mm[4];
 #pragma unroll
-      for (int e = 0; e < D; ++e) bm[e].zero();
-      for (int b = 0; b < a.k; ++b) {
-        T vb = vsh[wp][b];
-        mm.add_prod(Mi[(int64_t)c * a.k + b], vb);
+      for (int u = 0; u < 4; ++u) {
+        mm[u].zero();
 #pragma unroll
-        for (int e = 0; e < D; ++e) bm[e].add_prod(Bm[((int64_t)e * a.k + c) * a.k + b], vb);
+        for (int e = 0; e < D; ++e) bm[e][u].zero();
       }
-      s_m.add_prod((T)mm.value(), v[j]);
+      int b = 0;
+      for (; b + 3 < a.k; b += 4) {
 #pragma unroll
-      for (int e = 0; e < D; ++e) s_b[e].add_prod((T)bm[e].value(), v[j]);
+        for (int u = 0; u < 4; ++u) {
+          const T vb = vsh[wp][b + u];
+          mm[u].add_prod(Mi[(int64_t)(b + u) * a.k + c], vb);
+#pragma unroll
+          for (int e = 0; e < D; ++e) bm[e][u].add_prod(Bm[((int64_t)e * a.k + b + u) * a.k + c], vb);
+        }
+      }
+      for (; b < a.k; ++b) {
+        const T vb = vsh[wp][b];
+        mm[0].add_prod(Mi[(int64_t)b * a.k + c], vb);
+#pragma unroll
+        for (int e = 0; e < D; ++e) bm[e][0].add_prod(Bm[((int64_t)e * a.k + b) * a.k + c], vb);
+      }
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        mm[0].merge(mm[u].s, mm[u].c);
+#pragma unroll
+        for (int e = 0; e < D; ++e) bm[e][0].merge(bm[e][u].s, bm[e][u].c);
+      }
+      s_m.add_prod((T)mm[0].value(), v[j]);
+#pragma unroll
+      for (int e = 0; e < D; ++e) s_b[e].add_prod((T)bm[e][0].value(), v[j]);
     }
     __syncwarp();
     warp_merge(s_m);

@@ -22,71 +22,11 @@
 #include <cmath>
 
 #include "love_internal.cuh"
+#include "fft_core.cuh"
 
 namespace love {
 namespace {
-
-template <typename R> struct Cplx;
-template <> struct Cplx<float> { using type = float2; };
-template <> struct Cplx<double> { using type = double2; };
-
-template <typename C>
-__device__ __forceinline__ C cmul(C a, C b) {
-  C r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
-}
-template <typename C>
-__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
-template <typename C>
-__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
-
-__device__ __forceinline__ int bitrev(int i, int logL) { return (int)(__brev((unsigned)i) >> (32 - logL)); }
-
-// F interleaved arrays x[i * F + f] of length L; decimation in time on
-// bit-reversed input, natural-order output.  tw: master table W_N^j.
-template <typename C>
-__device__ void fft_dit(C* x, int L, int logF, const C* __restrict__ tw, int N, bool inverse) {
-  const int F = 1 << logF;
-  const int work = (L >> 1) << logF;
-  for (int half = 1; half < L; half <<= 1) {
-    const int tws = N / (2 * half);
-    for (int t = threadIdx.x; t < work; t += blockDim.x) {
-      int f = t & (F - 1), b = t >> logF;
-      int j = b & (half - 1);
-      int i1 = ((b - j) << 1) + j, i2 = i1 + half;
-      C w = tw[j * tws];
-      if (inverse) w.y = -w.y;
-      C a = x[(i1 << logF) + f];
-      C c = cmul(x[(i2 << logF) + f], w);
-      x[(i1 << logF) + f] = cadd(a, c);
-      x[(i2 << logF) + f] = csub(a, c);
-    }
-    __syncthreads();
-  }
-}
-// decimation in frequency: natural-order input, bit-reversed output
-template <typename C>
-__device__ void fft_dif(C* x, int L, int logF, const C* __restrict__ tw, int N, bool inverse) {
-  const int F = 1 << logF;
-  const int work = (L >> 1) << logF;
-  for (int half = L >> 1; half >= 1; half >>= 1) {
-    const int tws = N / (2 * half);
-    for (int t = threadIdx.x; t < work; t += blockDim.x) {
-      int f = t & (F - 1), b = t >> logF;
-      int j = b & (half - 1);
-      int i1 = ((b - j) << 1) + j, i2 = i1 + half;
-      C w = tw[j * tws];
-      if (inverse) w.y = -w.y;
-      C a = x[(i1 << logF) + f];
-      C c = x[(i2 << logF) + f];
-      x[(i1 << logF) + f] = cadd(a, c);
-      x[(i2 << logF) + f] = cmul(csub(a, c), w);
-    }
-    __syncthreads();
-  }
-}
+using namespace fftcore;
 
 // address of element i of fibre `fid` of column `col` along mode e
 struct ModeGeom {
@@ -109,6 +49,8 @@ __global__ void k_toep_small(const IO* __restrict__ in, IO* __restrict__ out, Mo
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
   const int F = 1 << logF;
+  C* w = x + ((size_t)N << logF);   // [N / 2] twiddles
+  load_twiddles(w, N, tw, N);
   const int64_t fib0 = (int64_t)blockIdx.x * F;
   // load (fibre fastest), zero padded, into bit-reversed slots
   for (int t = threadIdx.x; t < (N << logF); t += blockDim.x) {
@@ -125,7 +67,7 @@ __global__ void k_toep_small(const IO* __restrict__ in, IO* __restrict__ out, Mo
     x[(bitrev(i, logN) << logF) + f] = c;
   }
   __syncthreads();
-  fft_dit(x, N, logF, tw, N, false);
+  fft_dit(x, N, logF, w, false);
   for (int t = threadIdx.x; t < (N << logF); t += blockDim.x) {
     int i = t >> logF;
     R l = lam[i];
@@ -133,7 +75,7 @@ __global__ void k_toep_small(const IO* __restrict__ in, IO* __restrict__ out, Mo
     x[t].y *= l;
   }
   __syncthreads();
-  fft_dif(x, N, logF, tw, N, true);
+  fft_dif(x, N, logF, w, true);
   for (int t = threadIdx.x; t < (N << logF); t += blockDim.x) {
     int f = t & (F - 1), i = t >> logF;
     int64_t fb = fib0 + f;
@@ -155,6 +97,8 @@ __global__ void k_four_a(const IO* __restrict__ in, typename Cplx<R>::type* __re
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
   const int FA = 1 << logFA;
+  C* w = x + ((size_t)N2 << logFA);   // [N2 / 2] twiddles
+  load_twiddles(w, N2, tw, N);
   const int n1_0 = blockIdx.x * FA;
   const int64_t fb = blockIdx.y;
   const int64_t col = fb / mg.nfib, fid = fb - col * mg.nfib;
@@ -168,7 +112,7 @@ __global__ void k_four_a(const IO* __restrict__ in, typename Cplx<R>::type* __re
     x[(bitrev(n2, logN2) << logFA) + f] = c;
   }
   __syncthreads();
-  fft_dit(x, N2, logFA, tw, N, false);
+  fft_dit(x, N2, logFA, w, false);
   C* wdst = work + fb * (int64_t)N;
   for (int t = threadIdx.x; t < (N2 << logFA); t += blockDim.x) {
     int f = t & (FA - 1), k2 = t >> logFA;
@@ -189,6 +133,8 @@ __global__ void k_four_b(typename Cplx<R>::type* __restrict__ work, int N, int N
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
   const int FB = 1 << logFB;
+  C* w = x + ((size_t)N1 << logFB);   // [N1 / 2] twiddles
+  load_twiddles(w, N1, tw, N);
   const int k2_0 = blockIdx.x * FB;
   const int64_t fb = blockIdx.y;
   C* wrow = work + fb * (int64_t)N;
@@ -198,7 +144,7 @@ __global__ void k_four_b(typename Cplx<R>::type* __restrict__ work, int N, int N
     x[(bitrev(n1, logN1) << logFB) + f] = wrow[(int64_t)(k2_0 + f) * N1 + n1];
   }
   __syncthreads();
-  fft_dit(x, N1, logFB, tw, N, false);
+  fft_dit(x, N1, logFB, w, false);
   if (lam == nullptr) {
     for (int t = threadIdx.x; t < (N1 << logFB); t += blockDim.x) {
       int f = t & (FB - 1), k1 = t >> logFB;
@@ -213,7 +159,7 @@ __global__ void k_four_b(typename Cplx<R>::type* __restrict__ work, int N, int N
     x[t].y *= l;
   }
   __syncthreads();
-  fft_dif(x, N1, logFB, tw, N, true);
+  fft_dif(x, N1, logFB, w, true);
   for (int t = threadIdx.x; t < (N1 << logFB); t += blockDim.x) {
     int n1 = t & (N1 - 1), f = t >> logN1;
     wrow[(int64_t)(k2_0 + f) * N1 + n1] = x[(bitrev(n1, logN1) << logFB) + f];
@@ -229,6 +175,8 @@ __global__ void k_four_c(const typename Cplx<R>::type* __restrict__ work, IO* __
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* x = reinterpret_cast<C*>(smem_raw);
   const int FA = 1 << logFA;
+  C* w = x + ((size_t)N2 << logFA);   // [N2 / 2] twiddles
+  load_twiddles(w, N2, tw, N);
   const int n1_0 = blockIdx.x * FA;
   const int64_t fb = blockIdx.y;
   const int64_t col = fb / mg.nfib, fid = fb - col * mg.nfib;
@@ -241,7 +189,7 @@ __global__ void k_four_c(const typename Cplx<R>::type* __restrict__ work, IO* __
     x[t] = cmul(wsrc[(int64_t)k2 * N1 + n1], w);
   }
   __syncthreads();
-  fft_dif(x, N2, logFA, tw, N, true);
+  fft_dif(x, N2, logFA, w, true);
   for (int t = threadIdx.x; t < (N2 << logFA); t += blockDim.x) {
     int f = t & (FA - 1), n2 = t >> logFA;
     int64_t idx = (int64_t)(n1_0 + f) + (int64_t)N1 * n2;
@@ -301,11 +249,6 @@ inline int four_logF(int L, int cap, int64_t count) {
   return l;
 }
 
-template <typename K>
-love_status allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return LOVE_OK;
-  return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
 
 template <typename R>
 int small_logF(int N, int64_t total) {
@@ -319,23 +262,23 @@ int small_logF(int N, int64_t total) {
   return l;
 }
 
-// One mode of K_UU applied to FP32 or FP64 data; the transform itself always
-// runs in FP64 (twiddles and lambda in FP64): K_UU is m-sized, so this costs
-// little, and it keeps the Toeplitz product accurate to the rounding of its
-// inputs and outputs (an FP32 transform of length N carries ~log2(N) 2^-24).
-template <typename IO>
+// One mode of K_UU applied to FP32 or FP64 data.  The transform runs in R =
+// FP64 (twiddles and lambda in FP64): K_UU is m-sized, so this costs little,
+// and it keeps the Toeplitz product accurate to the rounding of its inputs and
+// outputs (an FP32 transform of length N carries ~log2(N) 2^-24).
+template <typename IO, typename R>
 love_status toeplitz_mode(const FftPlan& p, const IO* in, IO* out, ModeGeom mg, int ncol, void* work,
                           bool deriv, cudaStream_t s) {
-  using R = double;
-  using C = double2;
-  const C* tw = (const C*)p.tw_d;
-  const R* lam = (const R*)(deriv ? p.lamdl_d : p.lam_d);
+  using C = typename Cplx<R>::type;
+  const bool dbl = sizeof(R) == 8;
+  const C* tw = (const C*)(dbl ? p.tw_d : p.tw_f);
+  const R* lam = (const R*)(deriv ? (dbl ? p.lamdl_d : p.lamdl_f) : (dbl ? p.lam_d : p.lam_f));
   const int N = (int)p.N;
   const int64_t total = mg.nfib * ncol;
   if (p.N2 == 1) {
     int logF = small_logF<R>(N, total);
     int F = 1 << logF;
-    size_t sm = (size_t)N * F * sizeof(C);
+    size_t sm = ((size_t)N * F + N / 2) * sizeof(C);
     int threads = std::min(512, std::max(64, (N * F) / 4));
     int64_t blocks = (total + F - 1) / F;
     LOVE_TRY(allow_smem(k_toep_small<IO, R>, sm));
@@ -350,7 +293,7 @@ love_status toeplitz_mode(const FftPlan& p, const IO* in, IO* out, ModeGeom mg, 
   int logFB = four_logF(N1, cap, (int64_t)N2 * total);
   int FB = 1 << logFB;
   dim3 ga(N1 / FA, (unsigned)total), gb(N2 / FB, (unsigned)total);
-  size_t sma = (size_t)N2 * FA * sizeof(C), smb = (size_t)N1 * FB * sizeof(C);
+  size_t sma = ((size_t)N2 * FA + N2 / 2) * sizeof(C), smb = ((size_t)N1 * FB + N1 / 2) * sizeof(C);
   LOVE_TRY(allow_smem(k_four_a<IO, R>, sma));
   LOVE_TRY(allow_smem(k_four_b<R>, smb));
   LOVE_TRY(allow_smem(k_four_c<IO, R>, sma));
@@ -367,7 +310,7 @@ love_status fft_forward_small_f64(const FftPlan& p, const double2* src, double2*
   const int N = (int)p.N;
   cudaError_t e = cudaMemcpyAsync(work, src, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_check(e);
-  size_t sm = (size_t)N * sizeof(double2);
+  size_t sm = ((size_t)N + N / 2) * sizeof(double2);
   LOVE_TRY(allow_smem(k_four_b<double>, sm));
   LOVE_COUNT_LAUNCH(); k_four_b<double><<<dim3(1, 1), 256, sm, s>>>(work, N, N, 1, ilog2(N), 0, (const double2*)p.tw_d, nullptr, dst);
   return cuda_check(cudaGetLastError());
@@ -420,9 +363,9 @@ love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocato
       int logFA = four_logF(p.N2, 2048, p.N1);
       int logFB = four_logF(p.N1, 2048, p.N2);
       dim3 ga(p.N1 >> logFA, 1), gb(p.N2 >> logFB, 1);
-      LOVE_COUNT_LAUNCH(); k_four_a<double, double><<<ga, 256, (size_t)p.N2 * (1 << logFA) * sizeof(double2), s>>>(
+      LOVE_COUNT_LAUNCH(); k_four_a<double, double><<<ga, 256, ((size_t)p.N2 * (1 << logFA) + p.N2 / 2) * sizeof(double2), s>>>(
           re, wk, mg, (int)N, p.N1, p.N2, ilog2(p.N2), logFA, (const double2*)p.tw_d);
-      LOVE_COUNT_LAUNCH(); k_four_b<double><<<gb, 256, (size_t)p.N1 * (1 << logFB) * sizeof(double2), s>>>(
+      LOVE_COUNT_LAUNCH(); k_four_b<double><<<gb, 256, ((size_t)p.N1 * (1 << logFB) + p.N1 / 2) * sizeof(double2), s>>>(
           wk, (int)N, p.N1, p.N2, ilog2(p.N1), logFB, (const double2*)p.tw_d, nullptr, X);
     }
     LOVE_COUNT_LAUNCH(); k_lambda_store<<<nb, 256, 0, s>>>(X, N, (double*)(deriv ? p.lamdl_d : p.lam_d),
@@ -463,7 +406,7 @@ love_status kuu_apply(const GridHost& g, const FftPlan* plans, const T* v, T* ou
   const T* src = v;
   for (int e = 0; e < g.dim; ++e) {
     ModeGeom mg{g.g[e], g.stride[e], g.m / g.g[e], ldc};
-    LOVE_TRY(toeplitz_mode<T>(plans[e], src, out, mg, ncol, work, e == deriv_dim, s));
+    LOVE_TRY((toeplitz_mode<T, double>(plans[e], src, out, mg, ncol, work, e == deriv_dim, s)));
     src = out;
   }
   return LOVE_OK;

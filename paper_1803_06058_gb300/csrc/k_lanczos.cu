@@ -358,6 +358,29 @@ struct TileArgs {
   DevStatus* status;
 };
 
+// 4 consecutive rows of one column in shared memory (one 16-byte access for
+// float, two for double)
+template <typename T> struct Row4;
+template <> struct Row4<float> {
+  static __device__ __forceinline__ void load(const float* p, float* v) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  }
+  static __device__ __forceinline__ void store(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Row4<double> {
+  static __device__ __forceinline__ void load(const double* p, double* v) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  static __device__ __forceinline__ void store(double* p, const double* v) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
 // One reorthogonalisation sweep over the row tiles of [Q_j | y].  Per tile,
 // TILE_R rows of columns 0..j of Q (2-D TMA boxes of bc columns) and of y (a
 // 1-D bulk copy) land in one stage of a shared-memory ring, so every step
@@ -365,13 +388,13 @@ struct TileArgs {
 //   DOT          c = Q_j^T y                       (alpha_j = c_j)
 //   UPDATE_DOT   y -= Q_j c;   c' = Q_j^T y
 //   UPDATE_NORM  y -= Q_j c';  beta_j = |y|;  q_{j+1} = y (scaled on next use)
-// The update gives each row two threads (the two halves of the columns, two
-// independent FMA chains each); the dots give warp w the columns w, w + 8, ...
-// with each lane owning TILE_R / 32 rows.  Two CTAs share an SM so that one
-// computes while the other waits for its ring.
+// Both the update and the dots give warp w the columns w, w + 8, ... and lane
+// l the rows 4l .. 4l + 3 (16-byte shared-memory accesses); the update's eight
+// per-warp partial sums of a row are added in a fixed order.
 template <typename T, int MODE, int KPW>
 __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constant__ TileArgs<T> a) {
   using Acc = typename AccOf<T>::type;
+  static_assert(TILE_R == 128 && TILE_T == 256, "row-quad mapping assumes 128 rows, 8 warps");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LanczosState* st = a.st;
   if (st->done) return;
@@ -380,10 +403,10 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const size_t stage_elems = (size_t)(a.kpad + 1) * TILE_R;               // Q columns, then y
   T* ring = reinterpret_cast<T*>(smem_raw);                                // [stages][kpad + 1][TILE_R]
-  T* cf = ring + (size_t)a.stages * stage_elems;                           // [kcols]
-  T* hp = cf + a.kcols;                                                     // [TILE_R]
+  T* cf = ring + (size_t)a.stages * stage_elems;                           // [kcols] (16-byte padded)
+  T* hp = cf + ((a.kcols + 3) & ~3);                                       // [NWARP][TILE_R]
   uint64_t* bar = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(hp + TILE_R) + 15) & ~uintptr_t(15));    // [stages]
+      (reinterpret_cast<uintptr_t>(hp + NWARP * TILE_R) + 15) & ~uintptr_t(15));  // [stages]
   __shared__ Acc red[NWARP];
 
   if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
@@ -418,6 +441,7 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
   for (int s = 0; s < KPW; ++s) acc[s].zero();
   Acc nacc;
   nacc.zero();
+  const int r0 = 4 * lane;   // this lane's rows r0 .. r0 + 3
 
   int it = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -431,27 +455,28 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
     }
     T* Qt = ring + (size_t)s * stage_elems;
     T* yt = Qt + (size_t)a.kpad * TILE_R;
-    // ---- update: y -= Q_j c, two threads per row
+    // ---- update: y -= Q_j c
     if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
-      const int r = tid & (TILE_R - 1), h = tid / TILE_R;
-      const int mid = (ncols + 1) >> 1;
-      const int i1 = h ? ncols : mid;
-      T s0 = T(0), s1 = T(0);
-      int i = h ? mid : 0;
-      for (; i + 1 < i1; i += 2) {
-        s0 = fma(Qt[(size_t)i * TILE_R + r], cf[i], s0);
-        s1 = fma(Qt[(size_t)(i + 1) * TILE_R + r], cf[i + 1], s1);
+      T ps[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
+      for (int i = warp; i < ncols; i += NWARP) {
+        T q[4];
+        Row4<T>::load(Qt + (size_t)i * TILE_R + r0, q);
+        const T ci = cf[i];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) ps[r] = fma(q[r], ci, ps[r]);
       }
-      if (i < i1) s0 = fma(Qt[(size_t)i * TILE_R + r], cf[i], s0);
-      const T part = s0 + s1;
-      if (h) hp[r] = part;
+      Row4<T>::store(hp + warp * TILE_R + r0, ps);
       __syncthreads();
-      if (!h) {
-        const T yv = yt[r] - (part + hp[r]);
-        const int64_t p = tile * TILE_R + r;
+      if (tid < TILE_R) {
+        T sum = hp[tid];
+#pragma unroll
+        for (int w = 1; w < NWARP; ++w) sum += hp[w * TILE_R + tid];
+        const T yv = yt[tid] - sum;
+        const int64_t p = tile * TILE_R + tid;
         if (MODE == MODE_UPDATE_DOT) {
           a.y[p] = yv;
-          yt[r] = yv;
+          yt[tid] = yv;
           fence_proxy_async();
         } else {
           if (j + 1 < a.kcols)
@@ -463,22 +488,23 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
       }
       if (MODE == MODE_UPDATE_DOT) __syncthreads();
     }
-    // ---- column dots: warp w owns columns w, w + NWARP, ...
+    // ---- column dots: c_i += q_i . y over this tile
     if (MODE != MODE_UPDATE_NORM) {
-      T yr[TILE_R / 32];
-#pragma unroll
-      for (int r = 0; r < TILE_R / 32; ++r) yr[r] = yt[lane + 32 * r];
+      T yr[4];
+      Row4<T>::load(yt + r0, yr);
 #pragma unroll
       for (int s2 = 0; s2 < KPW; ++s2) {
         const int i = warp + NWARP * s2;
         if (i < ncols) {
-          // a partial over this lane's TILE_R / 32 rows, folded into the
-          // double-float sum: the partials are ~sqrt(TILE_R / 32 / n) of the
-          // total, so their rounding stays far below the final rounding
-          const T* qc = Qt + (size_t)i * TILE_R;
-          T part = T(0);
-#pragma unroll
-          for (int r = 0; r < TILE_R / 32; ++r) part = fma(qc[lane + 32 * r], yr[r], part);
+          // a partial over this lane's 4 rows, folded into the double-float
+          // sum: the partials are ~sqrt(4 / n) of the total, so their
+          // rounding stays far below the final rounding
+          T q[4];
+          Row4<T>::load(Qt + (size_t)i * TILE_R + r0, q);
+          T part = q[0] * yr[0];
+          part = fma(q[1], yr[1], part);
+          part = fma(q[2], yr[2], part);
+          part = fma(q[3], yr[3], part);
           acc[s2].add(part);
         }
       }
@@ -922,11 +948,6 @@ __global__ void k_permute_out(const T* __restrict__ v, const int32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-template <typename K>
-love_status allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return LOVE_OK;
-  return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
 
 struct DevBuf {
   const Allocator* al;
@@ -977,26 +998,43 @@ love_status gather_any(love_ski* ski, const T* u, T a, T b, const T* v, T* out, 
 }
 
 // Ring geometry per launch: a stage holds the j + 1 live columns (rounded up
-// to the box width) plus the y column; as many stages (2..8) as fit a budget
-// that leaves room for two CTAs per SM.
+// to the box width) plus the y column.  Two CTAs per SM whenever each can
+// keep at least two stages (one computes while the other waits on its ring),
+// with as many stages as fit (up to 8); otherwise one CTA with as many stages
+// as fit the SM's shared memory.
 inline size_t tile_smem(int stages, int kpad, int kcols, size_t elem) {
-  return (size_t)stages * (kpad + 1) * TILE_R * elem + (size_t)kcols * elem + TILE_R * elem + 16 + 8 * stages;
+  return (size_t)stages * (kpad + 1) * TILE_R * elem + (size_t)((kcols + 3) & ~3) * elem +
+         (size_t)NWARP * TILE_R * elem + 16 + 8 * (size_t)stages;
 }
-inline int tile_stages(int kpad, int kcols, size_t elem) {
-  const size_t budget = 104 * 1024, cap = 225 * 1024;
-  int st = (int)std::min<size_t>(8, budget / ((size_t)(kpad + 1) * TILE_R * elem));
-  st = std::max(st, 2);
-  while (st > 1 && tile_smem(st, kpad, kcols, elem) > cap) --st;
-  return tile_smem(st, kpad, kcols, elem) <= cap ? st : 0;
+struct TileGeom {
+  int stages, ctas;
+};
+inline TileGeom tile_geom(int kpad, int kcols, size_t elem) {
+  // per-CTA dynamic limit: 227 KB opt-in less ~1 KB for the kernel's static
+  // shared memory; per SM: 228 KB, with 1 KB reserved per CTA plus the static part
+  const size_t cta_cap = 231424, sm_cap = 233472, reserved = 2048;
+  for (int ctas = 2; ctas >= 1; --ctas)
+    for (int st = 8; st >= (ctas == 2 ? 2 : 1); --st) {
+      const size_t b = tile_smem(st, kpad, kcols, elem);
+      if (b <= cta_cap && (size_t)ctas * (b + reserved) <= sm_cap) return TileGeom{st, ctas};
+    }
+  return TileGeom{0, 1};
 }
 constexpr int TILE_CTAS_PER_SM = 2;
+
+template <typename T>
+love_status make_qmap(T* Q, int64_t ldq, int kcols, int bc, CUtensorMap* out);
 
 template <typename T, int MODE>
 love_status tile_run(TileArgs<T> a, cudaStream_t s) {
   const int ncols = a.j + 1;
   a.kpad = (ncols + a.bc - 1) / a.bc * a.bc;
-  a.stages = tile_stages(a.kpad, a.kcols, sizeof(T));
-  if (a.stages == 0) return LOVE_ERR_UNSUPPORTED;
+  const TileGeom tg = tile_geom(a.kpad, a.kcols, sizeof(T));
+  if (tg.stages == 0) return LOVE_ERR_UNSUPPORTED;
+  a.stages = tg.stages;
+  // the tensor map spans the live columns only (at least one box wide): box
+  // columns past its extent read as zeros without touching memory
+  LOVE_TRY(make_qmap<T>(a.Q, a.ldq, std::min(std::max(ncols, a.bc), a.kcols), a.bc, &a.qmap));
   const size_t smem = tile_smem(a.stages, a.kpad, a.kcols, sizeof(T));
   const int64_t ntiles = a.n_pad / TILE_R;
 #define LOVE_TILE_CASE(KPW)                                                                    \
@@ -1005,7 +1043,7 @@ love_status tile_run(TileArgs<T> a, cudaStream_t s) {
     LOVE_TRY(allow_smem(kern, smem));                                                          \
     int per_sm = 0;                                                                            \
     LOVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE_T, smem));     \
-    per_sm = std::min(std::max(per_sm, 1), TILE_CTAS_PER_SM);                                  \
+    per_sm = std::min(std::max(per_sm, 1), tg.ctas);                                           \
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms());              \
     LOVE_COUNT_LAUNCH(); kern<<<grid, TILE_T, smem, s>>>(a);                                   \
     return cuda_check(cudaGetLastError());                                                     \
@@ -1120,7 +1158,6 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
   ta.n_pad = ski->n_pad;
   ta.kcols = k;
   ta.bc = bc;
-  LOVE_TRY(make_qmap<T>(Q, ldq, k, bc, &ta.qmap));
   ta.Q = Q;
   ta.ldq = ldq;
   ta.y = y.as<T>();
@@ -1333,14 +1370,20 @@ __global__ void k_gram_band(GridDev g, const T* __restrict__ xs, const int* __re
   }
 }
 
-// t = G q + s^2 p (= A p);  pi = q . t (= <p, A p>_K)
+// The new direction p = r + beta p', q = s + beta q' (q = K p) is formed on
+// the fly (at the node and at its band neighbours, the same fma everywhere)
+// and written to the other buffer of a pair; then t = G q + s^2 p (= A p) and
+// pi = q . t (= <p, A p>_K).
 template <int D>
-__global__ void k_mcg_band(GridDev g, const double* __restrict__ G, const double* __restrict__ q,
-                           const double* __restrict__ pv, double noise, double* __restrict__ t, double2* partial,
-                           LanczosState* st, int max_iter, DevStatus* status) {
+__global__ void k_mcg_band(GridDev g, const double* __restrict__ G, const double* __restrict__ r,
+                           const double* __restrict__ sv, const double* __restrict__ p_old,
+                           const double* __restrict__ q_old, double* __restrict__ p_new, double* __restrict__ q_new,
+                           double noise, double* __restrict__ t, double2* partial, LanczosState* st, int max_iter,
+                           DevStatus* status) {
   constexpr int B = Band<D>::B;
   __shared__ DotAccD red[32];
   if (st->cg_done) return;
+  const double be = st->cg_beta;
   DotAccD api;
   api.zero();
   for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < g.m;
@@ -1357,12 +1400,16 @@ __global__ void k_mcg_band(GridDev g, const double* __restrict__ G, const double
       if (D == 2) in = in && a1 >= 0 && a1 < g.g[1];
       if (in) {
         const int64_t nb = D == 1 ? a0 : (int64_t)a0 * g.stride[0] + a1;
-        gq = fma(G[(int64_t)o * g.m + node], q[nb], gq);
+        gq = fma(G[(int64_t)o * g.m + node], fma(be, q_old[nb], sv[nb]), gq);
       }
     }
-    const double tv = gq + noise * pv[node];
+    const double pn = fma(be, p_old[node], r[node]);
+    const double qn = fma(be, q_old[node], sv[node]);
+    p_new[node] = pn;
+    q_new[node] = qn;
+    const double tv = gq + noise * pn;
     t[node] = tv;
-    api.add_prod(q[node], tv);
+    api.add_prod(qn, tv);
   }
   block_merge(api, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, api);
@@ -1414,17 +1461,6 @@ __global__ void k_mcg_update(int64_t m, double* __restrict__ w, double* __restri
   }
 }
 
-// p = r + beta p;  q = s + beta q
-__global__ void k_mcg_dir(int64_t m, double* __restrict__ pv, double* __restrict__ q, const double* __restrict__ r,
-                          const double* __restrict__ sv, const LanczosState* st) {
-  if (st->cg_done) return;
-  const double be = st->cg_beta;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    pv[i] = fma(be, pv[i], r[i]);
-    q[i] = fma(be, q[i], sv[i]);
-  }
-}
-
 // |y|^2 -> the stopping threshold tol^2 s^2 |y|^2
 template <typename T>
 __global__ void k_mcg_ynorm(int64_t n, const T* __restrict__ y, double* __restrict__ yd, double tol, double noise,
@@ -1449,7 +1485,8 @@ __global__ void k_mcg_ynorm(int64_t n, const T* __restrict__ y, double* __restri
   }
 }
 
-// r = b, p = b, q = s = K b, w = 0;  rho = r . s
+// r = b, s = K b, w = 0, p' = q' = 0 (so the first direction is p = r, q = s);
+// rho = r . s
 __global__ void k_mcg_start(int64_t m, const double* __restrict__ b, const double* __restrict__ Kb,
                             double* __restrict__ r, double* __restrict__ pv, double* __restrict__ sv,
                             double* __restrict__ q, double* __restrict__ w, double2* partial, LanczosState* st) {
@@ -1458,9 +1495,9 @@ __global__ void k_mcg_start(int64_t m, const double* __restrict__ b, const doubl
   a.zero();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     r[i] = b[i];
-    pv[i] = b[i];
+    pv[i] = 0.0;
     sv[i] = Kb[i];
-    q[i] = Kb[i];
+    q[i] = 0.0;
     w[i] = 0.0;
     a.add_prod(b[i], Kb[i]);
   }
@@ -1490,12 +1527,14 @@ love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int
   size_t fwb = fft_work_bytes(gh, ski->fft, 1, true);
   const bool conv = sizeof(T) != sizeof(double);
   if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * 2048) || !Gb.get(sizeof(double) * B * m) ||
-      !vec.get(sizeof(double) * 7 * m) || (conv && !yb.get(sizeof(double) * std::max<int64_t>(n, 1))) ||
+      !vec.get(sizeof(double) * 9 * m) || (conv && !yb.get(sizeof(double) * std::max<int64_t>(n, 1))) ||
       !fw.get(std::max<size_t>(fwb, 16)))
     return LOVE_ERR_OOM;
   LanczosState* st = stb.as<LanczosState>();
   double* v = vec.as<double>();
-  double *b = v, *r = v + m, *pv = v + 2 * m, *sv = v + 3 * m, *q = v + 4 * m, *t = v + 5 * m, *Kt = v + 6 * m;
+  double *b = v, *r = v + m, *sv = v + 2 * m, *t = v + 3 * m, *Kt = v + 4 * m;
+  double* pbuf[2] = {v + 5 * m, v + 6 * m};  // directions p, q: double-buffered
+  double* qbuf[2] = {v + 7 * m, v + 8 * m};
   double* w = a;  // a = K z accumulates in place
   double2* pp = part.as<double2>();
   const int sblocks = (int)std::min<int64_t>((m * 32 + 255) / 256, (int64_t)num_sms() * 16);
@@ -1513,22 +1552,29 @@ love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int
   LOVE_COUNT_LAUNCH();
   k_mcg_ynorm<T><<<nblocks, 256, 0, s>>>(n, (const T*)ski->ys, conv ? yb.as<double>() : nullptr, tol, gh.noise, pp, st);
   LOVE_LAUNCH_CHECK();
+  // K products in FP64 transforms: with FP32 transforms (error ~log2(N) 2^-24)
+  // the K-inner product loses positivity on the high-frequency components and
+  // the iteration stops early (mean errors ~6e-3 std(y) on the n = 1e6 workload)
+  auto kmul = [&](const double* in, double* out) -> love_status {
+    return kuu_apply<double>(gh, ski->fft, in, out, 1, m, fw.p, -1, s);
+  };
   LOVE_TRY(scatter_any<T, double>(ski, yd, nullptr, 1.0, b, s));
-  LOVE_TRY(kuu_apply<double>(gh, ski->fft, b, Kt, 1, m, fw.p, -1, s));
-  LOVE_COUNT_LAUNCH(); k_mcg_start<<<mblocks, 256, 0, s>>>(m, b, Kt, r, pv, sv, q, w, pp, st);
+  LOVE_TRY(kmul(b, Kt));
+  LOVE_COUNT_LAUNCH(); k_mcg_start<<<mblocks, 256, 0, s>>>(m, b, Kt, r, pbuf[0], sv, qbuf[0], w, pp, st);
   LOVE_LAUNCH_CHECK();
   int it = 0;
   const int chunk = 64;
   while (it <= max_iter) {
     for (int c = 0; c < chunk && it <= max_iter; ++c, ++it) {
+      const double *po = pbuf[it & 1], *qo = qbuf[it & 1];
+      double *pn = pbuf[(it + 1) & 1], *qn = qbuf[(it + 1) & 1];
       if (dim == 1) {
-        LOVE_COUNT_LAUNCH(); k_mcg_band<1><<<mblocks, 256, 0, s>>>(g, Gb.as<double>(), q, pv, gh.noise, t, pp, st, max_iter, ski->status);
+        LOVE_COUNT_LAUNCH(); k_mcg_band<1><<<mblocks, 256, 0, s>>>(g, Gb.as<double>(), r, sv, po, qo, pn, qn, gh.noise, t, pp, st, max_iter, ski->status);
       } else {
-        LOVE_COUNT_LAUNCH(); k_mcg_band<2><<<mblocks, 256, 0, s>>>(g, Gb.as<double>(), q, pv, gh.noise, t, pp, st, max_iter, ski->status);
+        LOVE_COUNT_LAUNCH(); k_mcg_band<2><<<mblocks, 256, 0, s>>>(g, Gb.as<double>(), r, sv, po, qo, pn, qn, gh.noise, t, pp, st, max_iter, ski->status);
       }
-      LOVE_TRY(kuu_apply<double>(gh, ski->fft, t, Kt, 1, m, fw.p, -1, s));
-      LOVE_COUNT_LAUNCH(); k_mcg_update<<<mblocks, 256, 0, s>>>(m, w, r, sv, q, t, Kt, pp, st, ski->status);
-      LOVE_COUNT_LAUNCH(); k_mcg_dir<<<mblocks, 256, 0, s>>>(m, pv, q, r, sv, st);
+      LOVE_TRY(kmul(t, Kt));
+      LOVE_COUNT_LAUNCH(); k_mcg_update<<<mblocks, 256, 0, s>>>(m, w, r, sv, qn, t, Kt, pp, st, ski->status);
       LOVE_LAUNCH_CHECK();
     }
     int done = 0;
@@ -1623,6 +1669,27 @@ template love_status scatter_multi<float>(love_ski*, const float*, int64_t, int,
 template love_status scatter_multi<double>(love_ski*, const double*, int64_t, int, double*, int64_t, cudaStream_t);
 template love_status cg_solve<float>(love_ski*, const float*, double*, double, int, int*, cudaStream_t);
 template love_status cg_solve<double>(love_ski*, const double*, double*, double, int, int*, cudaStream_t);
+// mean column of the packed cache: Rc[r, k] = a[r] (cache dtype)
+template <typename OutT>
+__global__ void k_set_mean_col(const double* __restrict__ a, int64_t m, int k, OutT* __restrict__ out, int ld) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  if constexpr (std::is_same<OutT, __nv_bfloat16>::value) out[r * ld + k] = __double2bfloat16(a[r]);
+  else out[r * ld + k] = (OutT)a[r];
+}
+love_status cache_set_mean(love_cache* c, const double* a, cudaStream_t s) {
+  const int64_t m = c->grid.m;
+  const int blocks = ceil_div(m, 256);
+  LOVE_COUNT_LAUNCH();
+  if (c->cache_dtype == LOVE_BF16)
+    k_set_mean_col<__nv_bfloat16><<<blocks, 256, 0, s>>>(a, m, c->k_eff, (__nv_bfloat16*)c->Rc, c->ld);
+  else if (c->cache_dtype == LOVE_F64)
+    k_set_mean_col<double><<<blocks, 256, 0, s>>>(a, m, c->k_eff, (double*)c->Rc, c->ld);
+  else
+    k_set_mean_col<float><<<blocks, 256, 0, s>>>(a, m, c->k_eff, (float*)c->Rc, c->ld);
+  return cuda_check(cudaGetLastError());
+}
+
 template love_status build_cache<float>(love_ski*, love_cache*, const float*, int64_t, const double*, cudaStream_t,
                                         float*, const double*);
 template love_status build_cache<double>(love_ski*, love_cache*, const double*, int64_t, const double*,
@@ -1725,7 +1792,6 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
   ta.n_pad = m_pad;
   ta.kcols = ks;
   ta.bc = bc;
-  LOVE_TRY(make_qmap<double>(Q, ldq, ks, bc, &ta.qmap));
   ta.Q = Q;
   ta.ldq = ldq;
   ta.y = y.as<double>();

@@ -17,6 +17,8 @@
 // p - |v|^2 (var/p ~ 1e-7 on the 1-D, n = 1e6 workload) is taken without
 // losing the variance's leading digits.  The 16 prior products of the 1-D
 // stencil are spread over the group's lanes and folded into the same sum.
+#include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "love_internal.cuh"
@@ -35,6 +37,7 @@ struct PredArgs {
   int k;           // variance columns
   int has_mean;
   int exact_prior;
+  int root;        // variance from the posterior root: +|S^T w|^2, no prior term
   double sf;
   df cl[LOVE_MAX_DIM][4];      // Toeplitz entries T_e[0..3] (s_f folded into e = 0), double-float
   double cld[LOVE_MAX_DIM][4];
@@ -98,9 +101,53 @@ __device__ __forceinline__ double local_quad_d(const double* w, const double* c)
   return r;
 }
 
+// acc[0..VC) = sum over the 4^D stencil rows r of w_r * (column group cg of row r)
+template <typename CT, typename R, int D>
+__device__ __forceinline__ void gather_rows(const PredArgs& a, const typename VecOf<CT>::type* __restrict__ base_ptr,
+                                            int NG, const int (&base)[D], const R (&w)[D][4], bool ok, int cg,
+                                            R (&acc)[VecOf<CT>::n]) {
+  using V = typename VecOf<CT>::type;
+  constexpr int VC = VecOf<CT>::n;
+#pragma unroll
+  for (int c = 0; c < VC; ++c) acc[c] = R(0);
+  if (!ok) return;
+  if (D == 1) {
+    // small outer Keys weights first, so the two large terms are added last
+    const V* p = base_ptr + (int64_t)(base[0] - 1) * NG + cg;
+    const V r0 = ldg_vec(p), r1 = ldg_vec(p + NG), r2 = ldg_vec(p + 2 * NG), r3 = ldg_vec(p + 3 * NG);
+    vec_fma(acc, r3, w[0][3]);
+    vec_fma(acc, r0, w[0][0]);
+    vec_fma(acc, r2, w[0][2]);
+    vec_fma(acc, r1, w[0][1]);
+  } else if (D == 2) {
+#pragma unroll
+    for (int r0 = 0; r0 < 4; ++r0) {
+      const int64_t row0 = (int64_t)(base[0] - 1 + r0) * a.g.stride[0] + (base[D - 1] - 1);
+#pragma unroll
+      for (int r1 = 0; r1 < 4; ++r1)
+        vec_fma(acc, ldg_vec(base_ptr + (row0 + r1) * NG + cg), w[0][r0] * w[D - 1][r1]);
+    }
+  } else {
+#pragma unroll
+    for (int r0 = 0; r0 < 4; ++r0)
+#pragma unroll
+      for (int r1 = 0; r1 < 4; ++r1) {
+        const int64_t row0 = (int64_t)(base[0] - 1 + r0) * a.g.stride[0] +
+                             (int64_t)(base[1] - 1 + r1) * a.g.stride[1] + (base[D - 1] - 1);
+        const R w01 = w[0][r0] * w[1][r1];
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2)
+          vec_fma(acc, ldg_vec(base_ptr + (row0 + r2) * NG + cg), w01 * w[D - 1][r2]);
+      }
+  }
+}
+
 // G lanes per point.  R = arithmetic type (float for F32/BF16 caches, double for F64).
+// Serves points [.., a.t): the calling warp's first point is warp_first + lane / G
+// and every group advances by gstride, so all groups of a warp iterate the same
+// number of times (uniform shuffles).
 template <typename CT, typename R, int D, int G>
-__global__ void __launch_bounds__(256) k_predict(PredArgs a) {
+__device__ __forceinline__ void predict_groups(const PredArgs& a, int64_t warp_first, int64_t gstride) {
   using V = typename VecOf<CT>::type;
   constexpr int VC = VecOf<CT>::n;
   constexpr int NROW = D == 1 ? 4 : (D == 2 ? 16 : 64);
@@ -110,11 +157,6 @@ __global__ void __launch_bounds__(256) k_predict(PredArgs a) {
   const int NG = a.ld / VC;
   const V* __restrict__ base_ptr = reinterpret_cast<const V*>(a.Rc);
   const R* __restrict__ xs = reinterpret_cast<const R*>(a.x);
-  const int64_t groups_per_block = blockDim.x / G;
-  const int64_t gid0 = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / G;
-  const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
-  // all groups of a warp iterate the same number of times (uniform shuffles)
-  const int64_t warp_first = gid0 - (lane / G);
   for (int64_t pt0 = warp_first; pt0 < a.t; pt0 += gstride) {
     const int64_t pt = pt0 + lane / G;
     const bool live = pt < a.t;
@@ -133,50 +175,25 @@ __global__ void __launch_bounds__(256) k_predict(PredArgs a) {
     bool has_mu = false;
     for (int cg = li; cg < NG; cg += G) {
       R acc[VC];
+      gather_rows<CT, R, D>(a, base_ptr, NG, base, w, ok, cg, acc);
+      if ((cg + 1) * VC <= a.k) {
+        // a group of variance columns only (all but the last one or two)
 #pragma unroll
-      for (int c = 0; c < VC; ++c) acc[c] = R(0);
-      if (ok) {
-        if (D == 1) {
-          // small outer Keys weights first, so the two large terms are added last
-          const V* p = base_ptr + (int64_t)(base[0] - 1) * NG + cg;
-          const V r0 = ldg_vec(p), r1 = ldg_vec(p + NG), r2 = ldg_vec(p + 2 * NG), r3 = ldg_vec(p + 3 * NG);
-          vec_fma(acc, r3, w[0][3]);
-          vec_fma(acc, r0, w[0][0]);
-          vec_fma(acc, r2, w[0][2]);
-          vec_fma(acc, r1, w[0][1]);
-        } else if (D == 2) {
+        for (int c = 0; c < VC; ++c) sq = fma(acc[c], acc[c], sq);
+      } else {
 #pragma unroll
-          for (int r0 = 0; r0 < 4; ++r0) {
-            const int64_t row0 = (int64_t)(base[0] - 1 + r0) * a.g.stride[0] + (base[1] - 1);
-#pragma unroll
-            for (int r1 = 0; r1 < 4; ++r1)
-              vec_fma(acc, ldg_vec(base_ptr + (row0 + r1) * NG + cg), w[0][r0] * w[1][r1]);
-          }
-        } else {
-#pragma unroll
-          for (int r0 = 0; r0 < 4; ++r0)
-#pragma unroll
-            for (int r1 = 0; r1 < 4; ++r1) {
-              const int64_t row0 = (int64_t)(base[0] - 1 + r0) * a.g.stride[0] +
-                                   (int64_t)(base[1] - 1 + r1) * a.g.stride[1] + (base[2] - 1);
-              const R w01 = w[0][r0] * w[1][r1];
-#pragma unroll
-              for (int r2 = 0; r2 < 4; ++r2) vec_fma(acc, ldg_vec(base_ptr + (row0 + r2) * NG + cg), w01 * w[2][r2]);
-            }
+        for (int c = 0; c < VC; ++c) {
+          const int col = cg * VC + c;
+          if (col < a.k) sq = fma(acc[c], acc[c], sq);
+          else if (col == a.k) { mu = acc[c]; has_mu = true; }
         }
-      }
-#pragma unroll
-      for (int c = 0; c < VC; ++c) {
-        const int col = cg * VC + c;
-        if (col < a.k) sq = fma(acc[c], acc[c], sq);
-        else if (col == a.k) { mu = acc[c]; has_mu = true; }
       }
     }
     (void)NROW;
     // group sum of (prior terms - squares)
     if constexpr (std::is_same<R, float>::value) {
-      df tot = {-sq, 0.f};
-      if (ok) {
+      df tot = {a.root ? sq : -sq, 0.f};
+      if (ok && !a.root) {
         if (a.exact_prior) {
           if (li == 0) tot = df_add(tot, df_from_double(a.sf));
         } else if (D == 1) {
@@ -216,8 +233,8 @@ __global__ void __launch_bounds__(256) k_predict(PredArgs a) {
       }
       if (live && ok && has_mu && a.has_mean) reinterpret_cast<float*>(a.mean)[pt] = (float)mu;
     } else {
-      double tot = -(double)sq;
-      if (ok && li == 0) {
+      double tot = a.root ? (double)sq : -(double)sq;
+      if (ok && li == 0 && !a.root) {
         if (a.exact_prior) {
           tot += a.sf;
         } else {
@@ -252,6 +269,42 @@ __global__ void __launch_bounds__(256) k_predict(PredArgs a) {
 }
 
 template <typename CT, typename R, int D, int G>
+__global__ void __launch_bounds__(256, D == 3 ? 2 : 4) k_predict(PredArgs a) {
+  const int64_t groups_per_block = blockDim.x / G;
+  const int64_t gid0 = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / G;
+  predict_groups<CT, R, D, G>(a, gid0 - ((threadIdx.x & 31) / G), (int64_t)gridDim.x * groups_per_block);
+}
+
+// Batched form: a persistent grid walks a list of row chunks, each inside one
+// GP; the CTA copies that GP's descriptor to shared memory, points it at the
+// GP's rows of the concatenated x / mean / var, and serves the chunk.
+template <typename CT, typename R, int D, int G>
+__global__ void __launch_bounds__(256, D == 3 ? 2 : 4) k_predict_batched(const PredArgs* __restrict__ descs,
+                                                         const int64_t* __restrict__ t_off,
+                                                         const PredChunk* __restrict__ chunks, int nchunks,
+                                                         const void* x, void* mean, void* var) {
+  __shared__ PredArgs sa;
+  __shared__ int64_t begin;
+  const int64_t groups_per_block = blockDim.x / G;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const PredChunk ch = chunks[c];
+      sa = descs[ch.gp];
+      const int64_t off = t_off[ch.gp];
+      sa.x = reinterpret_cast<const R*>(x) + off * D;
+      sa.var = reinterpret_cast<R*>(var) + off;
+      sa.mean = mean ? reinterpret_cast<R*>(mean) + off : nullptr;
+      sa.has_mean = mean != nullptr;
+      sa.t = ch.end;
+      begin = ch.begin;
+    }
+    __syncthreads();
+    predict_groups<CT, R, D, G>(sa, begin + (threadIdx.x / 32) * (32 / G), groups_per_block);
+  }
+}
+
+template <typename CT, typename R, int D, int G>
 love_status launch_predict(const PredArgs& a, cudaStream_t s) {
   const int threads = 256;
   const int64_t groups = (a.t + 0);
@@ -263,10 +316,12 @@ love_status launch_predict(const PredArgs& a, cudaStream_t s) {
   return cuda_check(cudaGetLastError());
 }
 
+// lanes per point: 4 in 1-D (timed fastest of 4 / 8 / 16 on the 1-D n = 1e6
+// workload by the batch autotuner), 16 in 2-D, 32 in 3-D
 template <typename CT, typename R>
 love_status predict_dim(const PredArgs& a, cudaStream_t s) {
   switch (a.g.dim) {
-    case 1: return launch_predict<CT, R, 1, 8>(a, s);
+    case 1: return launch_predict<CT, R, 1, 4>(a, s);
     case 2: return launch_predict<CT, R, 2, 16>(a, s);
     default: return launch_predict<CT, R, 3, 32>(a, s);
   }
@@ -274,18 +329,13 @@ love_status predict_dim(const PredArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-love_status predict_launch(love_cache* c, int64_t t, const void* x, void* mean, void* var, cudaStream_t s) {
-  if (t == 0) return LOVE_OK;
+namespace {
+PredArgs make_pred_args(const love_cache* c) {
   PredArgs a{};
   a.g = c->grid.dev();
-  a.t = t;
-  a.x = x;
-  a.mean = mean;
-  a.var = var;
   a.Rc = c->Rc;
   a.ld = c->ld;
   a.k = c->k_eff;
-  a.has_mean = mean != nullptr;
   a.exact_prior = (c->flags & LOVE_PRIOR_EXACT) ? 1 : 0;
   a.sf = c->grid.sf;
   for (int e = 0; e < LOVE_MAX_DIM; ++e)
@@ -297,9 +347,81 @@ love_status predict_launch(love_cache* c, int64_t t, const void* x, void* mean, 
       a.cld[e][q] = v;
     }
   a.status = c->status;
+  return a;
+}
+
+template <typename CT, typename R, int D, int G>
+love_status launch_batched(const void* descs, const int64_t* toff, const PredChunk* chunks, int nchunks,
+                           int ctas_per_sm, const void* x, void* mean, void* var, cudaStream_t s) {
+  const int blocks = std::max(1, std::min(nchunks, ctas_per_sm * num_sms()));
+  LOVE_COUNT_LAUNCH();
+  k_predict_batched<CT, R, D, G><<<blocks, 256, 0, s>>>((const PredArgs*)descs, toff, chunks, nchunks, x, mean, var);
+  return cuda_check(cudaGetLastError());
+}
+template <typename CT, typename R>
+love_status batched_dim(int dim, int lanes, const void* descs, const int64_t* toff, const PredChunk* chunks,
+                        int nchunks, int ctas, const void* x, void* mean, void* var, cudaStream_t s) {
+#define LOVE_PB(D, G) \
+  if (dim == D && lanes == G) return launch_batched<CT, R, D, G>(descs, toff, chunks, nchunks, ctas, x, mean, var, s);
+  LOVE_PB(1, 4) LOVE_PB(1, 8) LOVE_PB(1, 16)
+  LOVE_PB(2, 8) LOVE_PB(2, 16) LOVE_PB(2, 32)
+  LOVE_PB(3, 8) LOVE_PB(3, 16) LOVE_PB(3, 32)
+#undef LOVE_PB
+  return LOVE_ERR_ARG;
+}
+}  // namespace
+
+love_status predict_launch(love_cache* c, int64_t t, const void* x, void* mean, void* var, cudaStream_t s) {
+  if (t == 0) return LOVE_OK;
+  PredArgs a = make_pred_args(c);
+  a.t = t;
+  a.x = x;
+  a.mean = mean;
+  a.var = var;
+  a.has_mean = mean != nullptr;
   if (c->dtype == LOVE_F64) return predict_dim<double, double>(a, s);
   if (c->cache_dtype == LOVE_BF16) return predict_dim<__nv_bfloat16, float>(a, s);
   return predict_dim<float, float>(a, s);
+}
+
+// var = |S^T w*|^2 from the sampler root S (m x ld_s rows in the data dtype)
+love_status predict_root_launch(love_cache* c, int64_t t, const void* x, void* var, cudaStream_t s) {
+  if (t == 0) return LOVE_OK;
+  PredArgs a = make_pred_args(c);
+  a.Rc = c->S;
+  a.ld = c->ld_s;
+  a.k = c->ks;
+  a.has_mean = 0;
+  a.root = 1;
+  a.t = t;
+  a.x = x;
+  a.mean = nullptr;
+  a.var = var;
+  if (c->dtype == LOVE_F64) return predict_dim<double, double>(a, s);
+  return predict_dim<float, float>(a, s);
+}
+
+size_t predict_desc_bytes() { return sizeof(PredArgs); }
+void predict_fill_desc(const love_cache* c, void* dst) {
+  PredArgs a = make_pred_args(c);
+  std::memcpy(dst, &a, sizeof(PredArgs));
+}
+int predict_lane_candidates(int dim, int* out) {
+  static const int c1[] = {4, 8, 16}, c2[] = {8, 16, 32}, c3[] = {8, 16, 32};
+  const int* c = dim == 1 ? c1 : (dim == 2 ? c2 : c3);
+  const int n = 3;
+  for (int i = 0; i < n; ++i) out[i] = c[i];
+  return n;
+}
+love_status predict_batched_launch(const void* descs, const int64_t* toff, const PredChunk* chunks, int nchunks,
+                                   int dim, love_dtype dtype, love_dtype cache_dtype, int lanes, int ctas_per_sm,
+                                   const void* x, void* mean, void* var, cudaStream_t s) {
+  if (nchunks == 0) return LOVE_OK;
+  if (dtype == LOVE_F64)
+    return batched_dim<double, double>(dim, lanes, descs, toff, chunks, nchunks, ctas_per_sm, x, mean, var, s);
+  if (cache_dtype == LOVE_BF16)
+    return batched_dim<__nv_bfloat16, float>(dim, lanes, descs, toff, chunks, nchunks, ctas_per_sm, x, mean, var, s);
+  return batched_dim<float, float>(dim, lanes, descs, toff, chunks, nchunks, ctas_per_sm, x, mean, var, s);
 }
 
 }  // namespace love

@@ -17,16 +17,13 @@
 #include <cmath>
 #include <vector>
 
+#include <type_traits>
+
 #include "love_internal.cuh"
 
 namespace love {
 namespace {
 
-template <typename K>
-love_status allow_smem_s(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return LOVE_OK;
-  return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
 
 // l_11 = sqrt(alpha_1), e_j = beta_j / l_jj, l_{j+1,j+1} = sqrt(alpha_{j+1} - e_j^2)
 __global__ void k_chol_tri(const double* alpha, const double* beta, int k, double* d, double* e, int* ok) {
@@ -349,6 +346,109 @@ __global__ void __launch_bounds__(256) k_sample_gemm(const T* __restrict__ G, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same product on the tensor cores for FP32 data (Sec. 3.3, eq. sample:
+// F = mu + W*^T S Z is a dense t x k_s by k_s x s contraction).  Each FP32
+// operand is split into two TF32 parts, x = hi + lo (hi = x rounded to TF32,
+// lo = the rounded remainder), and each product is accumulated as
+// lo*hi + hi*lo + hi*hi in FP32 (the lo*lo term, ~2^-22 relative, is dropped):
+// close to FP32 accuracy on the TF32 tensor path.  mma.sync m16n8k8 (TF32 in,
+// FP32 accumulate); CTA tile 128 points x 64 samples, 8 warps of 32 x 32,
+// k in chunks of 32 staged through shared memory.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int TCM = 128, TCN = 64, TCK = 32;
+__global__ void __launch_bounds__(256) k_sample_gemm_tc(const float* __restrict__ G, int ld_g,
+                                                        const float* __restrict__ Z, int s, int ks,
+                                                        const float* __restrict__ mu, int64_t t,
+                                                        float* __restrict__ F) {
+  __shared__ float Gs[TCM][TCK + 4];   // row stride 36: fragment loads hit 32 distinct banks
+  __shared__ float Zs[TCK][TCN + 8];   // row stride 72: likewise
+  const int64_t i0 = (int64_t)blockIdx.x * TCM;
+  const int j0 = blockIdx.y * TCN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;   // this warp's 32 x 32 sub-tile
+  float acc[2][4][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+  for (int c0 = 0; c0 < ks; c0 += TCK) {
+    // stage G[i0 .. +128, c0 .. +32] and Z[c0 .. +32, j0 .. +64], zero outside
+    for (int idx = threadIdx.x; idx < TCM * TCK; idx += 256) {
+      const int ii = idx / TCK, cc = idx % TCK;
+      const int64_t i = i0 + ii;
+      Gs[ii][cc] = (i < t && c0 + cc < ks) ? G[i * ld_g + c0 + cc] : 0.f;
+    }
+    for (int idx = threadIdx.x; idx < TCK * TCN; idx += 256) {
+      const int cc = idx / TCN, jj = idx % TCN;
+      Zs[cc][jj] = (c0 + cc < ks && j0 + jj < s) ? Z[(int64_t)(c0 + cc) * s + j0 + jj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k8 = 0; k8 < TCK; k8 += 8) {
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int r = wm + 16 * a + gid;
+        split_tf32(Gs[r][k8 + tig], ah[a][0], al[a][0]);
+        split_tf32(Gs[r + 8][k8 + tig], ah[a][1], al[a][1]);
+        split_tf32(Gs[r][k8 + tig + 4], ah[a][2], al[a][2]);
+        split_tf32(Gs[r + 8][k8 + tig + 4], ah[a][3], al[a][3]);
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int cidx = wn + 8 * b + gid;
+        split_tf32(Zs[k8 + tig][cidx], bh[b][0], bl[b][0]);
+        split_tf32(Zs[k8 + tig + 4][cidx], bh[b][1], bl[b][1]);
+      }
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          mma_tf32(acc[a][b], al[a], bh[b]);
+          mma_tf32(acc[a][b], ah[a], bl[b]);
+          mma_tf32(acc[a][b], ah[a], bh[b]);
+        }
+    }
+    __syncthreads();
+  }
+  // accumulator (row = point, column = sample): q = 0, 1 -> (gid, 2 tig + q), q = 2, 3 -> (gid + 8, 2 tig + q - 2)
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = i0 + wm + 16 * a + gid + 8 * h;
+      if (i >= t) continue;
+      const float m_ = mu[i];
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int j = j0 + wn + 8 * b + 2 * tig + q;
+          if (j < s) F[(int64_t)j * t + i] = m_ + acc[a][b][2 * h + q];
+        }
+    }
+}
+
 // Philox4x32-10: 10 rounds of (hi0,lo0) = M0 x0, (hi1,lo1) = M1 x2,
 // x <- (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0), key += Weyl constants between rounds.
 __device__ __forceinline__ void philox4x32_10(uint32_t x[4], uint32_t k0, uint32_t k1) {
@@ -452,7 +552,7 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
     const int np = keff + (keff & 1);
     size_t sm = sizeof(float) * (2 * (size_t)np * np + 2 * np);
     if (sm > 220 * 1024) return LOVE_ERR_UNSUPPORTED;   // k' > ~165
-    LOVE_TRY(allow_smem_s(k_jacobi_par, sm));
+    LOVE_TRY(allow_smem(k_jacobi_par, sm));
     double* lam = B.as<double>();                        // first n entries of B as scratch
     Buf L(al, s);
     if (!L.get(sizeof(double) * keff)) return LOVE_ERR_OOM;
@@ -460,7 +560,7 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
     LOVE_COUNT_LAUNCH(); k_scale_eig<<<ceil_div(nn, 256), 256, 0, s>>>(L.as<double>(), V.as<double>(), keff, B.as<double>());
     (void)lam;
     size_t smb = sizeof(T) * nn;
-    LOVE_TRY(allow_smem_s(k_root_from_eig<T>, smb));
+    LOVE_TRY(allow_smem(k_root_from_eig<T>, smb));
     LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<double>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);
     LOVE_LAUNCH_CHECK();
     LOVE_CUDA(cudaStreamSynchronize(s));
@@ -474,22 +574,45 @@ template love_status sampler_build<float>(love_ski*, love_cache*, const float*, 
 template love_status sampler_build<double>(love_ski*, love_cache*, const double*, int, uint64_t, double,
                                            cudaStream_t);
 
+static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+template <typename T>
+static size_t sample_ws_bytes_t(const love_cache* c, int64_t t, int s_count) {
+  const int vec = 16 / (int)sizeof(T);
+  const int ld_g = (c->ks + vec - 1) / vec * vec;
+  return round256(sizeof(T) * (size_t)t * ld_g) + round256(sizeof(T) * (size_t)t) +
+         round256(sizeof(T) * (size_t)c->ks * s_count);
+}
+
+// ws: optional work space of sample_ws_bytes_t bytes (then nothing is allocated)
 template <typename T>
 static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_count, const void* z, uint64_t seed,
-                               void* out, cudaStream_t s) {
+                               void* out, cudaStream_t s, void* ws = nullptr) {
   const Allocator& al = c->alloc;
   const int ks = c->ks;
   const int vec = 16 / (int)sizeof(T);
   const int ld_g = (ks + vec - 1) / vec * vec;
   Buf Gb(al, s), mub(al, s), zb(al, s);
-  if (!Gb.get(sizeof(T) * (size_t)t * ld_g) || !mub.get(sizeof(T) * (size_t)t)) return LOVE_ERR_OOM;
+  T *Gp, *mup, *zp = nullptr;
+  if (ws) {
+    char* w = (char*)ws;
+    Gp = (T*)w;
+    mup = (T*)(w + round256(sizeof(T) * (size_t)t * ld_g));
+    zp = (T*)((char*)mup + round256(sizeof(T) * (size_t)t));
+  } else {
+    if (!Gb.get(sizeof(T) * (size_t)t * ld_g) || !mub.get(sizeof(T) * (size_t)t)) return LOVE_ERR_OOM;
+    Gp = Gb.as<T>();
+    mup = mub.as<T>();
+  }
   const T* Z = (const T*)z;
   if (!Z) {
     int64_t cnt = (int64_t)ks * s_count;
-    if (!zb.get(sizeof(T) * cnt)) return LOVE_ERR_OOM;
+    if (!zp) {
+      if (!zb.get(sizeof(T) * cnt)) return LOVE_ERR_OOM;
+      zp = zb.as<T>();
+    }
     int64_t blocks4 = (cnt + 3) / 4;
-    LOVE_COUNT_LAUNCH(); k_philox_normals<T><<<ceil_div(blocks4, 256), 256, 0, s>>>(cnt, seed, zb.as<T>());
-    Z = zb.as<T>();
+    LOVE_COUNT_LAUNCH(); k_philox_normals<T><<<ceil_div(blocks4, 256), 256, 0, s>>>(cnt, seed, zp);
+    Z = zp;
   }
   SampleGatherArgs a{};
   a.g = c->grid.dev();
@@ -502,9 +625,9 @@ static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_co
   a.ld_c = c->ld;
   a.kc = c->k_eff;
   a.cache_dtype = c->cache_dtype;
-  a.G = Gb.p;
+  a.G = Gp;
   a.ld_g = ld_g;
-  a.mu = mub.p;
+  a.mu = mup;
   a.status = c->status;
   int blocks = (int)std::min<int64_t>((t * 32 + 255) / 256, (int64_t)num_sms() * 16);
   switch (a.g.dim) {
@@ -512,8 +635,13 @@ static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_co
     case 2: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 2><<<blocks, 256, 0, s>>>(a); break;
     default: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 3><<<blocks, 256, 0, s>>>(a);
   }
-  dim3 grid((unsigned)((t + 63) / 64), (unsigned)((s_count + 63) / 64));
-  LOVE_COUNT_LAUNCH(); k_sample_gemm<T><<<grid, 256, 0, s>>>(Gb.as<T>(), ld_g, Z, s_count, ks, mub.as<T>(), t, (T*)out);
+  if constexpr (std::is_same<T, float>::value) {
+    dim3 grid((unsigned)((t + TCM - 1) / TCM), (unsigned)((s_count + TCN - 1) / TCN));
+    LOVE_COUNT_LAUNCH(); k_sample_gemm_tc<<<grid, 256, 0, s>>>(Gp, ld_g, Z, s_count, ks, mup, t, (float*)out);
+  } else {
+    dim3 grid((unsigned)((t + 63) / 64), (unsigned)((s_count + 63) / 64));
+    LOVE_COUNT_LAUNCH(); k_sample_gemm<T><<<grid, 256, 0, s>>>(Gp, ld_g, Z, s_count, ks, mup, t, (T*)out);
+  }
   return cuda_check(cudaGetLastError());
 }
 
@@ -521,6 +649,22 @@ love_status sample_launch(love_cache* c, int64_t t, const void* x, int s_count, 
                           void* out, cudaStream_t s) {
   if (c->dtype == LOVE_F64) return sample_impl<double>(c, t, x, s_count, z, seed, out, s);
   return sample_impl<float>(c, t, x, s_count, z, seed, out, s);
+}
+
+size_t sample_ws_bytes(const love_cache* c, int64_t t, int s_count) {
+  return c->dtype == LOVE_F64 ? sample_ws_bytes_t<double>(c, t, s_count) : sample_ws_bytes_t<float>(c, t, s_count);
+}
+love_status sample_launch_z_ws(love_cache* c, int64_t t, const void* x, int s_count, const void* z, uint64_t seed,
+                               void* out, void* ws, cudaStream_t s) {
+  if (t == 0 || s_count == 0) return LOVE_OK;
+  if (c->dtype == LOVE_F64) return sample_impl<double>(c, t, x, s_count, z, seed, out, s, ws);
+  return sample_impl<float>(c, t, x, s_count, z, seed, out, s, ws);
+}
+love_status sample_launch_ws(love_cache* c, int64_t t, const void* x, int s_count, uint64_t seed, void* out,
+                             void* ws, cudaStream_t s) {
+  if (t == 0 || s_count == 0) return LOVE_OK;
+  if (c->dtype == LOVE_F64) return sample_impl<double>(c, t, x, s_count, nullptr, seed, out, s, ws);
+  return sample_impl<float>(c, t, x, s_count, nullptr, seed, out, s, ws);
 }
 
 }  // namespace love

@@ -12,6 +12,9 @@
 #include <new>
 #include <vector>
 
+#include <mutex>
+#include <thread>
+
 #include "love_internal.cuh"
 
 namespace love {
@@ -121,6 +124,23 @@ Allocator make_alloc(const love_allocator* a) {
 int round_up(int v, int q) { return (v + q - 1) / q * q; }
 
 // CUDA events around the pre-compute phases (reported by love_cache_info)
+// Auxiliary streams for work that overlaps a call's main stream (kept for the
+// process's lifetime, handed out round-robin).
+cudaStream_t aux_stream() {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> pool;
+  static unsigned next = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (pool.empty()) {
+    for (int i = 0; i < 16; ++i) {
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) pool.push_back(st);
+    }
+    if (pool.empty()) return nullptr;
+  }
+  return pool[next++ % pool.size()];
+}
+
 struct PhaseEvents {
   cudaEvent_t e[5] = {};
   bool ok = true;
@@ -152,6 +172,9 @@ void destroy_cache_buffers(love_cache* c, cudaStream_t s) {
   al.free(c->B, (size_t)c->grid.dim * c->k_eff * c->k_eff * dtype_size(c->dtype), s);
   al.free(c->Minv, (size_t)c->k_eff * c->k_eff * dtype_size(c->dtype), s);
   al.free(c->status, sizeof(DevStatus), s);
+  al.free(c->sws, c->sws_bytes, s);
+  c->sws = nullptr;
+  c->sws_bytes = 0;
   delete[] c->alpha;
   delete[] c->beta;
   c->Rc = c->S = c->P = c->KdP = c->B = c->Minv = nullptr;
@@ -361,6 +384,20 @@ love_status love_cache_destroy(love_cache_t c) {
 
 }  // extern "C"
 
+// The grid-space mean CG needs only the training data, not the Lanczos
+// basis, so it runs on an auxiliary stream, driven by its own host thread,
+// while the Lanczos, cache and sampler kernels run on the caller's stream;
+// its mean weights are written into the cache after both finish.
+struct MeanJob {
+  std::thread th;
+  love_status rc = LOVE_OK;
+  int iters = 0;
+  float ms = 0.f;
+  ~MeanJob() {
+    if (th.joinable()) th.join();
+  }
+};
+
 template <typename T>
 static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o, cudaStream_t s, love_cache** out,
                                    int* k_eff_out) {
@@ -368,10 +405,57 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   const Allocator& al = ski->alloc;
   int k = std::min<int64_t>(o->k, std::min<int64_t>(ski->n, g.m));
   double tau = o->breakdown_tol > 0 ? o->breakdown_tol : (sizeof(T) == 8 ? 1e-12 : 1e-8);
+  unsigned flags = o->flags;
+  if (!ski->ys) flags &= ~LOVE_WANT_MEAN;
+  const bool want_mean = (flags & LOVE_WANT_MEAN) != 0;
+  const bool grid_cg = want_mean && mean_grid_cg_supported(ski);
+  const double cg_tol = o->cg_tol > 0 ? o->cg_tol : (sizeof(T) == 8 ? 1e-12 : 1e-6);
+  const int cg_maxit = o->cg_max_iter > 0 ? o->cg_max_iter : 4000;
   const int64_t ldq = ski->n_pad;
   size_t qb = sizeof(T) * (size_t)ldq * k;
+  const size_t amb = sizeof(double) * (size_t)g.m;
+  double* am = nullptr;  // mean weights from the grid CG
+  if (grid_cg) {
+    am = (double*)al.alloc(amb, s);
+    if (!am) return LOVE_ERR_OOM;
+  }
   T* Q = (T*)al.alloc(qb, s);
-  if (!Q) return LOVE_ERR_OOM;
+  if (!Q) {
+    al.free(am, amb, s);
+    return LOVE_ERR_OOM;
+  }
+  MeanJob mj;
+  if (grid_cg) {
+    cudaStream_t s2 = aux_stream();
+    cudaEvent_t go = nullptr;
+    love_status erc = cuda_check(cudaEventCreateWithFlags(&go, cudaEventDisableTiming));
+    if (erc == LOVE_OK) erc = cuda_check(cudaEventRecord(go, s));
+    if (erc == LOVE_OK) erc = cuda_check(cudaStreamWaitEvent(s2, go, 0));
+    if (go) cudaEventDestroy(go);
+    if (erc != LOVE_OK) {
+      al.free(Q, qb, s);
+      al.free(am, amb, s);
+      return erc;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    mj.th = std::thread([ski, cg_tol, cg_maxit, am, s2, dev, &mj] {
+      cudaSetDevice(dev);
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s2);
+      mj.rc = mean_grid_cg<T>(ski, cg_tol, cg_maxit, am, &mj.iters, s2);
+      cudaEventRecord(e1, s2);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&mj.ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    });
+  }
+  auto join_mean = [&]() {
+    if (mj.th.joinable()) mj.th.join();
+  };
   std::vector<double> alpha(k + 1), beta(k + 1);
   int keff = 0;
   PhaseEvents ev;
@@ -379,7 +463,9 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   love_status rc = lanczos_run<T>(ski, k, tau, Q, ldq, alpha.data(), beta.data(), &keff, s);
   ev.record(1, s);
   if (rc != LOVE_OK) {
+    join_mean();
     al.free(Q, qb, s);
+    al.free(am, amb, s);
     return rc;
   }
   // status from the Lanczos kernels (NaN, timeout)
@@ -390,35 +476,28 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   else if (dst.bits & (1u << LOVE_ERR_NAN)) rc = LOVE_ERR_NAN;
   if (rc == LOVE_OK && keff < 1) rc = LOVE_ERR_NAN;
   if (rc != LOVE_OK) {
+    join_mean();
     cudaMemsetAsync(ski->status, 0, sizeof(DevStatus), s);
     al.free(Q, qb, s);
+    al.free(am, amb, s);
     return rc;
   }
-  unsigned flags = o->flags;
-  if (!ski->ys) flags &= ~LOVE_WANT_MEAN;
   love_cache* c = new_cache(g, ski->dtype, o->cache_dtype, flags, keff, al, s);
   if (!c) {
+    join_mean();
     al.free(Q, qb, s);
+    al.free(am, amb, s);
     return LOVE_ERR_OOM;
   }
   std::copy(alpha.begin(), alpha.begin() + keff, c->alpha);
   std::copy(beta.begin(), beta.begin() + std::max(keff - 1, 0), c->beta);
-  double* z = nullptr;       // K^^-1 y (n-space CG) ...
-  double* am = nullptr;      // ... or the mean weights directly (grid CG)
-  const bool grid_cg = mean_grid_cg_supported(ski);
-  size_t zb = sizeof(double) * (grid_cg ? (size_t)g.m : (size_t)ldq);
-  if (flags & LOVE_WANT_MEAN) {
-    double* buf = (double*)al.alloc(zb, s);
-    if (!buf) rc = LOVE_ERR_OOM;
-    double tol = o->cg_tol > 0 ? o->cg_tol : (sizeof(T) == 8 ? 1e-12 : 1e-6);
-    int maxit = o->cg_max_iter > 0 ? o->cg_max_iter : 4000;
-    if (grid_cg) {
-      am = buf;
-      if (rc == LOVE_OK) rc = mean_grid_cg<T>(ski, tol, maxit, am, &c->cg_iters, s);
-    } else {
-      z = buf;
-      if (rc == LOVE_OK) rc = cg_solve<T>(ski, (const T*)ski->ys, z, tol, maxit, &c->cg_iters, s);
-    }
+  // n-space mean CG (3-D grids), on this stream
+  double* z = nullptr;
+  const size_t zb = sizeof(double) * (size_t)ldq;
+  if (want_mean && !grid_cg) {
+    z = (double*)al.alloc(zb, s);
+    if (!z) rc = LOVE_ERR_OOM;
+    if (rc == LOVE_OK) rc = cg_solve<T>(ski, (const T*)ski->ys, z, cg_tol, cg_maxit, &c->cg_iters, s);
   }
   ev.record(2, s);
   if (rc == LOVE_OK && (flags & LOVE_WANT_GRAD)) {
@@ -431,11 +510,10 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     rt_keep = (T*)al.alloc(rtb, s);
     if (!rt_keep) rc = LOVE_ERR_OOM;
   }
-  if (rc == LOVE_OK) rc = build_cache<T>(ski, c, Q, ldq, z, s, rt_keep, am);
+  if (rc == LOVE_OK) rc = build_cache<T>(ski, c, Q, ldq, z, s, rt_keep, nullptr);
   if (rc == LOVE_OK && (flags & LOVE_WANT_GRAD)) rc = backward_tables(c, ski->fft, c->P, keff, s);
   ev.record(3, s);
   if (z) al.free(z, zb, s);
-  if (am) al.free(am, zb, s);
   al.free(Q, qb, s);
   if (rc == LOVE_OK && (flags & LOVE_WANT_SAMPLER)) {
     int ks = o->sampler_k > 0 ? o->sampler_k : o->k;
@@ -444,8 +522,19 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   }
   if (rt_keep) al.free(rt_keep, rtb, s);
   ev.record(4, s);
+  // the grid CG's mean weights into the cache's mean column
+  join_mean();
+  if (grid_cg) {
+    if (rc == LOVE_OK) rc = mj.rc;
+    c->cg_iters = mj.iters;
+    if (rc == LOVE_OK) rc = cache_set_mean(c, am, s);
+  }
   if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
-  if (rc == LOVE_OK) ev.elapsed(c->phase_ms);
+  al.free(am, amb, s);
+  if (rc == LOVE_OK) {
+    ev.elapsed(c->phase_ms);
+    if (grid_cg) c->phase_ms[1] = mj.ms;
+  }
   if (rc != LOVE_OK) {
     love_cache_destroy(c);
     return rc;
@@ -479,13 +568,29 @@ love_status love_predict_mean_var(love_cache_t c, int64_t t, const void* x_test,
   return predict_launch(c, t, x_test, mean, var, cs(stream));
 }
 
+love_status love_predict_var_root(love_cache_t c, int64_t t, const void* x_test, void* var, love_stream_t stream) {
+  if (!c || t < 0) return LOVE_ERR_ARG;
+  if (!c->S) return LOVE_ERR_STATE;
+  if (t == 0) return LOVE_OK;
+  if (!x_test || !var) return LOVE_ERR_ARG;
+  return predict_root_launch(c, t, x_test, var, cs(stream));
+}
+
 love_status love_sample(love_cache_t c, int64_t t, const void* x_test, int s_count, const void* z, uint64_t seed,
                         void* out, love_stream_t stream) {
   if (!c || t < 0 || s_count < 0) return LOVE_ERR_ARG;
   if (!c->S) return LOVE_ERR_STATE;
   if (t == 0 || s_count == 0) return LOVE_OK;
   if (!x_test || !out) return LOVE_ERR_ARG;
-  return sample_launch(c, t, x_test, s_count, z, seed, out, cs(stream));
+  // work space kept on the cache: no allocator call once it is large enough
+  const size_t need = sample_ws_bytes(c, t, s_count);
+  if (need > c->sws_bytes) {
+    c->alloc.free(c->sws, c->sws_bytes, cs(stream));
+    c->sws = c->alloc.alloc(need, cs(stream));
+    c->sws_bytes = c->sws ? need : 0;
+    if (!c->sws) return LOVE_ERR_OOM;
+  }
+  return sample_launch_z_ws(c, t, x_test, s_count, z, seed, out, c->sws, cs(stream));
 }
 
 love_status love_var_backward(love_cache_t c, int64_t t, const void* x_test, const void* grad_var, void* grad_x,

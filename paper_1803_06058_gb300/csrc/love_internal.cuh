@@ -177,6 +177,7 @@ struct DotAccF {
 };
 struct DotAccD {
   double s;
+  static constexpr double c = 0.0;
   __device__ __forceinline__ void zero() { s = 0.0; }
   __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ void add(double p) { s += p; }
@@ -318,6 +319,8 @@ struct love_cache {
   int sampler_fallback = 0;
   float phase_ms[4] = {0, 0, 0, 0};
   DevStatus* status = nullptr;
+  void* sws = nullptr;         // love_sample work space (grown on demand, kept)
+  size_t sws_bytes = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -355,6 +358,8 @@ love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_i
 bool mean_grid_cg_supported(const love_ski* ski);
 template <typename T>
 love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s);
+// write mean weights a (m, FP64) into the cache's mean column
+love_status cache_set_mean(love_cache* c, const double* a, cudaStream_t s);
 // zmean: K^^-1 y (n-vector, cell-sorted) or amean: the mean weights themselves
 template <typename T>
 love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, const double* zmean,
@@ -387,6 +392,7 @@ int predict_lane_candidates(int dim, int* out);
 love_status predict_batched_launch(const void* descs, const int64_t* toff, const PredChunk* chunks, int nchunks,
                                    int dim, love_dtype dtype, love_dtype cache_dtype, int lanes, int ctas_per_sm,
                                    const void* x, void* mean, void* var, cudaStream_t s);
+love_status predict_root_launch(love_cache* c, int64_t t, const void* x, void* var, cudaStream_t s);
 love_status predict_launch(love_cache* c, int64_t t, const void* x, void* mean, void* var,
                            cudaStream_t s);
 love_status backward_launch(love_cache* c, int64_t t, const void* x, const void* gv, void* gx,
@@ -401,6 +407,8 @@ love_status sample_launch(love_cache* c, int64_t t, const void* x, int s_count, 
 size_t sample_ws_bytes(const love_cache* c, int64_t t, int s_count);
 love_status sample_launch_ws(love_cache* c, int64_t t, const void* x, int s_count, uint64_t seed, void* out,
                              void* ws, cudaStream_t s);
+love_status sample_launch_z_ws(love_cache* c, int64_t t, const void* x, int s_count, const void* z, uint64_t seed,
+                               void* out, void* ws, cudaStream_t s);
 
 // api helpers
 extern thread_local int g_last_cuda_error;
@@ -410,6 +418,29 @@ inline love_status cuda_check(cudaError_t e) {
   if (e == cudaSuccess) return LOVE_OK;
   g_last_cuda_error = (int)e;
   return LOVE_ERR_CUDA;
+}
+
+// raise a kernel's dynamic shared-memory limit (above the 48 KB default)
+template <typename K>
+inline love_status allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return LOVE_OK;
+  // always raise the kernel's limit to the most it can take (the device's
+  // opt-in maximum less the kernel's static shared memory), not to `bytes`:
+  // concurrent host threads launching the same kernel with different sizes
+  // then never lower the limit under one another
+  static int limit = 0;
+  if (limit == 0) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return cuda_check(e);
+    const int l = optin - (int)fa.sharedSizeBytes;
+    limit = l > 48 * 1024 ? l : 48 * 1024;
+  }
+  if (bytes > (size_t)limit) return LOVE_ERR_UNSUPPORTED;
+  return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
 }
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 int num_sms();

@@ -135,3 +135,41 @@ def test_sample_edge_cases(love):
     bad = torch.tensor([[0.5], [2.0], [0.25]], device="cuda")
     F = love.love_sample(cache, bad, 4, seed=1).cpu().numpy()
     assert np.all(np.isnan(F[:, 1])) and np.all(np.isfinite(F[:, [0, 2]]))
+
+
+@pytest.mark.parametrize("dim,g", [(1, 50), (2, 16), (3, 8)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_variance_from_root_on_imported_root(love, dim, g, dtype):
+    """love_predict_var_root = |S^T w*|^2 against the oracle on the same
+    (rounded) root.  A sum of squares: relative error of a 4^d-row FP32 gather
+    and a k'-term FP32 sum, (4^d + k') 2^-24 < 1e-5; FP64 1e-12."""
+    from oracle import love as ol
+    wl = small_workload(dim=dim, g=g, n=1500, k=20, t=333, dtype=dtype, ls=0.25)
+    _, c_o = oracle_cache(wl)
+    S_o, _ = ol.sampler_precompute(c_o, k=24, seed=5)
+    rc = rounded_cache(c_o, dtype)
+    rc.S = np.asarray(np.asarray(S_o, np.float32 if dtype == "f32" else np.float64), np.float64)
+    dev = love.love_cache_import(wl.grid_size, wl.grid_lo, wl.grid_hi, wl.lengthscale, wl.outputscale,
+                                 wl.noise, rc.Rt, a=rc.a, S=rc.S, dtype=dtype)
+    xs = np.asarray(wl.x_test(), np.float32 if dtype == "f32" else np.float64)
+    v = love.love_predict_var_root(dev, torch.tensor(xs, device="cuda")).double().cpu().numpy()
+    v_o = ol.predict_root(rc, xs.astype(np.float64))
+    tol = 1e-5 if dtype == "f32" else 1e-12
+    np.testing.assert_allclose(v, v_o, rtol=tol, atol=tol * v_o.max() * 1e-3)
+
+
+def test_variance_from_root_pipeline_properties(love):
+    """FP32 pipeline with the sampler: 0 <= |S^T w*|^2 <= p, and without a
+    sampler the call is refused (LOVE_ERR_STATE)."""
+    from oracle import love as ol
+    from oracle import grid as og
+    wl = small_workload(dim=1, g=200, n=20000, k=40, t=2000, ls=0.1, noise=0.0025)
+    ski = gpu_ski(love, torch, wl)
+    cache = love.love_precompute(ski, k=40, want_mean=False, want_sampler=True)
+    xs = np.asarray(wl.x_test(), np.float32)
+    v = love.love_predict_var_root(cache, torch.tensor(xs, device="cuda")).double().cpu().numpy()
+    p = ol.prior(og.grid_from_workload(wl), xs.astype(np.float64))
+    assert np.all(v >= 0) and np.all(v <= p * (1 + 1e-5))
+    c2 = love.love_precompute(ski, k=10, want_mean=False)
+    with pytest.raises(love.LoveError):
+        love.love_predict_var_root(c2, torch.tensor(xs, device="cuda"))

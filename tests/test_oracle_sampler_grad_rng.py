@@ -39,6 +39,19 @@ def test_sampler_root_matches_exact_posterior_covariance_at_exhaustion():
     np.testing.assert_allclose(np.diag(got), v, rtol=1e-6, atol=1e-12)
 
 
+def test_root_variance_is_the_exact_variance_at_exhaustion():
+    """|S^T w*|^2 with the posterior root: a sum of squares, and at Krylov
+    exhaustion (S S^T = K_UU - C) the exact SKI variance, here computed by the
+    independent push-through solve."""
+    ski, xs = _small(g=20, n=300)
+    c = L.precompute(ski, k=300)
+    L.sampler_precompute(c, k=ski.grid.m, seed=7, tau=1e-13)
+    _, v_exact = E.exact_pushthrough(ski, xs)
+    vr = L.predict_root(c, xs)
+    assert np.all(vr >= 0)
+    np.testing.assert_allclose(vr, v_exact, rtol=1e-6, atol=1e-9 * np.max(v_exact))
+
+
 def test_sample_covariance_converges_and_sample_is_deterministic():
     ski, xs = _small(g=16, n=200, noise=0.1)
     c = L.precompute(ski, k=200)
