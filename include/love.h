@@ -154,6 +154,19 @@ LOVE_API love_status love_cache_destroy(love_cache_t cache);
 LOVE_API love_status love_predict_mean_var(love_cache_t cache, int64_t t, const void* x_test,
                                   void* mean, void* var, love_stream_t stream);
 
+/* love_predict_covariance -- posterior cross-covariances between two sets of
+ * test points (Sec. 3: eq. pred_covar_ski_fast for i != j, Algorithm 1 with
+ * two point sets):  cov[i, j] = p(x1_i, x2_j) - (Rt^T w1_i) . (Rt^T w2_j), with
+ * p the SKI prior w1_i^T K_UU w2_j (or outputscale * k(x1_i, x2_j) with
+ * LOVE_PRIOR_EXACT).  x1: t1 x dim, x2: t2 x dim device arrays; cov: t1 x t2
+ * row-major device array; all in the ski dtype.  Entries of a point whose
+ * stencil leaves the grid are NaN (and LOVE_ERR_DOMAIN is recorded).  Takes
+ * temporary device memory from the cache's allocator (O((t1 + t2) k)).  With
+ * x1 = x2 the diagonal is the variance of love_predict_mean_var (up to
+ * rounding). */
+LOVE_API love_status love_predict_covariance(love_cache_t cache, int64_t t1, const void* x1, int64_t t2,
+                                             const void* x2, void* cov, love_stream_t stream);
+
 /* love_predict_var_root -- predictive variance from the posterior root S of
  * Sec. 3.3 (S S^T ~ K_UU - Rt Rt^T, the sampler cache): var = |S^T w*|^2 at
  * each of t test points.  A sum of squares, so no cancellation against the

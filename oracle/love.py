@@ -114,6 +114,24 @@ def predict(cache: LoveCache, x: np.ndarray, prior_mode: str = "ski"):
     return mean, var
 
 
+def predict_cov(cache: LoveCache, x1: np.ndarray, x2: np.ndarray, prior_mode: str = "ski") -> np.ndarray:
+    """Posterior cross-covariances (eq. pred_covar_ski_fast with i != j, Alg. 1 on
+    two point sets): cov[i, j] = p(x1_i, x2_j) - (Rt^T w1_i) . (Rt^T w2_j), with p
+    the SKI prior w1^T K_UU w2 or, in "exact" mode, outputscale * k(x1_i, x2_j)."""
+    grid = cache.grid
+    W1, W2 = grid.W(x1), grid.W(x2)                                   # m x t1, m x t2
+    if prior_mode == "exact":
+        a = np.atleast_2d(x1).reshape(-1, grid.dim)
+        b = np.atleast_2d(x2).reshape(-1, grid.dim)
+        d2 = np.zeros((a.shape[0], b.shape[0]))
+        for e in range(grid.dim):
+            d2 += (a[:, e][:, None] - b[:, e][None, :]) ** 2 / (2.0 * grid.lengthscale[e] ** 2)
+        P = grid.outputscale * np.exp(-d2)
+    else:
+        P = W1.T @ grid.kuu_matmul(W2.toarray())
+    return P - (W1.T @ cache.Rt) @ (W2.T @ cache.Rt).T
+
+
 # -- sampler ------------------------------------------------------------------
 def sampler_precompute(cache: LoveCache, k: int, seed: int, tau: float = 1e-12):
     """S with S S^T ~ K_UU - Rt Rt^T via Lanczos (Sec. 3.3)."""

@@ -335,6 +335,18 @@ def love_predict_mean_var(cache: Cache, x_test: torch.Tensor, want_mean: bool = 
     return mean, var
 
 
+def love_predict_covariance(cache: Cache, x1: torch.Tensor, x2: Optional[torch.Tensor] = None,
+                            stream=None) -> torch.Tensor:
+    """t1 x t2 posterior cross-covariances (x2 defaults to x1)."""
+    dt = _TORCH[cache.dtype]
+    x1 = _as_points(x1, cache.dim, dt)
+    x2 = x1 if x2 is None else _as_points(x2, cache.dim, dt)
+    out = torch.empty((x1.shape[0], x2.shape[0]), dtype=dt, device=x1.device)
+    check("love_predict_covariance", lib().love_predict_covariance(cache.handle, x1.shape[0], _ptr(x1), x2.shape[0],
+                                                                   _ptr(x2), _ptr(out), _stream(stream)))
+    return out
+
+
 def love_predict_var_root(cache: Cache, x_test: torch.Tensor, stream=None, out_var=None) -> torch.Tensor:
     """Variance from the posterior root: |S^T w*|^2 (needs want_sampler)."""
     dt = _TORCH[cache.dtype]

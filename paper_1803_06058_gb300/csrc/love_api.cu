@@ -568,6 +568,14 @@ love_status love_predict_mean_var(love_cache_t c, int64_t t, const void* x_test,
   return predict_launch(c, t, x_test, mean, var, cs(stream));
 }
 
+love_status love_predict_covariance(love_cache_t c, int64_t t1, const void* x1, int64_t t2, const void* x2,
+                                    void* cov, love_stream_t stream) {
+  if (!c || t1 < 0 || t2 < 0) return LOVE_ERR_ARG;
+  if (t1 == 0 || t2 == 0) return LOVE_OK;
+  if (!x1 || !x2 || !cov) return LOVE_ERR_ARG;
+  return cov_launch(c, t1, x1, t2, x2, cov, cs(stream));
+}
+
 love_status love_predict_var_root(love_cache_t c, int64_t t, const void* x_test, void* var, love_stream_t stream) {
   if (!c || t < 0) return LOVE_ERR_ARG;
   if (!c->S) return LOVE_ERR_STATE;

@@ -393,6 +393,9 @@ love_status predict_batched_launch(const void* descs, const int64_t* toff, const
                                    int dim, love_dtype dtype, love_dtype cache_dtype, int lanes, int ctas_per_sm,
                                    const void* x, void* mean, void* var, cudaStream_t s);
 love_status predict_root_launch(love_cache* c, int64_t t, const void* x, void* var, cudaStream_t s);
+// k_cov.cu: t1 x t2 posterior cross-covariances (row-major, data dtype)
+love_status cov_launch(love_cache* c, int64_t t1, const void* x1, int64_t t2, const void* x2, void* out,
+                       cudaStream_t s);
 love_status predict_launch(love_cache* c, int64_t t, const void* x, void* mean, void* var,
                            cudaStream_t s);
 love_status backward_launch(love_cache* c, int64_t t, const void* x, const void* gv, void* gx,

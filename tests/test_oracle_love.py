@@ -171,3 +171,33 @@ def test_exact_prior_mode_uses_outputscale():
     _, v_ex = L.predict(c, xs, prior_mode="exact")
     p = ski.grid.local_kernel_quadform(xs)
     np.testing.assert_allclose(v_ex - v_ski, 2.5 - p, atol=1e-13)
+
+
+def test_cross_covariance_is_the_exact_posterior_covariance_at_exhaustion():
+    """predict_cov at Krylov exhaustion equals W1^T (K_UU - C) W2 with C from the
+    independent push-through solve; with x1 = x2 it is symmetric PSD and its
+    diagonal is the LOVE variance."""
+    from oracle import exact as E
+    from oracle import love as L
+    from oracle import grid as og
+    from oracle import ski as os_
+    rng = np.random.default_rng(21)
+    g = 18
+    lo, hi = -2.0 / (g - 5), 1.0 + 2.0 / (g - 5)
+    grid = og.Grid([g], [lo], [hi], [0.2], 1.3)
+    x = rng.uniform(0, 1, (300, 1))
+    ski = os_.SKI(grid, x, 0.05, np.sin(6 * x[:, 0]))
+    c = L.precompute(ski, k=300)
+    x1 = rng.uniform(0, 1, (40, 1))
+    x2 = rng.uniform(0, 1, (25, 1))
+    C = E.pushthrough_C(ski)
+    target = grid.W(x1).T @ (grid.dense_kuu() - C) @ grid.W(x2)
+    got = L.predict_cov(c, x1, x2)
+    assert np.max(np.abs(got - target)) < 1e-9 * np.max(np.abs(target))
+    S = L.predict_cov(c, x1, x1)
+    np.testing.assert_allclose(S, S.T, atol=1e-12)
+    assert np.min(np.linalg.eigvalsh(S)) > -1e-10
+    np.testing.assert_allclose(np.diag(S), L.predict(c, x1)[1], rtol=1e-9, atol=1e-14)
+    # the exact-prior form: outputscale * k on the diagonal
+    Se = L.predict_cov(c, x1, x1, prior_mode="exact")
+    np.testing.assert_allclose(np.diag(Se), L.predict(c, x1, prior_mode="exact")[1], rtol=1e-9, atol=1e-14)
