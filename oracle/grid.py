@@ -156,3 +156,103 @@ class Grid:
 def grid_from_workload(wl) -> Grid:
     return Grid(size=list(wl.grid_size), lo=list(wl.grid_lo), hi=list(wl.grid_hi),
                 lengthscale=list(wl.lengthscale), outputscale=float(wl.outputscale))
+
+
+@dataclasses.dataclass
+class AdditiveGrid:
+    """Additive composition of one-dimensional KISS-GP kernels (Sec. 3, "Extension
+    to additive kernel compositions"): k~(x, x') = sum_e w_e(x_e)^T K_e w_e(x'_e),
+    written as one SKI kernel with the stacked interpolation vector
+    w(x) = [w_1(x_1); ...; w_d(x_d)] (4 nonzeros per component) and the
+    block-diagonal K_UU = diag(K_1, ..., K_d), K_e = s_f T_e on grid e.
+
+    Same interface as Grid (W, kuu_matmul, dense_kuu, local_kernel_quadform, m,
+    dim), so the LOVE oracle runs on it unchanged.  Grid index of node j of
+    component e: offset(e) + j, offset(e) = size[0] + ... + size[e-1].
+    """
+    size: List[int]
+    lo: List[float]
+    hi: List[float]
+    lengthscale: List[float]
+    outputscale: float = 1.0
+
+    @property
+    def dim(self) -> int:
+        return len(self.size)
+
+    @property
+    def m(self) -> int:
+        return int(np.sum(self.size))
+
+    @property
+    def h(self) -> List[float]:
+        return [(self.hi[e] - self.lo[e]) / (self.size[e] - 1) for e in range(self.dim)]
+
+    @property
+    def offsets(self) -> List[int]:
+        return [int(np.sum(self.size[:e])) for e in range(self.dim)]
+
+    def component(self, e: int) -> Grid:
+        return Grid([self.size[e]], [self.lo[e]], [self.hi[e]], [self.lengthscale[e]], self.outputscale)
+
+    def toeplitz_col(self, e: int) -> np.ndarray:
+        return self.component(e).toeplitz_col(0)
+
+    def dense_kuu(self, deriv_dim: int = -1) -> np.ndarray:
+        return scipy.linalg.block_diag(*[self.component(e).dense_kuu(0 if e == deriv_dim else -1)
+                                         for e in range(self.dim)])
+
+    def kuu_matmul(self, V: np.ndarray, deriv_dim: int = -1) -> np.ndarray:
+        out = np.zeros_like(np.asarray(V, dtype=np.float64))
+        for e, off in enumerate(self.offsets):
+            sl = slice(off, off + self.size[e])
+            out[sl] = self.component(e).kuu_matmul(np.asarray(V, dtype=np.float64)[sl],
+                                                   deriv_dim=0 if e == deriv_dim else -1)
+        return out
+
+    def interp(self, x: np.ndarray, check: bool = True):
+        x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+        if x.shape[1] != self.dim:
+            x = x.reshape(-1, self.dim)
+        return [keys.interp_1d(x[:, e], self.lo[e], self.h[e], self.size[e], check) for e in range(self.dim)]
+
+    def stencil(self, x: np.ndarray, check: bool = True, deriv_dim: int = -1):
+        """Rows and values of the 4 d nonzeros of the stacked w_x (component by
+        component; deriv_dim = e: d w_x / d x_e, nonzero in component e only)."""
+        per = self.interp(x, check)
+        rows, vals = [], []
+        for e, ((i, w, dw), off) in enumerate(zip(per, self.offsets)):
+            rows.append(off + i[:, None] + np.arange(-1, 3)[None, :])
+            if deriv_dim < 0:
+                vals.append(w)
+            else:
+                vals.append(dw if e == deriv_dim else np.zeros_like(w))
+        return np.concatenate(rows, axis=1), np.concatenate(vals, axis=1)
+
+    def W(self, x: np.ndarray, check: bool = True, deriv_dim: int = -1) -> sp.csr_matrix:
+        rows, vals = self.stencil(x, check, deriv_dim)
+        n = rows.shape[0]
+        cols = np.repeat(np.arange(n), rows.shape[1])
+        return sp.csr_matrix((vals.ravel(), (rows.ravel(), cols)), shape=(self.m, n))
+
+    def local_kernel_quadform(self, x: np.ndarray, deriv_x: int = -1,
+                              deriv_l: int = -1, check: bool = True) -> np.ndarray:
+        """w_x^T K_UU w_x = s_f sum_e w_e^T T_e^loc w_e (a sum over components)."""
+        per = self.interp(x, check)
+        out = np.zeros(per[0][0].shape[0])
+        for e, (_, w, dw) in enumerate(per):
+            c = self.component(e)
+            cc = c.toeplitz_col_dl(0) if e == deriv_l else c.toeplitz_col(0)
+            if deriv_l >= 0 and e != deriv_l:
+                continue
+            if deriv_x >= 0 and e != deriv_x:
+                continue
+            Tloc = scipy.linalg.toeplitz(cc[:4])
+            left = dw if e == deriv_x else w
+            out = out + self.outputscale * np.einsum("nr,rs,ns->n", left, Tloc, w)
+        return out
+
+
+def additive_grid_from_workload(wl) -> AdditiveGrid:
+    return AdditiveGrid(size=list(wl.grid_size), lo=list(wl.grid_lo), hi=list(wl.grid_hi),
+                        lengthscale=list(wl.lengthscale), outputscale=float(wl.outputscale))
