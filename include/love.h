@@ -88,6 +88,17 @@ typedef struct {
   double noise;               /* sigma^2 > 0                                 */
   love_dtype dtype;           /* LOVE_F32 or LOVE_F64: x, y and the Lanczos  */
   const love_allocator* allocator;  /* NULL -> cudaMallocAsync             */
+  int additive;               /* 0: the product kernel above.  1: the additive
+                                 composition of the paper's Sec. 3 extension,
+                                 sum_e outputscale exp(-(x_e - x'_e)^2 / (2 l_e^2)):
+                                 one 1-D grid per dimension, stacked
+                                 interpolation vectors (4 nonzeros per
+                                 dimension) and a block-diagonal K_UU,
+                                 m = sum_e grid_size[e].  Supported by ski_mvm,
+                                 ski_mvm_kuu, love_precompute (variance and mean
+                                 caches, sampler), love_predict_mean_var,
+                                 love_predict_var_root and love_sample; the
+                                 other calls return LOVE_ERR_UNSUPPORTED. */
 } love_ski_desc;
 
 typedef struct love_ski* love_ski_t;

@@ -22,6 +22,7 @@ from __future__ import annotations
 import ctypes as C
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -65,7 +66,7 @@ TORCH_ALLOCATOR = _lib.love_allocator(_torch_alloc, _torch_free, None)
 
 
 def _desc(dim, n, grid_size, grid_lo, grid_hi, lengthscale, outputscale, noise, dtype,
-          use_torch_allocator=True):
+          use_torch_allocator=True, additive=False):
     d = _lib.love_ski_desc()
     d.dim = dim
     d.n = n
@@ -78,6 +79,7 @@ def _desc(dim, n, grid_size, grid_lo, grid_hi, lengthscale, outputscale, noise, 
     d.noise = float(noise)
     d.dtype = dtype
     d.allocator = C.pointer(TORCH_ALLOCATOR) if use_torch_allocator else None
+    d.additive = 1 if additive else 0
     return d
 
 
@@ -136,7 +138,10 @@ def _as_points(x: torch.Tensor, dim: int, dtype: torch.dtype) -> torch.Tensor:
 
 def ski_build(x_train: torch.Tensor, y_train: Optional[torch.Tensor], grid_size: Sequence[int],
               grid_lo: Sequence[float], grid_hi: Sequence[float], lengthscale: Sequence[float],
-              outputscale: float, noise: float, stream=None, use_torch_allocator=True) -> Ski:
+              outputscale: float, noise: float, stream=None, use_torch_allocator=True,
+              additive: bool = False) -> Ski:
+    """KISS-GP structure of a training set.  additive=True: the additive
+    composition of 1-D kernels (block-diagonal K_UU, m = sum of grid_size)."""
     if x_train.dim() == 1:
         x_train = x_train.reshape(-1, 1)
     n, dim = x_train.shape
@@ -146,13 +151,12 @@ def ski_build(x_train: torch.Tensor, y_train: Optional[torch.Tensor], grid_size:
                                 or y_train.numel() != n or not y_train.is_cuda):
         raise ValueError("y_train must be a contiguous CUDA tensor of n values, same dtype as x")
     d = _desc(dim, n, grid_size, grid_lo, grid_hi, lengthscale, outputscale, noise, dt,
-              use_torch_allocator)
+              use_torch_allocator, additive)
     h = C.c_void_p()
     check("ski_build", lib().ski_build(C.byref(d), _ptr(x_train), _ptr(y_train), _stream(stream),
                                        C.byref(h)))
-    m = 1
-    for e in range(dim):
-        m *= int(grid_size[e])
+    sizes = [int(grid_size[e]) for e in range(dim)]
+    m = sum(sizes) if additive else int(np.prod(sizes))
     return Ski(h, d, dt, n, dim, m)
 
 
@@ -416,13 +420,13 @@ def love_var(cache: Cache, x: torch.Tensor, lengthscale: Optional[torch.Tensor] 
 
 def love_cache_import(grid_size, grid_lo, grid_hi, lengthscale, outputscale, noise, Rt, a=None,
                       S=None, alpha=None, beta=None, P=None, dtype="f32", cache_dtype=None,
-                      prior_exact=False, stream=None) -> Cache:
+                      prior_exact=False, stream=None, additive=False) -> Cache:
     """Build a cache from host (numpy) arrays computed elsewhere."""
     import numpy as np
     dim = len(grid_size)
     dt = _DT[dtype]
     cdt = dt if cache_dtype is None else _DT[cache_dtype]
-    d = _desc(dim, 1, grid_size, grid_lo, grid_hi, lengthscale, outputscale, noise, dt)
+    d = _desc(dim, 1, grid_size, grid_lo, grid_hi, lengthscale, outputscale, noise, dt, additive=additive)
     Rt = np.ascontiguousarray(Rt, dtype=np.float64)
     m, k = Rt.shape
     flags = ((WANT_MEAN if a is not None else 0) | (WANT_SAMPLER if S is not None else 0)

@@ -30,7 +30,7 @@ class love_ski_desc(C.Structure):
                 ("grid_lo", C.c_double * 3), ("grid_hi", C.c_double * 3),
                 ("outputscale", C.c_double), ("lengthscale", C.c_double * 3),
                 ("noise", C.c_double), ("dtype", C.c_int),
-                ("allocator", C.POINTER(love_allocator))]
+                ("allocator", C.POINTER(love_allocator)), ("additive", C.c_int)]
 
 
 class love_precompute_opts(C.Structure):

@@ -352,7 +352,7 @@ love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocato
   int nb = ceil_div(N, 256);
   LOVE_COUNT_LAUNCH(); k_twiddles<<<nb, 256, 0, s>>>((double2*)p.tw_d, (float2*)p.tw_f, N);
   for (int deriv = 0; deriv < 2; ++deriv) {
-    double scale = (e == 0) ? g.sf : 1.0;
+    double scale = (e == 0 || g.additive) ? g.sf : 1.0;   // s_f in every block of an additive K_UU
     LOVE_COUNT_LAUNCH(); k_embed_column<<<nb, 256, 0, s>>>(col, N, p.g, g.h[e], g.ls[e], scale, deriv);
     if (p.N2 == 1) {
       LOVE_TRY(fft_forward_small_f64(p, col, X, wk, s));
@@ -394,7 +394,8 @@ size_t fft_work_bytes(const GridHost& g, const FftPlan* plans, int ncol, bool db
   for (int e = 0; e < g.dim; ++e) {
     if (plans[e].N2 == 1) continue;
     (void)dbl;  // the transforms always run in FP64
-    size_t b = (size_t)plans[e].N * (size_t)(g.m / g.g[e]) * (size_t)ncol * 16;
+    const size_t fibres = g.additive ? 1 : (size_t)(g.m / g.g[e]);
+    size_t b = (size_t)plans[e].N * fibres * (size_t)ncol * 16;
     best = std::max(best, b);
   }
   return best;
@@ -403,6 +404,14 @@ size_t fft_work_bytes(const GridHost& g, const FftPlan* plans, int ncol, bool db
 template <typename T>
 love_status kuu_apply(const GridHost& g, const FftPlan* plans, const T* v, T* out, int ncol, int64_t ldc,
                       void* work, int deriv_dim, cudaStream_t s) {
+  if (g.additive) {
+    // block-diagonal K_UU: one Toeplitz product per 1-D block
+    for (int e = 0; e < g.dim; ++e) {
+      ModeGeom mg{g.g[e], 1, 1, ldc};
+      LOVE_TRY((toeplitz_mode<T, double>(plans[e], v + g.off[e], out + g.off[e], mg, ncol, work, e == deriv_dim, s)));
+    }
+    return LOVE_OK;
+  }
   const T* src = v;
   for (int e = 0; e < g.dim; ++e) {
     ModeGeom mg{g.g[e], g.stride[e], g.m / g.g[e], ldc};

@@ -84,6 +84,18 @@ struct Stencil {
   template <typename V>
   __device__ __forceinline__ V apply(const V* __restrict__ u, const GridDev& g) const {
     V acc = V(0);
+    if (D > 1 && g.additive) {
+      // stacked interpolation vector: 4 nonzeros per 1-D block
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        const V* p = u + g.off[e] + (base[e] - 1);
+        V a = V(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a += (V)w[e][r] * p[r];
+        acc += a;
+      }
+      return acc;
+    }
     if (D == 1) {
       const V* p = u + (base[0] - 1);
 #pragma unroll
@@ -198,10 +210,12 @@ __device__ __forceinline__ void node_index(int64_t node, const GridDev& g, int* 
 // u[node] = scale * sum over sorted points of w_p(node) v[p]   (u = W v).
 // A node collects ~4 n/m points in 1-D (400 on the n = 1e6, m = 1e4 grid), so
 // the sum is accumulated in double-float (Dot2) and rounded once.
+// map (additive composition): position of each sorted point in the order of v
 template <typename T, int D, typename V = T>
 __global__ void k_scatter(GridDev g, const T* __restrict__ xs, const int* __restrict__ cell_start,
                           const V* __restrict__ v, const double* __restrict__ scal, V scale, V* __restrict__ u,
-                          const V* __restrict__ v2, const double* __restrict__ beta2, const int* __restrict__ skip) {
+                          const V* __restrict__ v2, const double* __restrict__ beta2, const int* __restrict__ skip,
+                          const int32_t* __restrict__ map) {
   // with v2: scatters v + beta2 v2 (the CG direction r + beta p, formed on the fly)
   using Acc = typename AccOf<V>::type;
   if (skip && *skip) return;
@@ -219,8 +233,9 @@ __global__ void k_scatter(GridDev g, const T* __restrict__ xs, const int* __rest
     acc.zero();
     for (int f = lane; f < rg.total; f += 32) {
       int p = rg.point(f);
-      V val = v[p];
-      if (v2) val += b2 * v2[p];
+      const int pv = map ? map[p] : p;
+      V val = v[pv];
+      if (v2) val += b2 * v2[pv];
       acc.add_prod((V)node_weight<T, D>(xs + (int64_t)p * D, g, nd), val);
     }
     warp_merge(acc);
@@ -232,7 +247,8 @@ __global__ void k_scatter(GridDev g, const T* __restrict__ xs, const int* __rest
 // double-float accumulation as in k_scatter
 template <typename T, int D, int CH>
 __global__ void k_scatter_multi(GridDev g, const T* __restrict__ xs, const int* __restrict__ cell_start,
-                                const T* __restrict__ Q, int64_t ldq, int ncol, T* __restrict__ out, int64_t ldo) {
+                                const T* __restrict__ Q, int64_t ldq, int ncol, T* __restrict__ out, int64_t ldo,
+                                const int32_t* __restrict__ map) {
   using Acc = typename AccOf<T>::type;
   const int lane = threadIdx.x & 31;
   const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -248,10 +264,11 @@ __global__ void k_scatter_multi(GridDev g, const T* __restrict__ xs, const int* 
       for (int c = 0; c < CH; ++c) acc[c].zero();
       for (int f = lane; f < rg.total; f += 32) {
         int p = rg.point(f);
+        const int pq = map ? map[p] : p;
         T w = node_weight<T, D>(xs + (int64_t)p * D, g, nd);
 #pragma unroll
         for (int c = 0; c < CH; ++c)
-          if (c0 + c < ncol) acc[c].add_prod(w, Q[(int64_t)(c0 + c) * ldq + p]);
+          if (c0 + c < ncol) acc[c].add_prod(w, Q[(int64_t)(c0 + c) * ldq + pq]);
       }
       double val = 0.0;
 #pragma unroll
@@ -975,13 +992,27 @@ love_status scatter_launch(love_ski* ski, const V* v, const double* scal, V scal
   GridDev g = ski->grid.dev();
   int64_t warps = g.m;
   int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
-  LOVE_COUNT_LAUNCH(); k_scatter<T, D, V><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, v, scal, scale, u, v2, beta2, skip);
+  LOVE_COUNT_LAUNCH(); k_scatter<T, D, V><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, v, scal, scale, u, v2, beta2, skip, nullptr);
+  return cuda_check(cudaGetLastError());
+}
+// additive composition: block e of u = W_e v, over the points sorted in dimension e
+template <typename T, typename V>
+love_status scatter_additive(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s,
+                             const V* v2, const double* beta2, const int* skip) {
+  for (int e = 0; e < ski->grid.dim; ++e) {
+    const GridDev g = component_dev(ski->grid, e);
+    int blocks = (int)std::min<int64_t>(((int64_t)g.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
+    LOVE_COUNT_LAUNCH();
+    k_scatter<T, 1, V><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs1[e], ski->cs1[e], v, scal, scale,
+                                               u + ski->grid.off[e], v2, beta2, skip, ski->map1[e]);
+  }
   return cuda_check(cudaGetLastError());
 }
 // u = W v (or W (v + beta2 v2)) with coordinates of type T (the ski dtype) and values of type V
 template <typename T, typename V = T>
 love_status scatter_any(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s,
                         const V* v2 = nullptr, const double* beta2 = nullptr, const int* skip = nullptr) {
+  if (ski->grid.additive) return scatter_additive<T, V>(ski, v, scal, scale, u, s, v2, beta2, skip);
   switch (ski->grid.dim) {
     case 1: return scatter_launch<T, 1, V>(ski, v, scal, scale, u, s, v2, beta2, skip);
     case 2: return scatter_launch<T, 2, V>(ski, v, scal, scale, u, s, v2, beta2, skip);
@@ -1190,11 +1221,21 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
 template <typename T>
 love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* out, int64_t ldo, cudaStream_t s) {
   GridDev g = ski->grid.dev();
+  if (g.additive) {
+    for (int e = 0; e < g.dim; ++e) {
+      const GridDev ge = component_dev(ski->grid, e);
+      int blocks = (int)std::min<int64_t>(((int64_t)ge.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
+      LOVE_COUNT_LAUNCH();
+      k_scatter_multi<T, 1, 8><<<blocks, 256, 0, s>>>(ge, (const T*)ski->xs1[e], ski->cs1[e], Q, ldq, ncol,
+                                                      out + ski->grid.off[e], ldo, ski->map1[e]);
+    }
+    return cuda_check(cudaGetLastError());
+  }
   int blocks = (int)std::min<int64_t>((g.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
   switch (g.dim) {
-    case 1: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 1, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo); break;
-    case 2: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 2, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo); break;
-    default: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 3, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo);
+    case 1: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 1, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
+    case 2: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 2, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
+    default: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 3, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr);
   }
   return cuda_check(cudaGetLastError());
 }
@@ -1255,7 +1296,9 @@ love_status cg_solve_df(love_ski* ski, const float* b, double* x, double tol, in
 
 template <typename T>
 love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_iter, int* iters, cudaStream_t s) {
-  if (sizeof(T) == 4) return cg_solve_df(ski, (const float*)b, x, tol, max_iter, iters, s);
+  // the double-float form scatters over the product grid only; an additive
+  // grid takes the FP64-vector form below
+  if (sizeof(T) == 4 && !ski->grid.additive) return cg_solve_df(ski, (const float*)b, x, tol, max_iter, iters, s);
   const GridHost& gh = ski->grid;
   const GridDev g = gh.dev();
   const int64_t np = ski->n_pad;
@@ -1515,7 +1558,7 @@ __global__ void k_mcg_start(int64_t m, const double* __restrict__ b, const doubl
 
 }  // namespace
 
-bool mean_grid_cg_supported(const love_ski* ski) { return ski->grid.dim <= 2; }
+bool mean_grid_cg_supported(const love_ski* ski) { return ski->grid.dim <= 2 && !ski->grid.additive; }
 
 template <typename T>
 love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s) {

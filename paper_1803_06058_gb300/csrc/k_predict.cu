@@ -111,6 +111,16 @@ __device__ __forceinline__ void gather_rows(const PredArgs& a, const typename Ve
 #pragma unroll
   for (int c = 0; c < VC; ++c) acc[c] = R(0);
   if (!ok) return;
+  if (D > 1 && a.g.additive) {
+    // stacked interpolation vector: 4 rows per 1-D block
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      const V* p = base_ptr + (int64_t)(a.g.off[e] + base[e] - 1) * NG + cg;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) vec_fma(acc, ldg_vec(p + r * NG), w[e][r]);
+    }
+    return;
+  }
   if (D == 1) {
     // small outer Keys weights first, so the two large terms are added last
     const V* p = base_ptr + (int64_t)(base[0] - 1) * NG + cg;
@@ -206,7 +216,10 @@ __device__ __forceinline__ void predict_groups(const PredArgs& a, int64_t warp_f
         } else if (li == 0) {
           df p = local_quad_df(w[0], a.cl[0]);
 #pragma unroll
-          for (int e = 1; e < D; ++e) p = df_mul(p, local_quad_df(w[e], a.cl[e]));
+          for (int e = 1; e < D; ++e) {
+            const df q = local_quad_df(w[e], a.cl[e]);
+            p = a.g.additive ? df_add(p, q) : df_mul(p, q);   // sum of blocks / Kronecker product
+          }
           tot = df_add(tot, p);
         }
       }
@@ -238,11 +251,12 @@ __device__ __forceinline__ void predict_groups(const PredArgs& a, int64_t warp_f
         if (a.exact_prior) {
           tot += a.sf;
         } else {
-          double p = 1.0;
+          double p = a.g.additive ? 0.0 : 1.0;
 #pragma unroll
           for (int e = 0; e < D; ++e) {
             double wd[4] = {(double)w[e][0], (double)w[e][1], (double)w[e][2], (double)w[e][3]};
-            p *= local_quad_d(wd, a.cld[e]);
+            const double q = local_quad_d(wd, a.cld[e]);
+            p = a.g.additive ? p + q : p * q;
           }
           tot += p;
         }
@@ -337,11 +351,13 @@ PredArgs make_pred_args(const love_cache* c) {
   a.ld = c->ld;
   a.k = c->k_eff;
   a.exact_prior = (c->flags & LOVE_PRIOR_EXACT) ? 1 : 0;
-  a.sf = c->grid.sf;
+  // exact prior k(x, x): s_f, or d s_f for an additive composition of d kernels
+  a.sf = c->grid.sf * (c->grid.additive ? c->grid.dim : 1);
   for (int e = 0; e < LOVE_MAX_DIM; ++e)
     for (int q = 0; q < 4; ++q) {
-      // outputscale folded into dimension 0: p = prod_e w_e^T T_e w_e
-      double v = c->grid.cloc[e][q] * (e == 0 ? c->grid.sf : 1.0);
+      // outputscale folded into dimension 0: p = prod_e w_e^T T_e w_e (into every
+      // block of an additive grid: p = sum_e s_f w_e^T T_e w_e)
+      double v = c->grid.cloc[e][q] * ((e == 0 || c->grid.additive) ? c->grid.sf : 1.0);
       float hi = (float)v;
       a.cl[e][q] = {hi, (float)(v - (double)hi)};
       a.cld[e][q] = v;

@@ -263,6 +263,11 @@ __global__ void k_sample_gather(SampleGatherArgs a) {
       if (D == 1) {
         row = base[0] - 1 + r0;
         wq = w[0][r0];
+      } else if (a.g.additive) {
+        // stacked vector: 4 rows per 1-D block, the rest unused
+        const int e = q >> 2 < D ? q >> 2 : 0;
+        row = q < 4 * D ? (int64_t)a.g.off[e] + base[e] - 1 + (q & 3) : 0;
+        wq = q < 4 * D ? w[e][q & 3] : T(0);
       } else if (D == 2) {
         row = (int64_t)(base[0] - 1 + r1) * a.g.stride[0] + (base[1] - 1 + r0);
         wq = w[0][r1] * w[1][r0];

@@ -28,7 +28,9 @@ __global__ void k_cell_keys(const T* __restrict__ x, int64_t n, GridDev g, uint3
     int b;
     T w[4];
     ok &= keys_weights(s, g.g[e], b, w);
-    key += (uint32_t)b * (uint32_t)g.stride[e];
+    // additive composition: the primary order is by the cell of dimension 0
+    if (!g.additive) key += (uint32_t)b * (uint32_t)g.stride[e];
+    else if (e == 0) key = (uint32_t)b;
   }
   if (!ok) {
     key = 0;
@@ -165,7 +167,7 @@ __global__ void k_permute(const T* __restrict__ x, const T* __restrict__ y, cons
 
 template <typename T>
 love_status sort_impl(love_ski* ski, const void* x_in, const void* y_in, cudaStream_t s) {
-  const int64_t n = ski->n, m = ski->grid.m;
+  const int64_t n = ski->n, m = ski->grid.additive ? ski->grid.g[0] : ski->grid.m;   // cells keyed
   const GridDev gd = ski->grid.dev();
   const Allocator& al = ski->alloc;
   size_t kb = (size_t)n * 4;
@@ -202,7 +204,88 @@ love_status sort_impl(love_ski* ski, const void* x_in, const void* y_in, cudaStr
   return rc;
 }
 
+// key of a primary-ordered point: its cell in dimension e
+template <typename T>
+__global__ void k_cell_keys_dim(const T* __restrict__ xs, int64_t n, GridDev g, int e, uint32_t* __restrict__ keys,
+                                int32_t* __restrict__ vals) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b;
+  T w[4];
+  keys_weights(grid_coord(xs[i * g.dim + e], g, e), g.g[e], b, w);  // in range: checked by the primary sort
+  keys[i] = (uint32_t)b;
+  vals[i] = (int32_t)i;
+}
+// 1-D coordinates of dimension e in the order `map` (identity if null); padding rows interior
+template <typename T>
+__global__ void k_gather_dim(const T* __restrict__ xs, const int32_t* __restrict__ map, int64_t n, int64_t n_pad,
+                             GridDev g, int e, T* __restrict__ out) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pad) return;
+  out[p] = p < n ? xs[(int64_t)(map ? map[p] : p) * g.dim + e] : (T)(g.lo_d[e] + 2.0 * g.h_d[e]);
+}
+
+template <typename T>
+love_status sort_dims_impl(love_ski* ski, cudaStream_t s) {
+  const int64_t n = ski->n, np = ski->n_pad;
+  const GridDev gd = ski->grid.dev();
+  const Allocator& al = ski->alloc;
+  const T* xs = (const T*)ski->xs;
+  for (int e = 0; e < gd.dim; ++e) {
+    ski->xs1[e] = al.alloc(sizeof(T) * (size_t)np, s);
+    if (!ski->xs1[e]) return LOVE_ERR_OOM;
+  }
+  ski->cs1[0] = ski->cell_start;
+  LOVE_COUNT_LAUNCH(); k_gather_dim<T><<<ceil_div(np, 256), 256, 0, s>>>(xs, nullptr, n, np, gd, 0, (T*)ski->xs1[0]);
+  size_t kb = (size_t)n * 4;
+  int nblocks = ceil_div(n, SORT_TILE);
+  size_t hb = (size_t)RADIX * nblocks * 4;
+  uint32_t* k0 = (uint32_t*)al.alloc(kb, s);
+  uint32_t* k1 = (uint32_t*)al.alloc(kb, s);
+  int32_t* v0 = (int32_t*)al.alloc(kb, s);
+  int32_t* v1 = (int32_t*)al.alloc(kb, s);
+  uint32_t* hist = (uint32_t*)al.alloc(hb, s);
+  love_status rc = (k0 && k1 && v0 && v1 && hist) ? LOVE_OK : LOVE_ERR_OOM;
+  for (int e = 1; e < gd.dim && rc == LOVE_OK; ++e) {
+    const int64_t cells = gd.g[e];
+    ski->cs1[e] = (int32_t*)al.alloc(sizeof(int32_t) * (size_t)(cells + 1), s);
+    ski->map1[e] = (int32_t*)al.alloc(kb, s);
+    if (!ski->cs1[e] || !ski->map1[e]) {
+      rc = LOVE_ERR_OOM;
+      break;
+    }
+    LOVE_COUNT_LAUNCH(); k_cell_keys_dim<T><<<ceil_div(n, 256), 256, 0, s>>>(xs, n, gd, e, k0, v0);
+    int nbits = 1;
+    while ((int64_t(1) << nbits) < cells) ++nbits;
+    uint32_t *ka = k0, *kb2 = k1;
+    int32_t *va = v0, *vb = v1;
+    for (int shift = 0; shift < nbits; shift += 8) {
+      LOVE_COUNT_LAUNCH(); k_radix_hist<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, hist, nblocks);
+      LOVE_COUNT_LAUNCH(); k_exclusive_scan<<<1, 1024, 0, s>>>(hist, (int64_t)RADIX * nblocks);
+      LOVE_COUNT_LAUNCH(); k_radix_scatter<<<nblocks, SORT_THREADS, 0, s>>>(ka, va, kb2, vb, n, shift, hist, nblocks);
+      std::swap(ka, kb2);
+      std::swap(va, vb);
+    }
+    LOVE_COUNT_LAUNCH(); k_cell_start<<<ceil_div(n + 1, 256), 256, 0, s>>>(ka, n, cells, ski->cs1[e]);
+    rc = cuda_check(cudaMemcpyAsync(ski->map1[e], va, kb, cudaMemcpyDeviceToDevice, s));
+    if (rc != LOVE_OK) break;
+    LOVE_COUNT_LAUNCH(); k_gather_dim<T><<<ceil_div(np, 256), 256, 0, s>>>(xs, ski->map1[e], n, np, gd, e, (T*)ski->xs1[e]);
+    rc = cuda_check(cudaGetLastError());
+  }
+  al.free(k0, kb, s);
+  al.free(k1, kb, s);
+  al.free(v0, kb, s);
+  al.free(v1, kb, s);
+  al.free(hist, hb, s);
+  return rc;
+}
+
 }  // namespace
+
+love_status sort_additive_dims(love_ski* ski, cudaStream_t s) {
+  if (ski->dtype == LOVE_F64) return sort_dims_impl<double>(ski, s);
+  return sort_dims_impl<float>(ski, s);
+}
 
 love_status sort_training_points(love_ski* ski, const void* x_in, const void* y_in, cudaStream_t s) {
   if (ski->dtype == LOVE_F64) return sort_impl<double>(ski, x_in, y_in, s);

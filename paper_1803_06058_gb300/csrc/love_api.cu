@@ -61,7 +61,9 @@ GridDev GridHost::dev() const {
     d.inv_h_d[e] = 1.0 / h[e];
     d.lo_f[e] = (float)lo[e];
     d.inv_h_f[e] = (float)(1.0 / h[e]);
+    d.off[e] = (int)off[e];
   }
+  d.additive = additive ? 1 : 0;
   return d;
 }
 
@@ -91,11 +93,20 @@ love_status grid_from_desc(const love_ski_desc* d, GridHost& g) {
     }
     m *= g.g[e];
   }
+  g.additive = d->additive != 0;
+  if (g.additive) {
+    // blocks of 1-D grids, one after the other
+    m = 0;
+    for (int e = 0; e < d->dim; ++e) {
+      g.off[e] = m;
+      m += g.g[e];
+    }
+  }
   if (m > (int64_t(1) << 30)) return LOVE_ERR_UNSUPPORTED;
   g.m = m;
   int64_t st = 1;
   for (int e = d->dim - 1; e >= 0; --e) {
-    g.stride[e] = st;
+    g.stride[e] = g.additive ? 1 : st;
     st *= g.g[e];
   }
   for (int e = d->dim; e < LOVE_MAX_DIM; ++e) g.stride[e] = 1;
@@ -279,7 +290,12 @@ love_status ski_destroy(love_ski_t ski) {
   al.free(ski->perm, (size_t)ski->n * 4, s);
   al.free(ski->cell_start, (size_t)(ski->grid.m + 1) * 4, s);
   al.free(ski->status, sizeof(DevStatus), s);
-  for (int e = 0; e < ski->grid.dim; ++e) fft_plan_destroy(ski->fft[e], al, s);
+  for (int e = 0; e < ski->grid.dim; ++e) {
+    fft_plan_destroy(ski->fft[e], al, s);
+    al.free(ski->xs1[e], (size_t)ski->n_pad * es, s);
+    if (e > 0) al.free(ski->cs1[e], (size_t)(ski->grid.g[e] + 1) * 4, s);
+    al.free(ski->map1[e], (size_t)ski->n * 4, s);
+  }
   cudaStreamSynchronize(s);
   delete ski;
   return LOVE_OK;
@@ -316,6 +332,7 @@ love_status ski_build(const love_ski_desc* desc, const void* x_train, const void
   love_status rc = cuda_check(cudaMemsetAsync(ski->status, 0, sizeof(DevStatus), s));
   for (int e = 0; e < g.dim && rc == LOVE_OK; ++e) rc = fft_plan_create(ski->fft[e], g, e, al, s);
   if (rc == LOVE_OK) rc = sort_training_points(ski, x_train, y_train, s);
+  if (rc == LOVE_OK && g.additive) rc = sort_additive_dims(ski, s);
   DevStatus st{};
   if (rc == LOVE_OK) rc = cuda_check(cudaMemcpyAsync(&st, ski->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
@@ -554,6 +571,7 @@ love_status love_precompute(love_ski_t ski, const love_precompute_opts* opts, lo
   if (ski->dtype == LOVE_F64 && opts->cache_dtype != LOVE_F64) return LOVE_ERR_ARG;
   if (ski->dtype == LOVE_F32 && opts->cache_dtype == LOVE_F64) return LOVE_ERR_ARG;
   if (opts->sampler_k > LOVE_MAX_K) return LOVE_ERR_ARG;
+  if (ski->grid.additive && (opts->flags & LOVE_WANT_GRAD)) return LOVE_ERR_UNSUPPORTED;
   cudaStream_t s = cs(stream);
   if (ski->dtype == LOVE_F64) return precompute_impl<double>(ski, opts, s, out, k_eff);
   return precompute_impl<float>(ski, opts, s, out, k_eff);
@@ -571,6 +589,7 @@ love_status love_predict_mean_var(love_cache_t c, int64_t t, const void* x_test,
 love_status love_predict_covariance(love_cache_t c, int64_t t1, const void* x1, int64_t t2, const void* x2,
                                     void* cov, love_stream_t stream) {
   if (!c || t1 < 0 || t2 < 0) return LOVE_ERR_ARG;
+  if (c->grid.additive) return LOVE_ERR_UNSUPPORTED;
   if (t1 == 0 || t2 == 0) return LOVE_OK;
   if (!x1 || !x2 || !cov) return LOVE_ERR_ARG;
   return cov_launch(c, t1, x1, t2, x2, cov, cs(stream));
@@ -604,6 +623,7 @@ love_status love_sample(love_cache_t c, int64_t t, const void* x_test, int s_cou
 love_status love_var_backward(love_cache_t c, int64_t t, const void* x_test, const void* grad_var, void* grad_x,
                               double* grad_lengthscale, double* grad_noise, love_stream_t stream) {
   if (!c || t < 0) return LOVE_ERR_ARG;
+  if (c->grid.additive) return LOVE_ERR_UNSUPPORTED;
   if (!(c->flags & LOVE_WANT_GRAD) || !c->KdP) return LOVE_ERR_STATE;
   if (t > 0 && (!x_test || !grad_var)) return LOVE_ERR_ARG;
   return backward_launch(c, t, x_test, grad_var, grad_x, grad_lengthscale, grad_noise, cs(stream));
@@ -763,7 +783,7 @@ love_status love_get_device_status(love_cache_t c, int reset, love_device_status
 
 // ---- checkpoint ---------------------------------------------------------------
 static const char kMagic[8] = {'L', 'O', 'V', 'E', 'C', 'A', 'C', 'H'};
-static const uint32_t kVersion = 1;
+static const uint32_t kVersion = 2;
 
 struct CacheHeader {
   char magic[8];
@@ -776,6 +796,7 @@ struct CacheHeader {
   uint32_t flags;
   int32_t k_eff, ld, ks, ld_s, ld_g, cg_iters, sampler_fallback;
   uint64_t bytes_rc, bytes_s, bytes_p, bytes_kdp, bytes_b, bytes_minv;
+  int32_t additive, pad;     // version 2
 };
 
 static love_status write_dev(FILE* f, const void* dptr, size_t bytes, cudaStream_t s) {
@@ -801,6 +822,7 @@ love_status love_cache_save(love_cache_t c, const char* path, love_stream_t stre
   CacheHeader hd{};
   std::memcpy(hd.magic, kMagic, 8);
   hd.version = kVersion;
+  hd.additive = c->grid.additive ? 1 : 0;
   hd.dim = c->grid.dim;
   for (int e = 0; e < 3; ++e) {
     hd.g[e] = c->grid.g[e];
@@ -863,6 +885,7 @@ love_status love_cache_load(const char* path, const love_allocator* allocator, l
   }
   GridHost& g = c->grid;
   g.dim = hd.dim;
+  g.additive = hd.additive != 0;
   g.m = 1;
   for (int e = 0; e < 3; ++e) {
     g.g[e] = hd.g[e];
@@ -871,9 +894,16 @@ love_status love_cache_load(const char* path, const love_allocator* allocator, l
     g.ls[e] = hd.ls[e];
     g.m *= g.g[e];
   }
+  if (g.additive) {
+    g.m = 0;
+    for (int e = 0; e < g.dim; ++e) {
+      g.off[e] = g.m;
+      g.m += g.g[e];
+    }
+  }
   int64_t st = 1;
   for (int e = g.dim - 1; e >= 0; --e) {
-    g.stride[e] = st;
+    g.stride[e] = g.additive ? 1 : st;
     st *= g.g[e];
   }
   g.sf = hd.sf;

@@ -45,6 +45,8 @@ struct GridDev {
   double inv_h_d[LOVE_MAX_DIM];
   double h_d[LOVE_MAX_DIM];
   int m;
+  int additive;                 // additive composition: block-diagonal K_UU
+  int off[LOVE_MAX_DIM];        // (additive) first grid index of each block
 };
 
 // grid coordinate s = (x - lo)/h in the arithmetic of T.  The same function
@@ -272,6 +274,8 @@ struct Allocator {
 
 struct GridHost {
   int dim = 1;
+  bool additive = false;                 // block-diagonal K_UU of 1-D blocks
+  int64_t off[LOVE_MAX_DIM] = {0, 0, 0};  // (additive) first index of block e
   int64_t g[LOVE_MAX_DIM] = {1, 1, 1};
   int64_t stride[LOVE_MAX_DIM] = {1, 1, 1};
   int64_t m = 1;
@@ -285,6 +289,27 @@ struct GridHost {
   GridDev dev() const;
 };
 
+// one 1-D component (block e) of an additive grid, as a 1-D grid of its own
+inline GridDev component_dev(const GridHost& gh, int e) {
+  GridDev d = gh.dev();
+  GridDev c{};
+  c.dim = 1;
+  c.g[0] = d.g[e];
+  c.stride[0] = 1;
+  c.lo_f[0] = d.lo_f[e];
+  c.inv_h_f[0] = d.inv_h_f[e];
+  c.lo_d[0] = d.lo_d[e];
+  c.inv_h_d[0] = d.inv_h_d[e];
+  c.h_d[0] = d.h_d[e];
+  for (int q = 1; q < LOVE_MAX_DIM; ++q) {
+    c.g[q] = 1;
+    c.stride[q] = 1;
+  }
+  c.m = d.g[e];
+  c.additive = 0;
+  return c;
+}
+
 struct love_ski {
   GridHost grid;
   love_dtype dtype = LOVE_F32;
@@ -297,6 +322,12 @@ struct love_ski {
   int32_t* cell_start = nullptr;  // m + 1
   FftPlan fft[LOVE_MAX_DIM];
   DevStatus* status = nullptr;
+  // additive composition: per dimension e, the points sorted by their cell in
+  // dimension e: 1-D coordinates, cell starts (g_e + 1) and the position of
+  // each in the primary (dimension-0) order (null for e = 0)
+  void* xs1[LOVE_MAX_DIM] = {nullptr, nullptr, nullptr};
+  int32_t* cs1[LOVE_MAX_DIM] = {nullptr, nullptr, nullptr};
+  int32_t* map1[LOVE_MAX_DIM] = {nullptr, nullptr, nullptr};
 };
 
 struct love_cache {
@@ -329,6 +360,8 @@ namespace love {
 
 // k_sort.cu
 love_status sort_training_points(love_ski* ski, const void* x_in, const void* y_in, cudaStream_t s);
+// additive composition: the per-dimension orders (xs1, cs1, map1) from the primary order
+love_status sort_additive_dims(love_ski* ski, cudaStream_t s);
 
 // k_fft.cu
 love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocator& al, cudaStream_t s);
