@@ -139,7 +139,19 @@ typedef struct {
   int cg_max_iter;         /* <=0: 4000                                        */
   int sampler_k;           /* Lanczos steps for S; <=0: k                      */
   uint64_t sampler_seed;   /* SplitMix64 seed of the Rademacher probe          */
+  int reorth;              /* LOVE_REORTH_ALWAYS (0) or LOVE_REORTH_DETECT (1) */
+  double reorth_eta;       /* DETECT threshold on |Q_j^T y'| / |y'|; <=0: 2^-22 (F32) / 2^-51 (F64) */
 } love_precompute_opts;
+
+/* Reorthogonalisation of the Lanczos runs over K^ (love_precompute.reorth).
+ * ALWAYS: classical Gram-Schmidt twice at every step (Sec. 5).  DETECT: the
+ * second pass runs only where the first one left a measurable component,
+ * |Q_j^T y'| > eta |y'| with y' = y - Q_j Q_j^T y (measured in the same sweep
+ * that applies the first pass), so a healthy step reads Q_j twice instead of
+ * three times; the number of steps that skipped it is reported by
+ * love_cache_info.  The sampler's Lanczos run always takes both passes. */
+#define LOVE_REORTH_ALWAYS 0
+#define LOVE_REORTH_DETECT 1
 
 /* love_precompute -- the LOVE pre-compute phase (Sec. 3.2, Algorithm 1):
  * k Lanczos steps with full reorthogonalisation (Sec. 5) on K^ from the probe
@@ -226,6 +238,7 @@ typedef struct {
    * reorthogonalisation (incl. probe), [1] mean CG, [2] cache build (and the
    * gradient tables), [3] sampler; 0 for a cache that was imported or loaded */
   float phase_ms[4];
+  int reorth_skipped;      /* Lanczos steps that skipped the second pass (DETECT) */
 } love_cache_info_t;
 
 LOVE_API love_status love_cache_info(love_cache_t cache, love_cache_info_t* info);

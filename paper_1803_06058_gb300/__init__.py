@@ -186,17 +186,12 @@ def ski_mvm_kuu_noalloc(ski: Ski, v: torch.Tensor, out: Optional[torch.Tensor] =
 def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool = True,
                     want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
                     breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
-                    sampler_k: int = 0, sampler_seed: int = 0, stream=None) -> Cache:
-    o = _lib.love_precompute_opts()
-    o.k = k
-    o.cache_dtype = ski.dtype if cache_dtype is None else _DT[cache_dtype]
-    o.flags = ((WANT_MEAN if want_mean else 0) | (WANT_SAMPLER if want_sampler else 0)
-               | (WANT_GRAD if want_grad else 0) | (PRIOR_EXACT if prior_exact else 0))
-    o.breakdown_tol = breakdown_tol
-    o.cg_tol = cg_tol
-    o.cg_max_iter = cg_max_iter
-    o.sampler_k = sampler_k
-    o.sampler_seed = sampler_seed
+                    sampler_k: int = 0, sampler_seed: int = 0, reorth: str = "always", reorth_eta: float = 0.0,
+                    stream=None) -> Cache:
+    """reorth: "always" (two Gram-Schmidt passes every step) or "detect" (the
+    second pass only where |Q_j^T y'| > reorth_eta |y'|)."""
+    o = _opts(ski.dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,
+              cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta)
     h = C.c_void_p()
     keff = C.c_int(0)
     check("love_precompute", lib().love_precompute(ski.handle, C.byref(o), _stream(stream),
@@ -204,8 +199,11 @@ def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool =
     return Cache(h, ski.dtype, ski.dim)
 
 
+_REORTH = {"always": 0, "detect": 1}
+
+
 def _opts(dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,
-          cg_max_iter, sampler_k, sampler_seed):
+          cg_max_iter, sampler_k, sampler_seed, reorth="always", reorth_eta=0.0):
     o = _lib.love_precompute_opts()
     o.k = k
     o.cache_dtype = dtype if cache_dtype is None else _DT[cache_dtype]
@@ -216,19 +214,22 @@ def _opts(dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact
     o.cg_max_iter = cg_max_iter
     o.sampler_k = sampler_k
     o.sampler_seed = sampler_seed
+    o.reorth = _REORTH[reorth]
+    o.reorth_eta = reorth_eta
     return o
 
 
 def love_precompute_batched(skis: Sequence[Ski], k: int, cache_dtype: str = None, want_mean: bool = True,
                             want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
                             breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
-                            sampler_k: int = 0, sampler_seed: int = 0, workers: int = 0, stream=None):
+                            sampler_k: int = 0, sampler_seed: int = 0, workers: int = 0, reorth: str = "always",
+                            reorth_eta: float = 0.0, stream=None):
     """love_precompute for every ski (shared options), run concurrently; returns (caches, k_eff)."""
     B = len(skis)
     if B == 0:
         return [], []
     o = _opts(skis[0].dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol,
-              cg_tol, cg_max_iter, sampler_k, sampler_seed)
+              cg_tol, cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta)
     hs = (C.c_void_p * B)(*[s.handle for s in skis])
     out = (C.c_void_p * B)()
     keff = (C.c_int * B)()

@@ -37,14 +37,15 @@ class love_precompute_opts(C.Structure):
     _fields_ = [("k", C.c_int), ("cache_dtype", C.c_int), ("flags", C.c_uint),
                 ("breakdown_tol", C.c_double), ("cg_tol", C.c_double),
                 ("cg_max_iter", C.c_int), ("sampler_k", C.c_int),
-                ("sampler_seed", C.c_uint64)]
+                ("sampler_seed", C.c_uint64), ("reorth", C.c_int), ("reorth_eta", C.c_double)]
 
 
 class love_cache_info_t(C.Structure):
     _fields_ = [("dim", C.c_int), ("grid_size", C.c_int64 * 3), ("m", C.c_int64),
                 ("k_eff", C.c_int), ("ld", C.c_int), ("sampler_k", C.c_int),
                 ("cg_iters", C.c_int), ("sampler_fallback", C.c_int), ("dtype", C.c_int),
-                ("cache_dtype", C.c_int), ("flags", C.c_uint), ("phase_ms", C.c_float * 4)]
+                ("cache_dtype", C.c_int), ("flags", C.c_uint), ("phase_ms", C.c_float * 4),
+                ("reorth_skipped", C.c_int)]
 
 
 class love_device_status_t(C.Structure):

@@ -49,6 +49,8 @@ struct LanczosState {
   int k_eff;
   int kmax;
   unsigned counter;
+  int skip;        // detection mode: the second pass of this step is not needed
+  int n_skip;      // second passes skipped so far
   // CG
   double rr, rr0, pap, cg_alpha, cg_beta, tol2;
   int cg_done, cg_iters;
@@ -373,6 +375,8 @@ struct TileArgs {
   double2* partial;   // [gridDim][kcols + 1]
   LanczosState* st;
   DevStatus* status;
+  int detect;         // skip the second pass when |Q_j^T y'| <= eta |y'|
+  double eta2;        // eta^2
 };
 
 // 4 consecutive rows of one column in shared memory (one 16-byte access for
@@ -398,6 +402,26 @@ template <> struct Row4<double> {
   }
 };
 
+// end of step j: beta_j = sqrt(norm2); stop at kmax, on NaN or on breakdown
+// (beta_j <= tau max|alpha|), else the scale of the stored q_{j+1}
+__device__ void finish_step(LanczosState* st, DevStatus* status, int j) {
+  const double b = sqrt(st->norm2);
+  st->beta[j] = b;
+  if (!isfinite(b)) {
+    dev_flag(status, LOVE_ERR_NAN);
+    st->done = 1;
+    st->k_eff = j;
+  } else if (j + 1 >= st->kmax) {
+    st->k_eff = st->kmax;
+    st->done = 1;
+  } else if (b <= st->tau * st->maxabs) {
+    st->k_eff = j + 1;
+    st->done = 1;
+  } else {
+    st->scal[j + 1] = 1.0 / b;
+  }
+}
+
 // One reorthogonalisation sweep over the row tiles of [Q_j | y].  Per tile,
 // TILE_R rows of columns 0..j of Q (2-D TMA boxes of bc columns) and of y (a
 // 1-D bulk copy) land in one stage of a shared-memory ring, so every step
@@ -405,6 +429,12 @@ template <> struct Row4<double> {
 //   DOT          c = Q_j^T y                       (alpha_j = c_j)
 //   UPDATE_DOT   y -= Q_j c;   c' = Q_j^T y
 //   UPDATE_NORM  y -= Q_j c';  beta_j = |y|;  q_{j+1} = y (scaled on next use)
+// With `detect`, UPDATE_DOT also writes y' = y - Q_j c to the slot of q_{j+1}
+// and sums |y'|^2; its last CTA then measures what is left of y' in span(Q_j)
+// and, when |c'| <= eta |y'|, finishes the step itself (beta_j = |y'|) so the
+// UPDATE_NORM launch returns at once: the second pass runs only where the
+// first one left a detectable component (a DGKS-type test on the measured
+// c' instead of a norm-drop bound).
 // Both the update and the dots give warp w the columns w, w + 8, ... and lane
 // l the rows 4l .. 4l + 3 (16-byte shared-memory accesses); the update's eight
 // per-warp partial sums of a row are added in a fixed order.
@@ -414,7 +444,7 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
   static_assert(TILE_R == 128 && TILE_T == 256, "row-quad mapping assumes 128 rows, 8 warps");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LanczosState* st = a.st;
-  if (st->done) return;
+  if (st->done || (MODE == MODE_UPDATE_NORM && a.detect && st->skip)) return;
   const int j = a.j;
   const int ncols = j + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -495,7 +525,15 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
         const T yv = yt[tid] - sum;
         const int64_t p = tile * TILE_R + tid;
         if (MODE == MODE_UPDATE_DOT) {
-          a.y[p] = yv;
+          if (a.detect) {
+            if (j + 1 < a.kcols)
+              a.Q[(int64_t)(j + 1) * a.ldq + p] = yv;
+            else
+              a.y[p] = yv;
+            nacc.add_prod(yv, yv);
+          } else {
+            a.y[p] = yv;
+          }
           yt[tid] = yv;
           fence_proxy_async();
         } else {
@@ -551,9 +589,14 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
       warp_merge(acc[s2]);
       if (lane == 0 && i < ncols) acc_store(a.partial + (int64_t)blockIdx.x * pstride + i, acc[s2]);
     }
+    if (MODE == MODE_UPDATE_DOT && a.detect) {   // |y'|^2 in slot j + 1
+      block_merge(nacc, red);
+      if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride + ncols, nacc);
+    }
   }
   double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
-  bool last = last_cta_reduce<Acc>(a.partial, pstride, MODE == MODE_UPDATE_NORM ? 1 : ncols, result, &st->counter);
+  const int nres = MODE == MODE_UPDATE_NORM ? 1 : ncols + (MODE == MODE_UPDATE_DOT && a.detect ? 1 : 0);
+  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, &st->counter);
   if (!last || tid != 0) return;
   if (MODE == MODE_DOT) {
     double al = st->coef[j];
@@ -564,22 +607,20 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
       st->k_eff = j;
     }
     st->maxabs = fmax(st->maxabs, fabs(al));
-  } else if (MODE == MODE_UPDATE_NORM) {
-    double b = sqrt(st->norm2);
-    st->beta[j] = b;
-    if (!isfinite(b)) {
-      dev_flag(a.status, LOVE_ERR_NAN);
-      st->done = 1;
-      st->k_eff = j;
-    } else if (j + 1 >= st->kmax) {
-      st->k_eff = st->kmax;
-      st->done = 1;
-    } else if (b <= st->tau * st->maxabs) {
-      st->k_eff = j + 1;
-      st->done = 1;
-    } else {
-      st->scal[j + 1] = 1.0 / b;
+  } else if (MODE == MODE_UPDATE_DOT) {
+    if (a.detect) {
+      double c2 = 0.0;
+      for (int i = 0; i < ncols; ++i) c2 += st->coef2[i] * st->coef2[i];
+      const double yn = st->coef2[ncols];
+      st->skip = c2 <= a.eta2 * yn;   // false for NaN: the second pass reports it
+      if (st->skip) {
+        st->n_skip += 1;
+        st->norm2 = yn;
+        finish_step(st, a.status, j);
+      }
     }
+  } else {
+    finish_step(st, a.status, j);
   }
 }
 
@@ -641,6 +682,8 @@ __global__ void k_state_init(LanczosState* st, int kmax, double tau) {
   st->counter2 = 0;
   st->cg_done = 0;
   st->cg_iters = 0;
+  st->skip = 0;
+  st->n_skip = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1158,8 +1201,8 @@ love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaSt
 }
 
 template <typename T>
-love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, double* alpha_h, double* beta_h,
-                        int* k_eff, cudaStream_t s) {
+love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int64_t ldq, double* alpha_h,
+                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s) {
   const GridHost& gh = ski->grid;
   const int dim = gh.dim;
   if (k < 1 || k > LOVE_MAX_K) return LOVE_ERR_ARG;
@@ -1198,6 +1241,8 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
   ta.partial = part.as<double2>();
   ta.st = st;
   ta.status = ski->status;
+  ta.detect = eta > 0.0;
+  ta.eta2 = eta * eta;
   for (int j = 0; j < k; ++j) {
     // u = W q_j (q_j stored unnormalised, scaled by scal[j])
     LOVE_TRY(scatter_any<T>(ski, Q + (int64_t)j * ldq, st->scal + j, T(1), u1, s));
@@ -1205,16 +1250,22 @@ love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, dou
     // y = W^T u + s^2 q_j (q_j normalised in place)
     LOVE_TRY(lanczos_gather_any<T>(ski, u2, Q + (int64_t)j * ldq, y.as<T>(), st, j, s));
     ta.j = j;
+    ta.y = y.as<T>();
     LOVE_TRY(tile_run<T, MODE_DOT>(ta, s));
     LOVE_TRY(tile_run<T, MODE_UPDATE_DOT>(ta, s));
+    // detection mode: y' sits in the slot of q_{j+1}; the second pass works
+    // in place there (and returns at once when the step was finished)
+    if (ta.detect && j + 1 < k) ta.y = Q + (int64_t)(j + 1) * ldq;
     LOVE_TRY(tile_run<T, MODE_UPDATE_NORM>(ta, s));
   }
-  int keff = 0;
+  int keff = 0, nskip = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&nskip, &st->n_skip, sizeof(int), cudaMemcpyDeviceToHost, s));
   LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));
   LOVE_CUDA(cudaMemcpyAsync(alpha_h, st->alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   LOVE_CUDA(cudaMemcpyAsync(beta_h, st->beta, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   LOVE_CUDA(cudaStreamSynchronize(s));
   *k_eff = keff;
+  if (skipped) *skipped = nskip;
   return LOVE_OK;
 }
 
@@ -1708,9 +1759,10 @@ love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, c
 
 template love_status ski_mvm_sorted<float>(love_ski*, const float*, float*, void*, cudaStream_t);
 template love_status ski_mvm_sorted<double>(love_ski*, const double*, double*, void*, cudaStream_t);
-template love_status lanczos_run<float>(love_ski*, int, double, float*, int64_t, double*, double*, int*, cudaStream_t);
-template love_status lanczos_run<double>(love_ski*, int, double, double*, int64_t, double*, double*, int*,
-                                         cudaStream_t);
+template love_status lanczos_run<float>(love_ski*, int, double, double, float*, int64_t, double*, double*, int*,
+                                        int*, cudaStream_t);
+template love_status lanczos_run<double>(love_ski*, int, double, double, double*, int64_t, double*, double*, int*,
+                                         int*, cudaStream_t);
 template love_status scatter_multi<float>(love_ski*, const float*, int64_t, int, float*, int64_t, cudaStream_t);
 template love_status scatter_multi<double>(love_ski*, const double*, int64_t, int, double*, int64_t, cudaStream_t);
 template love_status cg_solve<float>(love_ski*, const float*, double*, double, int, int*, cudaStream_t);

@@ -422,6 +422,12 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   const Allocator& al = ski->alloc;
   int k = std::min<int64_t>(o->k, std::min<int64_t>(ski->n, g.m));
   double tau = o->breakdown_tol > 0 ? o->breakdown_tol : (sizeof(T) == 8 ? 1e-12 : 1e-8);
+  if (o->reorth != LOVE_REORTH_ALWAYS && o->reorth != LOVE_REORTH_DETECT) return LOVE_ERR_ARG;
+  // DETECT: skip the second pass while |Q_j^T y'| <= eta |y'|, eta = 4 units
+  // of rounding of the Q storage type unless given
+  const double eta = o->reorth != LOVE_REORTH_DETECT
+                         ? 0.0
+                         : (o->reorth_eta > 0 ? o->reorth_eta : (sizeof(T) == 8 ? 0x1p-51 : 0x1p-22));
   unsigned flags = o->flags;
   if (!ski->ys) flags &= ~LOVE_WANT_MEAN;
   const bool want_mean = (flags & LOVE_WANT_MEAN) != 0;
@@ -474,10 +480,10 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     if (mj.th.joinable()) mj.th.join();
   };
   std::vector<double> alpha(k + 1), beta(k + 1);
-  int keff = 0;
+  int keff = 0, skipped = 0;
   PhaseEvents ev;
   ev.record(0, s);
-  love_status rc = lanczos_run<T>(ski, k, tau, Q, ldq, alpha.data(), beta.data(), &keff, s);
+  love_status rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, s);
   ev.record(1, s);
   if (rc != LOVE_OK) {
     join_mean();
@@ -506,6 +512,7 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     al.free(am, amb, s);
     return LOVE_ERR_OOM;
   }
+  c->reorth_skipped = skipped;
   std::copy(alpha.begin(), alpha.begin() + keff, c->alpha);
   std::copy(beta.begin(), beta.begin() + std::max(keff - 1, 0), c->beta);
   // n-space mean CG (3-D grids), on this stream
@@ -644,6 +651,7 @@ love_status love_cache_info(love_cache_t c, love_cache_info_t* info) {
   info->cache_dtype = c->cache_dtype;
   info->flags = c->flags;
   for (int i = 0; i < 4; ++i) info->phase_ms[i] = c->phase_ms[i];
+  info->reorth_skipped = c->reorth_skipped;
   return LOVE_OK;
 }
 

@@ -347,6 +347,7 @@ struct love_cache {
   double* beta = nullptr;
   void* P = nullptr;           // m x k_eff column-major (dtype), kept for export
   int cg_iters = 0;
+  int reorth_skipped = 0;
   int sampler_fallback = 0;
   float phase_ms[4] = {0, 0, 0, 0};
   DevStatus* status = nullptr;
@@ -376,8 +377,8 @@ love_status kuu_apply(const GridHost& g, const FftPlan* plans, const T* v, T* ou
 // k_lanczos.cu
 struct LanczosWork;
 template <typename T>
-love_status lanczos_run(love_ski* ski, int k, double tau, T* Q, int64_t ldq, double* alpha_h,
-                        double* beta_h, int* k_eff, cudaStream_t s);
+love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int64_t ldq, double* alpha_h,
+                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s);
 template <typename T>
 love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaStream_t s);
 template <typename T>

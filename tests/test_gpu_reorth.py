@@ -1,0 +1,113 @@
+"""GPU checks of the detection-triggered reorthogonalisation (reorth="detect"):
+the Lanczos run of Sec. 3.2 with the second Gram-Schmidt pass of Sec. 5 taken
+only where the first pass left |Q_j^T y'| > eta |y'|.
+
+* With eta below any measurable component the second pass runs at every step
+  and the arithmetic is the same as reorth="always" (the first-pass vector is
+  only stored in another slot), so the caches agree bit for bit.
+* With the default eta the cache meets the same FP64-oracle tolerances as the
+  two-pass run (|d var| / p <= 1e-6 for FP32, 1e-9 relative for FP64).
+* Near Krylov exhaustion (k close to m) the first pass cancels most of y and
+  the test must call for the second pass at some steps.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import gpu_ski, oracle_cache, small_workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def love():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1803_06058_gb300 as pkg
+    return pkg
+
+
+def _var(love, cache, xs, dtype):
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    m, v = love.love_predict_mean_var(cache, torch.tensor(xs, dtype=tdt, device="cuda"), want_mean=True)
+    return m.double().cpu().numpy(), v.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dim,g,dtype", [(1, 200, "f32"), (2, 32, "f32"), (3, 14, "f32"), (1, 200, "f64")])
+def test_detect_with_tiny_eta_is_the_two_pass_run(love, dim, g, dtype):
+    wl = small_workload(dim=dim, g=g, n=20000, k=40, t=500, dtype=dtype, ls=0.1 if dim == 1 else 0.2,
+                        noise=0.0025)
+    ski = gpu_ski(love, torch, wl)
+    c2 = love.love_precompute(ski, k=40, reorth="always")
+    cd = love.love_precompute(ski, k=40, reorth="detect", reorth_eta=1e-150)
+    assert cd.info()["reorth_skipped"] == 0 and c2.info()["reorth_skipped"] == 0
+    e2, ed = love.love_cache_export(c2), love.love_cache_export(cd)
+    assert np.array_equal(e2["alpha"], ed["alpha"]) and np.array_equal(e2["beta"], ed["beta"])
+    assert np.array_equal(e2["Rt"], ed["Rt"])
+    xs = np.asarray(wl.x_test(), np.float64)
+    for a, b in zip(_var(love, c2, xs, dtype), _var(love, cd, xs, dtype)):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dim,g,n,k", [(1, 200, 20000, 40), (2, 32, 20000, 40), (3, 14, 20000, 40)])
+def test_detect_fp32_matches_oracle(love, dim, g, n, k):
+    from oracle import love as ol
+    wl = small_workload(dim=dim, g=g, n=n, k=k, t=2000, ls=0.1 if dim == 1 else 0.2, noise=0.0025)
+    ski_o, c_o = oracle_cache(wl)
+    ski = gpu_ski(love, torch, wl)
+    cache = love.love_precompute(ski, k=k, reorth="detect")
+    inf = cache.info()
+    assert 0 <= inf["reorth_skipped"] <= inf["k_eff"]
+    xs = np.asarray(wl.x_test(), np.float32).astype(np.float64)
+    m, v = _var(love, cache, xs, "f32")
+    m_ref, v_ref = ol.predict(c_o, xs)
+    p = ol.prior(c_o.grid, xs)
+    assert np.all(v >= 0) and np.all(v <= p * (1 + 1e-6))
+    assert np.max(np.abs(v - v_ref) / p) <= 1e-6
+    assert np.max(np.abs(m - m_ref)) <= 1e-4 * np.std(ski_o.y)
+
+
+def test_detect_fp64_matches_oracle(love):
+    from oracle import love as ol
+    wl = workloads.C1
+    _, c_o = oracle_cache(wl, cg_tol=1e-12)
+    ski = gpu_ski(love, torch, wl)
+    cache = love.love_precompute(ski, k=wl.k, reorth="detect")
+    xs = wl.x_test()
+    m, v = _var(love, cache, xs, "f64")
+    m_ref, v_ref = ol.predict(c_o, xs)
+    np.testing.assert_allclose(v, v_ref, rtol=1e-9)
+    np.testing.assert_allclose(m, m_ref, atol=1e-9)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_detect_calls_the_second_pass_near_exhaustion(love, dtype):
+    """m = 30 grid points, k = 30 steps: beta_j falls by orders of magnitude
+    as the Krylov space fills, the first pass cancels most of y and the
+    detection must run the second pass at some steps; the result still meets
+    the oracle where the two-pass run does."""
+    from oracle import love as ol
+    wl = small_workload(dim=1, g=30, n=5000, k=30, t=400, dtype=dtype, ls=0.3, noise=0.01)
+    _, c_o = oracle_cache(wl)
+    ski = gpu_ski(love, torch, wl)
+    c2 = love.love_precompute(ski, k=30, reorth="always")
+    cd = love.love_precompute(ski, k=30, reorth="detect")
+    inf = cd.info()
+    assert inf["reorth_skipped"] < inf["k_eff"]
+    xs = np.asarray(wl.x_test(), np.float64)
+    p = ol.prior(c_o.grid, xs)
+    _, v_ref = ol.predict(c_o, xs)
+    _, v2 = _var(love, c2, xs, dtype)
+    _, vd = _var(love, cd, xs, dtype)
+    e2 = np.max(np.abs(v2 - v_ref) / p)
+    ed = np.max(np.abs(vd - v_ref) / p)
+    tol = 1e-6 if dtype == "f32" else 1e-12
+    assert e2 <= tol and ed <= tol
+
+
+def test_reorth_mode_is_validated(love):
+    wl = small_workload(dim=1, g=40, n=500, k=8, t=10)
+    ski = gpu_ski(love, torch, wl)
+    with pytest.raises(KeyError):
+        love.love_precompute(ski, k=8, reorth="sometimes")
