@@ -141,6 +141,9 @@ typedef struct {
   uint64_t sampler_seed;   /* SplitMix64 seed of the Rademacher probe          */
   int reorth;              /* LOVE_REORTH_ALWAYS (0) or LOVE_REORTH_DETECT (1) */
   double reorth_eta;       /* DETECT threshold on |Q_j^T y'| / |y'|; <=0: 2^-22 (F32) / 2^-51 (F64) */
+  int cg_plain;            /* 1: the mean CG without preconditioner (Sec. 2.1); 0: on a 1-D grid
+                              the grid-space CG is preconditioned by the spectral inverse of
+                              B K_UU + s^2 I (B the averaged stencil of W W^T); same stopping rule */
 } love_precompute_opts;
 
 /* Reorthogonalisation of the Lanczos runs over K^ (love_precompute.reorth).

@@ -187,11 +187,12 @@ def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool =
                     want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
                     breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
                     sampler_k: int = 0, sampler_seed: int = 0, reorth: str = "always", reorth_eta: float = 0.0,
-                    stream=None) -> Cache:
+                    cg_plain: bool = False, stream=None) -> Cache:
     """reorth: "always" (two Gram-Schmidt passes every step) or "detect" (the
-    second pass only where |Q_j^T y'| > reorth_eta |y'|)."""
+    second pass only where |Q_j^T y'| > reorth_eta |y'|).  cg_plain: mean CG
+    without the spectral preconditioner (1-D grids use it by default)."""
     o = _opts(ski.dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,
-              cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta)
+              cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta, cg_plain)
     h = C.c_void_p()
     keff = C.c_int(0)
     check("love_precompute", lib().love_precompute(ski.handle, C.byref(o), _stream(stream),
@@ -203,7 +204,7 @@ _REORTH = {"always": 0, "detect": 1}
 
 
 def _opts(dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,
-          cg_max_iter, sampler_k, sampler_seed, reorth="always", reorth_eta=0.0):
+          cg_max_iter, sampler_k, sampler_seed, reorth="always", reorth_eta=0.0, cg_plain=False):
     o = _lib.love_precompute_opts()
     o.k = k
     o.cache_dtype = dtype if cache_dtype is None else _DT[cache_dtype]
@@ -216,6 +217,7 @@ def _opts(dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact
     o.sampler_seed = sampler_seed
     o.reorth = _REORTH[reorth]
     o.reorth_eta = reorth_eta
+    o.cg_plain = 1 if cg_plain else 0
     return o
 
 
@@ -223,13 +225,13 @@ def love_precompute_batched(skis: Sequence[Ski], k: int, cache_dtype: str = None
                             want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
                             breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
                             sampler_k: int = 0, sampler_seed: int = 0, workers: int = 0, reorth: str = "always",
-                            reorth_eta: float = 0.0, stream=None):
+                            reorth_eta: float = 0.0, cg_plain: bool = False, stream=None):
     """love_precompute for every ski (shared options), run concurrently; returns (caches, k_eff)."""
     B = len(skis)
     if B == 0:
         return [], []
     o = _opts(skis[0].dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol,
-              cg_tol, cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta)
+              cg_tol, cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta, cg_plain)
     hs = (C.c_void_p * B)(*[s.handle for s in skis])
     out = (C.c_void_p * B)()
     keff = (C.c_int * B)()

@@ -37,7 +37,8 @@ class love_precompute_opts(C.Structure):
     _fields_ = [("k", C.c_int), ("cache_dtype", C.c_int), ("flags", C.c_uint),
                 ("breakdown_tol", C.c_double), ("cg_tol", C.c_double),
                 ("cg_max_iter", C.c_int), ("sampler_k", C.c_int),
-                ("sampler_seed", C.c_uint64), ("reorth", C.c_int), ("reorth_eta", C.c_double)]
+                ("sampler_seed", C.c_uint64), ("reorth", C.c_int), ("reorth_eta", C.c_double),
+                ("cg_plain", C.c_int)]
 
 
 class love_cache_info_t(C.Structure):

@@ -59,6 +59,8 @@ struct LanczosState {
 
 namespace {
 
+constexpr int GM_R = 40;        // GMRES restart length (Arnoldi steps per cycle)
+constexpr int GM_CYCLES = 4;    // GMRES cycles before the mean solve falls back to plain CG
 constexpr int TILE_R = 128;     // rows per reorthogonalisation tile
 constexpr int TILE_T = 256;     // threads per tile CTA (two per row in the update)
 constexpr int NWARP = TILE_T / 32;
@@ -1607,16 +1609,91 @@ __global__ void k_mcg_start(int64_t m, const double* __restrict__ b, const doubl
   }
 }
 
+// ---- preconditioned grid-space solve (1-D grids) ------------------------------
+// M = B K + s^2 I, B the symmetric Toeplitz stencil of G = W W^T averaged over
+// the interior nodes (7 diagonals).  B and K are both Toeplitz, so on the
+// circulant embedding of length N, P = M^{-1} is approximated by the spectral
+// multiplier 1 / (lambda_B lambda_K + s^2) applied to the zero-padded vector
+// and cropped back to the grid.  P does not commute with K exactly (the crop),
+// so it is used as a right preconditioner of GMRES rather than inside CG.
+
+// bhat[d] = average over interior nodes of (G[node, node+d] + G[node, node-d]) / 2;
+// bhat[4] = fraction of interior nodes whose G_ii is below a fifth of the
+// average (empty stretches of the grid, where the stencil does not fit)
+__global__ void k_pcg_stencil(const double* __restrict__ G, int64_t m, double* __restrict__ bhat) {
+  __shared__ double red[4][256];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t lo = 6, hi = m - 6;   // nodes whose 7-wide band sees the whole data range
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    acc[0] += G[3 * m + i];
+#pragma unroll
+    for (int d = 1; d < 4; ++d) acc[d] += 0.5 * (G[(int64_t)(3 + d) * m + i] + G[(int64_t)(3 - d) * m + i]);
+  }
+#pragma unroll
+  for (int d = 0; d < 4; ++d) red[d][threadIdx.x] = acc[d];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int d = 0; d < 4; ++d) red[d][threadIdx.x] += red[d][threadIdx.x + w];
+    __syncthreads();
+  }
+  const double b0 = hi > lo ? red[0][0] / (double)(hi - lo) : 0.0;
+  if (threadIdx.x < 4) bhat[threadIdx.x] = hi > lo ? red[threadIdx.x][0] / (double)(hi - lo) : 0.0;
+  __syncthreads();
+  double cnt = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) cnt += G[3 * m + i] < 0.2 * b0 ? 1.0 : 0.0;
+  red[0][threadIdx.x] = cnt;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[0][threadIdx.x] += red[0][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bhat[4] = hi > lo ? red[0][0] / (double)(hi - lo) : 1.0;
+}
+
+// symbol of P on the embedding (stored / N like the K_UU spectrum) and the
+// largest eigenvalue of K's circulant embedding (>= the largest of K)
+__global__ void k_pcg_symbol(const double* __restrict__ lamK, int64_t N, const double* __restrict__ bhat, double noise,
+                             double* __restrict__ sym, unsigned long long* __restrict__ lk_bits) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double lb = bhat[0];
+#pragma unroll
+  for (int d = 1; d < 4; ++d) lb += 2.0 * bhat[d] * cospi(2.0 * (double)(d * j % N) / (double)N);
+  const double lk = fmax((double)N * lamK[j], 0.0);
+  sym[j] = 1.0 / ((fmax(lb, 0.0) * lk + noise) * (double)N);
+  atomicMax(lk_bits, (unsigned long long)__double_as_longlong(lk));   // lk >= 0: bit order = value order
+}
+
 }  // namespace
 
 bool mean_grid_cg_supported(const love_ski* ski) { return ski->grid.dim <= 2 && !ski->grid.additive; }
 
 template <typename T>
-love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s) {
+love_status mean_grid_gmres(love_ski* ski, double tol, int max_iter, double* a, int* iters, bool* converged,
+                            cudaStream_t s);
+
+template <typename T>
+love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s,
+                         bool precond) {
   const GridHost& gh = ski->grid;
   const GridDev g = gh.dev();
   const int dim = gh.dim;
   if (dim > 2) return LOVE_ERR_UNSUPPORTED;
+  int pre_iters = 0;
+  if (precond && dim == 1 && gh.g[0] >= 16) {
+    // the averaged stencil fits G where the training points are spread over
+    // the grid; where they are not (clusters, gaps) the GMRES setup declines
+    // (more than 10 % of the interior nearly empty) or, should it stall, the
+    // plain CG below takes over from zero after GM_CYCLES restarts
+    bool conv = false;
+    LOVE_TRY(mean_grid_gmres<T>(ski, tol, std::min(max_iter, GM_CYCLES * GM_R), a, &pre_iters, &conv, s));
+    if (conv || pre_iters >= max_iter) {
+      if (iters) *iters = pre_iters;
+      return LOVE_OK;
+    }
+    max_iter -= pre_iters;
+  }
   const int64_t m = gh.m, n = ski->n;
   const int B = dim == 1 ? 7 : 49;
   DevBuf stb(ski->alloc, s), part(ski->alloc, s), Gb(ski->alloc, s), vec(ski->alloc, s), yb(ski->alloc, s),
@@ -1682,11 +1759,11 @@ love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int
   int n_it = 0;
   LOVE_CUDA(cudaMemcpyAsync(&n_it, &st->cg_iters, sizeof(int), cudaMemcpyDeviceToHost, s));
   LOVE_CUDA(cudaStreamSynchronize(s));
-  if (iters) *iters = n_it;
+  if (iters) *iters = pre_iters + n_it;
   return LOVE_OK;
 }
-template love_status mean_grid_cg<float>(love_ski*, double, int, double*, int*, cudaStream_t);
-template love_status mean_grid_cg<double>(love_ski*, double, int, double*, int*, cudaStream_t);
+template love_status mean_grid_cg<float>(love_ski*, double, int, double*, int*, cudaStream_t, bool);
+template love_status mean_grid_cg<double>(love_ski*, double, int, double*, int*, cudaStream_t, bool);
 
 // cache build: Rt = K_UU W Q L^{-T}; a = K_UU W z; packed rows [Rt | a | 0]
 template <typename T>
@@ -1924,5 +2001,287 @@ template love_status sampler_lanczos<float>(const GridHost&, const FftPlan*, con
 template love_status sampler_lanczos<double>(const GridHost&, const FftPlan*, const Allocator&, const double*,
                                              int64_t, int, int, uint64_t, double, double*, int64_t, double*, double*,
                                              int*, DevStatus*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Right-preconditioned GMRES for the grid-space mean system (1-D grids):
+// A z = W y with A = G K_UU + s^2 I (G = W W^T banded), a = K_UU z; solved as
+// A P u = W y, z = P u, with P the spectral approximation of (B K_UU + s^2 I)^{-1}.
+// The Arnoldi basis V (m_pad x (R + 1), FP64) is orthogonalised by the same
+// CGS2 tile kernels as the Lanczos runs; the Hessenberg columns go through
+// Givens rotations on the device, so |g_{j+1}| is the Euclidean residual of
+// the current iterate.  The solve stops when |g_{j+1}|^2 <= tol^2 s^2 |y|^2 /
+// (2 lambda_max(K)), which implies the CG stopping rule r^T K r <= tol^2 s^2 |y|^2
+// for the recursively updated residual (as the plain CG applies it); a cycle
+// that ends without meeting it restarts from the recomputed residual b - A z.
+namespace {
+
+struct GmresState {
+  double H[(GM_R + 1) * GM_R];   // rotated Hessenberg columns (upper triangle), ld GM_R + 1
+  double cs[GM_R], sn[GM_R];
+  double g[GM_R + 1];
+  double y[GM_R];
+  int ncols;
+  int converged;
+  double target2;
+  unsigned long long lk_bits;   // largest eigenvalue of K's circulant embedding
+};
+
+__global__ void k_gm_target(GmresState* gm, const LanczosState* cg) {
+  const double lk = __longlong_as_double((long long)gm->lk_bits);
+  gm->target2 = 0.5 * cg->tol2 / fmax(lk, 1e-300);
+}
+
+// V[:, 0] = r (zero past m); g = (|r|, 0, ...); scal_0 = 1 / |r|
+__global__ void k_gm_start(int64_t m, int64_t m_pad, const double* __restrict__ r, double* __restrict__ v0,
+                           double2* partial, LanczosState* st, GmresState* gm, DevStatus* status) {
+  __shared__ DotAccD red[32];
+  DotAccD a;
+  a.zero();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = i < m ? r[i] : 0.0;
+    v0[i] = v;
+    a.add_prod(v, v);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter);
+  if (last && threadIdx.x == 0) {
+    const double b2 = st->norm2, b = sqrt(b2);
+    gm->g[0] = b;
+    for (int i = 1; i <= GM_R; ++i) gm->g[i] = 0.0;
+    gm->ncols = 0;
+    st->scal[0] = b > 0.0 ? 1.0 / b : 0.0;
+    if (!isfinite(b2)) dev_flag(status, LOVE_ERR_NAN);
+    if (!(b2 > gm->target2)) {
+      st->done = 1;
+      st->k_eff = 0;
+      gm->converged = 1;
+    }
+  }
+}
+
+// y = G (K P v) + s^2 (P v) over the padded rows (zero past m)
+__global__ void k_gm_band(int64_t m, int64_t m_pad, const double* __restrict__ G, const double* __restrict__ kv,
+                          const double* __restrict__ pv, double noise, double* __restrict__ y,
+                          const LanczosState* st) {
+  if (st->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_pad; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    if (i < m) {
+#pragma unroll
+      for (int o = 0; o < 7; ++o) {
+        const int64_t nb = i + o - 3;
+        if (nb >= 0 && nb < m) acc = fma(G[(int64_t)o * m + i], kv[nb], acc);
+      }
+      acc = fma(noise, pv[i], acc);
+    }
+    y[i] = acc;
+  }
+}
+
+// Hessenberg column j: h_ij = c_i + c'_i (the two Gram-Schmidt passes), h_{j+1,j}
+// = beta_j; earlier rotations, then the rotation that zeroes h_{j+1,j}
+__global__ void k_gm_givens(LanczosState* st, GmresState* gm, int j, DevStatus* status) {
+  if (j >= st->k_eff || gm->ncols != j) return;
+  double h[GM_R + 1];
+  for (int i = 0; i <= j; ++i) h[i] = st->coef[i] + st->coef2[i];
+  h[j + 1] = st->beta[j];
+  for (int i = 0; i < j; ++i) {
+    const double t = gm->cs[i] * h[i] + gm->sn[i] * h[i + 1];
+    h[i + 1] = -gm->sn[i] * h[i] + gm->cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double r = hypot(h[j], h[j + 1]);
+  const double c = r > 0.0 ? h[j] / r : 1.0, sn = r > 0.0 ? h[j + 1] / r : 0.0;
+  gm->cs[j] = c;
+  gm->sn[j] = sn;
+  h[j] = r;
+  gm->g[j + 1] = -sn * gm->g[j];
+  gm->g[j] = c * gm->g[j];
+  for (int i = 0; i <= j; ++i) gm->H[(int64_t)j * (GM_R + 1) + i] = h[i];
+  gm->ncols = j + 1;
+  if (!isfinite(gm->g[j + 1])) {
+    dev_flag(status, LOVE_ERR_NAN);
+    gm->converged = 1;   // nothing more to gain; the status reports it
+    st->done = 1;
+    st->k_eff = j;
+    gm->ncols = j;
+  } else if (gm->g[j + 1] * gm->g[j + 1] <= gm->target2) {
+    st->done = 1;
+    st->k_eff = j + 1;
+    gm->converged = 1;
+  }
+}
+
+// R y = g by back substitution (ncols columns)
+__global__ void k_gm_solve(GmresState* gm) {
+  const int kc = gm->ncols;
+  for (int i = kc - 1; i >= 0; --i) {
+    double v = gm->g[i];
+    for (int l = i + 1; l < kc; ++l) v -= gm->H[(int64_t)l * (GM_R + 1) + i] * gm->y[l];
+    const double d = gm->H[(int64_t)i * (GM_R + 1) + i];
+    gm->y[i] = d != 0.0 ? v / d : 0.0;
+  }
+}
+
+// u = V y
+__global__ void k_gm_combine(int64_t m, const double* __restrict__ V, int64_t ldv, const GmresState* gm,
+                             double* __restrict__ u) {
+  const int kc = gm->ncols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < kc; ++c) acc = fma(V[(int64_t)c * ldv + i], gm->y[c], acc);
+    u[i] = acc;
+  }
+}
+
+__global__ void k_gm_add(int64_t m, double* __restrict__ z, const double* __restrict__ d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] += d[i];
+}
+
+// r = b - (G K z + s^2 z)
+__global__ void k_gm_resid(int64_t m, const double* __restrict__ G, const double* __restrict__ kz,
+                           const double* __restrict__ z, const double* __restrict__ b, double noise,
+                           double* __restrict__ r) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+      const int64_t nb = i + o - 3;
+      if (nb >= 0 && nb < m) acc = fma(G[(int64_t)o * m + i], kz[nb], acc);
+    }
+    r[i] = b[i] - fma(noise, z[i], acc);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+love_status mean_grid_gmres(love_ski* ski, double tol, int max_iter, double* a, int* iters, bool* converged,
+                            cudaStream_t s) {
+  const GridHost& gh = ski->grid;
+  const GridDev g = gh.dev();
+  const int64_t m = gh.m, n = ski->n;
+  const int64_t m_pad = (m + TILE_R - 1) / TILE_R * TILE_R;
+  const FftPlan& kp = ski->fft[0];
+  const int bc = box_cols(sizeof(double));
+  const int max_grid = std::max(TILE_CTAS_PER_SM * num_sms(), 1024);
+  DevBuf stb(ski->alloc, s), cgb(ski->alloc, s), gmb(ski->alloc, s), part(ski->alloc, s), Gb(ski->alloc, s),
+      vec(ski->alloc, s), Vb(ski->alloc, s), yb(ski->alloc, s), fw(ski->alloc, s), symb(ski->alloc, s);
+  size_t fwb = fft_work_bytes(gh, ski->fft, 1, true);
+  const bool conv = sizeof(T) != sizeof(double);
+  if (!stb.get(sizeof(LanczosState)) || !cgb.get(sizeof(LanczosState)) || !gmb.get(sizeof(GmresState)) ||
+      !part.get(sizeof(double2) * (size_t)max_grid * (GM_R + 2)) || !Gb.get(sizeof(double) * 7 * m) ||
+      !vec.get(sizeof(double) * (6 * m + m_pad)) || !Vb.get(sizeof(double) * m_pad * (GM_R + 1)) ||
+      (conv && !yb.get(sizeof(double) * std::max<int64_t>(n, 1))) || !fw.get(std::max<size_t>(fwb, 16)) ||
+      !symb.get(sizeof(double) * (kp.N + 8)))
+    return LOVE_ERR_OOM;
+  LanczosState* st = stb.as<LanczosState>();   // Arnoldi state (tile kernels)
+  LanczosState* cg = cgb.as<LanczosState>();   // |y|^2 and the stopping threshold
+  GmresState* gm = gmb.as<GmresState>();
+  double* v = vec.as<double>();
+  double *b = v, *r = v + m, *z = v + 2 * m, *pv = v + 3 * m, *kv = v + 4 * m, *u = v + 5 * m, *yv = v + 6 * m;
+  double* V = Vb.as<double>();
+  double* sym = symb.as<double>();
+  double* bhat = sym + kp.N;
+  double2* pp = part.as<double2>();
+  const int sblocks = (int)std::min<int64_t>((m * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  const int mblocks = (int)std::min<int64_t>(ceil_div(m_pad, 256), 1024);
+  const int nblocks = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(n, 1), 256), 1024);
+  FftPlan pplan = kp;   // the same transform with the spectrum of P
+  pplan.lam_d = sym;
+  auto kmul = [&](const double* in, double* out) -> love_status {
+    return kuu_apply<double>(gh, ski->fft, in, out, 1, m, fw.p, -1, s);
+  };
+  auto pmul = [&](const double* in, double* out) -> love_status {
+    return kuu_apply<double>(gh, &pplan, in, out, 1, m, fw.p, -1, s);
+  };
+  LOVE_CUDA(cudaMemsetAsync(gm, 0, sizeof(GmresState), s));
+  LOVE_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * m, s));
+  LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(cg, 1, 0.0);
+  LOVE_COUNT_LAUNCH(); k_gram_band<T, 1><<<sblocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Gb.as<double>());
+  LOVE_COUNT_LAUNCH(); k_pcg_stencil<<<1, 256, 0, s>>>(Gb.as<double>(), m, bhat);
+  LOVE_LAUNCH_CHECK();
+  {
+    // more than 10 % of the interior nearly empty: leave the solve to the CG
+    double empty = 1.0;
+    LOVE_CUDA(cudaMemcpyAsync(&empty, bhat + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    if (!(empty <= 0.1)) {
+      *iters = 0;
+      return LOVE_OK;
+    }
+  }
+  LOVE_COUNT_LAUNCH();
+  k_pcg_symbol<<<ceil_div(kp.N, 256), 256, 0, s>>>((const double*)kp.lam_d, kp.N, bhat, gh.noise, sym, &gm->lk_bits);
+  const double* yd = conv ? yb.as<double>() : (const double*)ski->ys;
+  LOVE_COUNT_LAUNCH();
+  k_mcg_ynorm<T><<<nblocks, 256, 0, s>>>(n, (const T*)ski->ys, conv ? yb.as<double>() : nullptr, tol, gh.noise, pp, cg);
+  LOVE_COUNT_LAUNCH(); k_gm_target<<<1, 1, 0, s>>>(gm, cg);
+  LOVE_LAUNCH_CHECK();
+  LOVE_TRY(scatter_any<T, double>(ski, yd, nullptr, 1.0, b, s));
+  LOVE_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  TileArgs<double> ta{};
+  ta.n_pad = m_pad;
+  ta.kcols = GM_R + 1;
+  ta.bc = bc;
+  ta.Q = V;
+  ta.ldq = m_pad;
+  ta.y = yv;
+  ta.partial = pp;
+  ta.st = st;
+  ta.status = ski->status;
+  const int nb = std::min(4 * num_sms(), ceil_div(m_pad, 256));
+  int total = 0;
+  for (int cycle = 0; total < max_iter; ++cycle) {
+    LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, GM_R, 1e-14);
+    LOVE_COUNT_LAUNCH(); k_gm_start<<<mblocks, 256, 0, s>>>(m, m_pad, r, V, pp, st, gm, ski->status);
+    LOVE_LAUNCH_CHECK();
+    const int steps = std::min(GM_R, max_iter - total);
+    for (int j = 0; j < steps; ++j) {
+      double* vj = V + (int64_t)j * m_pad;
+      LOVE_COUNT_LAUNCH(); k_normalize_col<<<nb, 256, 0, s>>>(vj, m_pad, st->scal + j, st);
+      LOVE_TRY(pmul(vj, pv));
+      LOVE_TRY(kmul(pv, kv));
+      LOVE_COUNT_LAUNCH(); k_gm_band<<<mblocks, 256, 0, s>>>(m, m_pad, Gb.as<double>(), kv, pv, gh.noise, yv, st);
+      LOVE_LAUNCH_CHECK();
+      ta.j = j;
+      LOVE_TRY(tile_run<double, MODE_DOT>(ta, s));
+      LOVE_TRY(tile_run<double, MODE_UPDATE_DOT>(ta, s));
+      LOVE_TRY(tile_run<double, MODE_UPDATE_NORM>(ta, s));
+      LOVE_COUNT_LAUNCH(); k_gm_givens<<<1, 1, 0, s>>>(st, gm, j, ski->status);
+      LOVE_LAUNCH_CHECK();
+      if (j % 6 == 5) {   // stop launching once the cycle has converged
+        int done = 0;
+        LOVE_CUDA(cudaMemcpyAsync(&done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LOVE_CUDA(cudaStreamSynchronize(s));
+        if (done) break;
+      }
+    }
+    // z += P V y; a = K z
+    LOVE_COUNT_LAUNCH(); k_gm_solve<<<1, 1, 0, s>>>(gm);
+    LOVE_COUNT_LAUNCH(); k_gm_combine<<<mblocks, 256, 0, s>>>(m, V, m_pad, gm, u);
+    LOVE_TRY(pmul(u, pv));
+    LOVE_COUNT_LAUNCH(); k_gm_add<<<mblocks, 256, 0, s>>>(m, z, pv);
+    LOVE_TRY(kmul(z, a));
+    LOVE_LAUNCH_CHECK();
+    int hs[2] = {0, 0};   // columns, converged
+    LOVE_CUDA(cudaMemcpyAsync(&hs[0], &gm->ncols, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaMemcpyAsync(&hs[1], &gm->converged, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    total += hs[0];
+    if (hs[1]) *converged = true;
+    if (hs[1] || hs[0] == 0) break;   // converged, or no progress possible
+    // restart from the recomputed residual r = b - A z
+    LOVE_COUNT_LAUNCH(); k_gm_resid<<<mblocks, 256, 0, s>>>(m, Gb.as<double>(), a, z, b, gh.noise, r);
+    LOVE_LAUNCH_CHECK();
+  }
+  if (iters) *iters = total;
+  return LOVE_OK;
+}
+
+template love_status mean_grid_gmres<float>(love_ski*, double, int, double*, int*, bool*, cudaStream_t);
+template love_status mean_grid_gmres<double>(love_ski*, double, int, double*, int*, bool*, cudaStream_t);
 
 }  // namespace love

@@ -462,13 +462,14 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     }
     int dev = 0;
     cudaGetDevice(&dev);
-    mj.th = std::thread([ski, cg_tol, cg_maxit, am, s2, dev, &mj] {
+    const bool precond = o->cg_plain == 0;
+    mj.th = std::thread([ski, cg_tol, cg_maxit, am, s2, dev, precond, &mj] {
       cudaSetDevice(dev);
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s2);
-      mj.rc = mean_grid_cg<T>(ski, cg_tol, cg_maxit, am, &mj.iters, s2);
+      mj.rc = mean_grid_cg<T>(ski, cg_tol, cg_maxit, am, &mj.iters, s2, precond);
       cudaEventRecord(e1, s2);
       cudaEventSynchronize(e1);
       cudaEventElapsedTime(&mj.ms, e0, e1);

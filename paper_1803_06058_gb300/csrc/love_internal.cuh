@@ -391,7 +391,8 @@ love_status cg_solve(love_ski* ski, const T* b, double* x, double tol, int max_i
 // (G K_UU + s^2 I) z = W y with G = W W^T; dimensions 1 and 2
 bool mean_grid_cg_supported(const love_ski* ski);
 template <typename T>
-love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s);
+love_status mean_grid_cg(love_ski* ski, double tol, int max_iter, double* a, int* iters, cudaStream_t s,
+                         bool precond);
 // write mean weights a (m, FP64) into the cache's mean column
 love_status cache_set_mean(love_cache* c, const double* a, cudaStream_t s);
 // zmean: K^^-1 y (n-vector, cell-sorted) or amean: the mean weights themselves
