@@ -20,6 +20,7 @@
 // The twiddle table W_N^j and lambda are computed once per grid in FP64.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "love_internal.cuh"
 #include "fft_core.cuh"
@@ -197,6 +198,92 @@ __global__ void k_four_c(const typename Cplx<R>::type* __restrict__ work, IO* __
   }
 }
 
+// ----- short modes: dense double-float product ------------------------------
+// out[f, i] = sum_j c[|i - j|] x[f, j] for TF fibres per CTA (every output i
+// of them, so a product in place is safe): the fibres' inputs, the column of
+// T (float pairs) and the outputs in shared memory; thread t takes the outputs
+// i = i0 + t % 64 (i0 = 0, 64, ...) of TF / 4 fibres.  Products and sums in
+// double-float (two FP32 words, ~2^-46 relative per operation): the FP32
+// pipes run this several times faster than an FP64 FFT of the same mode.
+__device__ __forceinline__ void df_mac(float& s, float& t, float ch, float cl, float xh, float xl) {
+  const float p = ch * xh;
+  float e = fmaf(ch, xh, -p);
+  e = fmaf(ch, xl, e);
+  e = fmaf(cl, xh, e);
+  const float s2 = s + p;
+  const float bb = s2 - s;
+  t += ((s - (s2 - bb)) + (p - bb)) + e;
+  s = s2;
+}
+
+template <typename IO, int TF>
+__global__ void __launch_bounds__(256) k_toep_dense(const IO* __restrict__ in, IO* __restrict__ out, ModeGeom mg,
+                                                    int64_t total_fib, const float2* __restrict__ col) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int g = (int)mg.g;
+  float2* cs = reinterpret_cast<float2*>(smem_raw);   // [g]
+  float2* xs = cs + g;                                 // [TF][g] inputs
+  float2* ys = xs + (size_t)TF * g;                    // [TF][g] outputs
+  const int64_t fib0 = (int64_t)blockIdx.x * TF;
+  for (int r = threadIdx.x; r < g; r += blockDim.x) cs[r] = col[r];
+  // inputs: i fastest along a unit-stride mode, the fibre fastest otherwise
+  const bool unit = mg.stride == 1;
+  for (int t = threadIdx.x; t < TF * g; t += blockDim.x) {
+    const int f = unit ? t / g : t % TF;
+    const int i = unit ? t % g : t / TF;
+    const int64_t fb = fib0 + f;
+    double v = 0.0;
+    if (fb < total_fib) {
+      const int64_t c = fb / mg.nfib, fid = fb - c * mg.nfib;
+      v = (double)in[mg.offset(c, fid, i)];
+    }
+    const float h = (float)v;
+    xs[f * g + i] = make_float2(h, (float)(v - (double)h));
+  }
+  __syncthreads();
+  constexpr int NF = TF / 4;
+  const int fq = threadIdx.x >> 6;   // 4 groups of NF fibres
+  for (int i0 = 0; i0 < g; i0 += 64) {
+    const int i = i0 + (threadIdx.x & 63);
+    if (i >= g) continue;
+    float s[NF], t[NF];
+#pragma unroll
+    for (int u = 0; u < NF; ++u) s[u] = t[u] = 0.f;
+    for (int j = 0; j < g; ++j) {
+      const float2 c = cs[i > j ? i - j : j - i];
+#pragma unroll
+      for (int u = 0; u < NF; ++u) {
+        const float2 x = xs[(fq * NF + u) * g + j];
+        df_mac(s[u], t[u], c.x, c.y, x.x, x.y);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NF; ++u) ys[(fq * NF + u) * g + i] = make_float2(s[u], t[u]);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < TF * g; t += blockDim.x) {
+    const int f = unit ? t / g : t % TF;
+    const int i = unit ? t % g : t / TF;
+    const int64_t fb = fib0 + f;
+    if (fb < total_fib) {
+      const int64_t c = fb / mg.nfib, fid = fb - c * mg.nfib;
+      const float2 v = ys[f * g + i];
+      out[mg.offset(c, fid, i)] = (IO)((double)v.x + (double)v.y);
+    }
+  }
+}
+
+template <typename IO, int TF>
+love_status toep_dense_launch(const FftPlan& p, const IO* in, IO* out, ModeGeom mg, int64_t total, bool deriv,
+                              cudaStream_t s) {
+  const size_t sm = sizeof(float2) * (size_t)p.g * (1 + 2 * TF);
+  LOVE_TRY(allow_smem(k_toep_dense<IO, TF>, sm));
+  LOVE_COUNT_LAUNCH();
+  k_toep_dense<IO, TF><<<(unsigned)((total + TF - 1) / TF), 256, sm, s>>>(
+      in, out, mg, total, (const float2*)(deriv ? p.coldl2 : p.col2));
+  return cuda_check(cudaGetLastError());
+}
+
 // ----- plan set-up kernels ---------------------------------------------------
 __global__ void k_twiddles(double2* tw_d, float2* tw_f, int64_t N) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -270,6 +357,12 @@ template <typename IO, typename R>
 love_status toeplitz_mode(const FftPlan& p, const IO* in, IO* out, ModeGeom mg, int ncol, void* work,
                           bool deriv, cudaStream_t s) {
   using C = typename Cplx<R>::type;
+  if (p.col2 != nullptr && p.g <= TOEP_DENSE_MAX) {
+    // 16 fibres per CTA while that still gives two CTAs per SM, else 4
+    const int64_t total = mg.nfib * ncol;
+    if (total >= 16 * 2 * (int64_t)num_sms()) return toep_dense_launch<IO, 16>(p, in, out, mg, total, deriv, s);
+    return toep_dense_launch<IO, 4>(p, in, out, mg, total, deriv, s);
+  }
   const bool dbl = sizeof(R) == 8;
   const C* tw = (const C*)(dbl ? p.tw_d : p.tw_f);
   const R* lam = (const R*)(deriv ? (dbl ? p.lamdl_d : p.lamdl_f) : (dbl ? p.lam_d : p.lam_f));
@@ -323,7 +416,8 @@ __global__ void k_real_part(const double2* a, double* out, int64_t N) {
 
 }  // namespace
 
-love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocator& al, cudaStream_t s) {
+love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocator& al, cudaStream_t s,
+                            bool dense) {
   p.g = g.g[e];
   int64_t N = 4;
   while (N < 2 * p.g - 1) N <<= 1;
@@ -372,6 +466,25 @@ love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocato
                                       (float*)(deriv ? p.lamdl_f : p.lam_f));
   }
   LOVE_TRY(cuda_check(cudaGetLastError()));
+  if (dense && p.g <= TOEP_DENSE_MAX) {
+    // first columns of T_e and dT_e/dl for the dense product, as float pairs
+    const double scale = (e == 0 || g.additive) ? g.sf : 1.0;
+    std::vector<float2> hc((size_t)p.g), hd((size_t)p.g);
+    for (int64_t r = 0; r < p.g; ++r) {
+      const double d = (double)r * g.h[e];
+      const double v = scale * std::exp(-(d * d) / (2.0 * g.ls[e] * g.ls[e]));
+      const double vd = v * d * d / (g.ls[e] * g.ls[e] * g.ls[e]);
+      const float vh = (float)v, dh = (float)vd;
+      hc[(size_t)r] = make_float2(vh, (float)(v - (double)vh));
+      hd[(size_t)r] = make_float2(dh, (float)(vd - (double)dh));
+    }
+    p.col2 = al.alloc(sizeof(float2) * p.g, s);
+    p.coldl2 = al.alloc(sizeof(float2) * p.g, s);
+    if (!p.col2 || !p.coldl2) return LOVE_ERR_OOM;
+    LOVE_TRY(cuda_check(cudaMemcpyAsync(p.col2, hc.data(), sizeof(float2) * p.g, cudaMemcpyHostToDevice, s)));
+    LOVE_TRY(cuda_check(cudaMemcpyAsync(p.coldl2, hd.data(), sizeof(float2) * p.g, cudaMemcpyHostToDevice, s)));
+    LOVE_TRY(cuda_check(cudaStreamSynchronize(s)));   // the host columns go out of scope
+  }
   al.free(col, sizeof(double2) * N, s);
   al.free(X, sizeof(double2) * N, s);
   al.free(wk, sizeof(double2) * N, s);
@@ -386,6 +499,8 @@ void fft_plan_destroy(FftPlan& p, const Allocator& al, cudaStream_t s) {
   al.free(p.lam_f, sizeof(float) * p.N, s);
   al.free(p.lamdl_d, sizeof(double) * p.N, s);
   al.free(p.lamdl_f, sizeof(float) * p.N, s);
+  if (p.col2) al.free(p.col2, sizeof(float2) * p.g, s);
+  if (p.coldl2) al.free(p.coldl2, sizeof(float2) * p.g, s);
   p = FftPlan{};
 }
 

@@ -323,9 +323,12 @@ __device__ __forceinline__ void block_merge(Acc& a, Acc* sm) {
   a = sm[0];
 }
 
+// scratch: 8 x 32 double2 of shared memory for the wide form, or nullptr for
+// the narrow form (a given caller always takes the same form, so a sum's merge
+// order does not depend on how many sums are merged with it)
 template <typename Acc>
 __device__ bool last_cta_reduce(const double2* __restrict__ partial, int stride, int ncols, double* result,
-                                unsigned* counter) {
+                                unsigned* counter, double2* scratch = nullptr) {
   __shared__ int is_last;
   __threadfence();
   __syncthreads();
@@ -334,15 +337,47 @@ __device__ bool last_cta_reduce(const double2* __restrict__ partial, int stride,
   if (!is_last) return false;
   __threadfence();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = w; i < ncols; i += nw) {
-    Acc a;
-    a.zero();
-    for (int c = lane; c < (int)gridDim.x; c += 32) {
-      double2 p = __ldcg(partial + (int64_t)c * stride + i);
-      a.merge(p.x, p.y);
+  const int G = gridDim.x;
+  if (scratch == nullptr) {
+    // narrow: a warp per sum, lanes over the CTA partials
+    for (int i = w; i < ncols; i += nw) {
+      Acc a;
+      a.zero();
+#pragma unroll 8
+      for (int c = lane; c < G; c += 32) {
+        const double2 p = __ldcg(partial + (int64_t)c * stride + i);
+        a.merge(p.x, p.y);
+      }
+      warp_merge(a);
+      if (lane == 0) result[i] = a.value();
     }
-    warp_merge(a);
-    if (lane == 0) result[i] = a.value();
+  } else {
+    // wide: lanes over 32 consecutive sums (coalesced rows of the partial
+    // table), the first 8 warps over fixed eighths of the CTAs, then the eight
+    // warp sums in order
+    for (int i0 = 0; i0 < ncols; i0 += 32) {
+      const int i = i0 + lane;
+      Acc a;
+      a.zero();
+      if (w < 8 && i < ncols) {
+        const int cb = w * G / 8, ce = (w + 1) * G / 8;
+#pragma unroll 16
+        for (int c = cb; c < ce; ++c) {
+          const double2 p = __ldcg(partial + (int64_t)c * stride + i);
+          a.merge(p.x, p.y);
+        }
+      }
+      if (w < 8) scratch[w * 32 + lane] = make_double2((double)a.s, (double)a.c);
+      __syncthreads();
+      if (w == 0 && i < ncols) {
+        Acc t;
+        t.zero();
+#pragma unroll
+        for (int v = 0; v < 8; ++v) t.merge(scratch[v * 32 + lane].x, scratch[v * 32 + lane].y);
+        result[i] = t.value();
+      }
+      __syncthreads();
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
@@ -421,6 +456,65 @@ __device__ void finish_step(LanczosState* st, DevStatus* status, int j) {
     st->done = 1;
   } else {
     st->scal[j + 1] = 1.0 / b;
+  }
+}
+
+// End of a sweep (both kernel shapes): per-CTA partials of the column dots
+// (or of |y|^2), the last CTA's fixed-order merge, and the step's scalar work
+// (alpha_j; the detection test; beta_j, breakdown and the next scale).
+template <typename T, int MODE, int KPW>
+__device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename AccOf<T>::type (&acc)[KPW],
+                                               typename AccOf<T>::type& nacc, typename AccOf<T>::type* red,
+                                               double2* scratch) {
+  using Acc = typename AccOf<T>::type;
+  LanczosState* st = a.st;
+  const int j = a.j;
+  const int ncols = j + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // ---- CTA partials
+  const int pstride = a.kcols + 1;
+  if (MODE == MODE_UPDATE_NORM) {
+    block_merge(nacc, red);
+    if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride, nacc);
+  } else {
+#pragma unroll
+    for (int s2 = 0; s2 < KPW; ++s2) {
+      const int i = warp + NWARP * s2;
+      warp_merge(acc[s2]);
+      if (lane == 0 && i < ncols) acc_store(a.partial + (int64_t)blockIdx.x * pstride + i, acc[s2]);
+    }
+    if (MODE == MODE_UPDATE_DOT && a.detect) {   // |y'|^2 in slot j + 1
+      block_merge(nacc, red);
+      if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride + ncols, nacc);
+    }
+  }
+  double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
+  const int nres = MODE == MODE_UPDATE_NORM ? 1 : ncols + (MODE == MODE_UPDATE_DOT && a.detect ? 1 : 0);
+  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, &st->counter, scratch);
+  if (!last || tid != 0) return;
+  if (MODE == MODE_DOT) {
+    double al = st->coef[j];
+    st->alpha[j] = al;
+    if (!isfinite(al)) {
+      dev_flag(a.status, LOVE_ERR_NAN);
+      st->done = 1;
+      st->k_eff = j;
+    }
+    st->maxabs = fmax(st->maxabs, fabs(al));
+  } else if (MODE == MODE_UPDATE_DOT) {
+    if (a.detect) {
+      double c2 = 0.0;
+      for (int i = 0; i < ncols; ++i) c2 += st->coef2[i] * st->coef2[i];
+      const double yn = st->coef2[ncols];
+      st->skip = c2 <= a.eta2 * yn;   // false for NaN: the second pass reports it
+      if (st->skip) {
+        st->n_skip += 1;
+        st->norm2 = yn;
+        finish_step(st, a.status, j);
+      }
+    }
+  } else {
+    finish_step(st, a.status, j);
   }
 }
 
@@ -579,51 +673,122 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
     }
   }
 
-  // ---- CTA partials
-  const int pstride = a.kcols + 1;
-  if (MODE == MODE_UPDATE_NORM) {
-    block_merge(nacc, red);
-    if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride, nacc);
-  } else {
+  // every issued stage has been consumed: the ring is free for the merge
+  sweep_epilogue<T, MODE, KPW>(a, acc, nacc, red, reinterpret_cast<double2*>(smem_raw));
+}
+
+// The same three sweeps for short vectors (fewer row tiles than two per SM:
+// grid-sized Krylov bases, small training sets).  A CTA owns SMALL_R = 64 rows
+// and reads its rows of Q_j once, straight into registers (warp w: the columns
+// w, w + 8, ...; lane l: rows 2l, 2l + 1), so every load of the sweep is in
+// flight at once; y passes through shared memory between the update and the
+// dots.  Partials, merge and scalar work are those of the tiled sweep.
+constexpr int SMALL_R = 64;
+
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  static __device__ __forceinline__ void load(const float* p, float* v) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+};
+template <> struct Pair<double> {
+  static __device__ __forceinline__ void load(const double* p, double* v) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+};
+
+template <typename T, int MODE, int KPW>
+__global__ void __launch_bounds__(TILE_T) k_lanczos_small(const __grid_constant__ TileArgs<T> a) {
+  using Acc = typename AccOf<T>::type;
+  static_assert(SMALL_R == 64 && TILE_T == 256, "pair mapping assumes 64 rows, 8 warps");
+  __shared__ Acc red[NWARP];
+  __shared__ T hp[NWARP][SMALL_R];
+  __shared__ T ys[SMALL_R];
+  __shared__ T cf[LOVE_MAX_K + 8];
+  __shared__ double2 wsum[8 * 32];
+  LanczosState* st = a.st;
+  if (st->done || (MODE == MODE_UPDATE_NORM && a.detect && st->skip)) return;
+  const int j = a.j;
+  const int ncols = j + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
+    const double* c = MODE == MODE_UPDATE_DOT ? st->coef : st->coef2;
+    for (int i = tid; i < ncols; i += TILE_T) cf[i] = (T)c[i];
+  }
+  const int64_t row0 = (int64_t)blockIdx.x * SMALL_R;
+  const int r0 = 2 * lane;
+  T q[KPW][2];
+#pragma unroll
+  for (int s2 = 0; s2 < KPW; ++s2) {
+    const int i = warp + NWARP * s2;
+    if (i < ncols) {
+      Pair<T>::load(a.Q + (int64_t)i * a.ldq + row0 + r0, q[s2]);
+    } else {
+      q[s2][0] = T(0);
+      q[s2][1] = T(0);
+    }
+  }
+  if (tid < SMALL_R) ys[tid] = a.y[row0 + tid];
+  __syncthreads();
+  Acc acc[KPW];
+#pragma unroll
+  for (int s2 = 0; s2 < KPW; ++s2) acc[s2].zero();
+  Acc nacc;
+  nacc.zero();
+  // ---- update: y -= Q_j c
+  if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
+    T ps[2] = {T(0), T(0)};
 #pragma unroll
     for (int s2 = 0; s2 < KPW; ++s2) {
       const int i = warp + NWARP * s2;
-      warp_merge(acc[s2]);
-      if (lane == 0 && i < ncols) acc_store(a.partial + (int64_t)blockIdx.x * pstride + i, acc[s2]);
-    }
-    if (MODE == MODE_UPDATE_DOT && a.detect) {   // |y'|^2 in slot j + 1
-      block_merge(nacc, red);
-      if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride + ncols, nacc);
-    }
-  }
-  double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
-  const int nres = MODE == MODE_UPDATE_NORM ? 1 : ncols + (MODE == MODE_UPDATE_DOT && a.detect ? 1 : 0);
-  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, &st->counter);
-  if (!last || tid != 0) return;
-  if (MODE == MODE_DOT) {
-    double al = st->coef[j];
-    st->alpha[j] = al;
-    if (!isfinite(al)) {
-      dev_flag(a.status, LOVE_ERR_NAN);
-      st->done = 1;
-      st->k_eff = j;
-    }
-    st->maxabs = fmax(st->maxabs, fabs(al));
-  } else if (MODE == MODE_UPDATE_DOT) {
-    if (a.detect) {
-      double c2 = 0.0;
-      for (int i = 0; i < ncols; ++i) c2 += st->coef2[i] * st->coef2[i];
-      const double yn = st->coef2[ncols];
-      st->skip = c2 <= a.eta2 * yn;   // false for NaN: the second pass reports it
-      if (st->skip) {
-        st->n_skip += 1;
-        st->norm2 = yn;
-        finish_step(st, a.status, j);
+      if (i < ncols) {
+        const T ci = cf[i];
+        ps[0] = fma(q[s2][0], ci, ps[0]);
+        ps[1] = fma(q[s2][1], ci, ps[1]);
       }
     }
-  } else {
-    finish_step(st, a.status, j);
+    hp[warp][r0] = ps[0];
+    hp[warp][r0 + 1] = ps[1];
+    __syncthreads();
+    if (tid < SMALL_R) {
+      T sum = hp[0][tid];
+#pragma unroll
+      for (int w = 1; w < NWARP; ++w) sum += hp[w][tid];
+      const T yv = ys[tid] - sum;
+      const int64_t p = row0 + tid;
+      if (MODE == MODE_UPDATE_DOT) {
+        if (a.detect) {
+          if (j + 1 < a.kcols)
+            a.Q[(int64_t)(j + 1) * a.ldq + p] = yv;
+          else
+            a.y[p] = yv;
+          nacc.add_prod(yv, yv);
+        } else {
+          a.y[p] = yv;
+        }
+        ys[tid] = yv;
+      } else {
+        if (j + 1 < a.kcols)
+          a.Q[(int64_t)(j + 1) * a.ldq + p] = yv;
+        else
+          a.y[p] = yv;
+        nacc.add_prod(yv, yv);
+      }
+    }
+    if (MODE == MODE_UPDATE_DOT) __syncthreads();
   }
+  // ---- column dots: c_i += q_i . y over this CTA's rows
+  if (MODE != MODE_UPDATE_NORM) {
+    const T y0 = ys[r0], y1 = ys[r0 + 1];
+#pragma unroll
+    for (int s2 = 0; s2 < KPW; ++s2) {
+      const int i = warp + NWARP * s2;
+      if (i < ncols) acc[s2].add(fma(q[s2][1], y1, q[s2][0] * y0));
+    }
+  }
+  sweep_epilogue<T, MODE, KPW>(a, acc, nacc, red, wsum);
 }
 
 // Lanczos product y = W^T u + s^2 q_j (u = K_UU W q_j), normalising q_j in
@@ -1107,6 +1272,23 @@ love_status make_qmap(T* Q, int64_t ldq, int kcols, int bc, CUtensorMap* out);
 template <typename T, int MODE>
 love_status tile_run(TileArgs<T> a, cudaStream_t s) {
   const int ncols = a.j + 1;
+  if (a.n_pad / TILE_R < (int64_t)TILE_CTAS_PER_SM * num_sms()) {
+    // short vectors: one 64-row block per CTA, no staging ring
+    const unsigned grid = (unsigned)(a.n_pad / SMALL_R);
+#define LOVE_SMALL_CASE(KPW)                                                   \
+    if (ncols <= NWARP * KPW) {                                                \
+      LOVE_COUNT_LAUNCH(); k_lanczos_small<T, MODE, KPW><<<grid, TILE_T, 0, s>>>(a); \
+      return cuda_check(cudaGetLastError());                                   \
+    }
+    LOVE_SMALL_CASE(1)
+    LOVE_SMALL_CASE(2)
+    LOVE_SMALL_CASE(4)
+    LOVE_SMALL_CASE(8)
+    LOVE_SMALL_CASE(16)
+    LOVE_SMALL_CASE(32)
+#undef LOVE_SMALL_CASE
+    return LOVE_ERR_UNSUPPORTED;
+  }
   a.kpad = (ncols + a.bc - 1) / a.bc * a.bc;
   const TileGeom tg = tile_geom(a.kpad, a.kcols, sizeof(T));
   if (tg.stages == 0) return LOVE_ERR_UNSUPPORTED;
@@ -1914,33 +2096,58 @@ __global__ void k_normalize_col(double* __restrict__ q, int64_t n_pad, const dou
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x)
     q[i] *= sc;
 }
-// t[c] = sum_r R[r, c] q[r]   (R column-major, ldr), one block per column
+// Partial products of the sampler operator's low-rank term (R = Rt, m x k,
+// column-major): tp[c * RS + rs] = sum over rows of slice rs of R[r, c] q[r],
+// a block per (column, slice of GEMV_SLICE rows), each thread 4 rows.
+constexpr int GEMV_SLICE = 1024;
 template <typename T>
 __global__ void k_gemv_t(const T* __restrict__ R, int64_t ldr, int64_t m, const double* __restrict__ q,
-                         double* __restrict__ t, const LanczosState* st) {
+                         double* __restrict__ tp, const LanczosState* st) {
   __shared__ DotAccD red[32];
   if (st->done) return;
-  const int c = blockIdx.x;
+  const int c = blockIdx.x, rs = blockIdx.y;
+  const int64_t r0 = (int64_t)rs * GEMV_SLICE;
   DotAccD a;
   a.zero();
-  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) a.add_prod((double)R[(int64_t)c * ldr + r], q[r]);
+#pragma unroll
+  for (int u = 0; u < GEMV_SLICE / 256; ++u) {
+    const int64_t r = r0 + u * 256 + threadIdx.x;
+    if (r < m) a.add_prod((double)R[(int64_t)c * ldr + r], q[r]);
+  }
   block_merge(a, red);
-  if (threadIdx.x == 0) t[c] = a.value();
+  if (threadIdx.x == 0) tp[(int64_t)c * gridDim.y + rs] = a.value();
 }
-// y[r] = Kq[r] - sum_c R[r, c] t[c]  (0 on padding rows)
+// y[r] = Kq[r] - sum_c R[r, c] t[c]  (0 on padding rows); t[c] = the sum of
+// the RS slice partials (fixed order).  A block covers 32 rows: warp w takes
+// the columns w, w + 8, ..., lane l row l, then the 8 warp sums are added.
 template <typename T>
-__global__ void k_gemv_n_sub(const T* __restrict__ R, int64_t ldr, int64_t m, int64_t m_pad, int k,
-                             const double* __restrict__ t, const double* __restrict__ Kq, double* __restrict__ y,
+__global__ void k_gemv_n_sub(const T* __restrict__ R, int64_t ldr, int64_t m, int64_t m_pad, int k, int RS,
+                             const double* __restrict__ tp, const double* __restrict__ Kq, double* __restrict__ y,
                              const LanczosState* st) {
+  extern __shared__ double t_s[];   // [k] then [8][32]
   if (st->done) return;
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= m_pad) return;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double v = 0.0;
+    for (int rs = 0; rs < RS; ++rs) v += tp[(int64_t)c * RS + rs];
+    t_s[c] = v;
+  }
+  __syncthreads();
+  double* ws = t_s + k;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * 32 + lane;
   double acc = 0.0;
   if (r < m) {
-    acc = Kq[r];
-    for (int c = 0; c < k; ++c) acc -= (double)R[(int64_t)c * ldr + r] * t[c];
+#pragma unroll 4
+    for (int c = w; c < k; c += 8) acc = fma((double)R[(int64_t)c * ldr + r], t_s[c], acc);
   }
-  y[r] = acc;
+  ws[w * 32 + lane] = acc;
+  __syncthreads();
+  if (w == 0 && r < m_pad) {
+    double sum = 0.0;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) sum += ws[v * 32 + lane];
+    y[r] = r < m ? Kq[r] - sum : 0.0;
+  }
 }
 
 }  // namespace
@@ -1956,7 +2163,8 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
   DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s);
   size_t fwb = fft_work_bytes(gh, fft, 1, true);
   if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)max_grid * (ks + 1)) ||
-      !kq.get(sizeof(double) * m) || !y.get(sizeof(double) * m_pad) || !tv.get(sizeof(double) * (k + 1)) ||
+      !kq.get(sizeof(double) * m) || !y.get(sizeof(double) * m_pad) ||
+      !tv.get(sizeof(double) * (size_t)(k + 1) * (size_t)ceil_div(m, GEMV_SLICE)) ||
       !fw.get(std::max<size_t>(fwb, 16)))
     return LOVE_ERR_OOM;
   LanczosState* st = stb.as<LanczosState>();
@@ -1974,12 +2182,15 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
   ta.st = st;
   ta.status = status;
   const int nb = std::min(4 * num_sms(), ceil_div(m_pad, 256));
+  const int RS = ceil_div(m, GEMV_SLICE);
+  const size_t nsub_smem = sizeof(double) * ((size_t)k + 8 * 32);
+  LOVE_TRY(allow_smem(k_gemv_n_sub<T>, nsub_smem));
   for (int j = 0; j < ks; ++j) {
     double* qj = Q + (int64_t)j * ldq;
     LOVE_COUNT_LAUNCH(); k_normalize_col<<<nb, 256, 0, s>>>(qj, m_pad, st->scal + j, st);
     LOVE_TRY(kuu_apply<double>(gh, fft, qj, kq.as<double>(), 1, m, fw.p, -1, s));
-    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<k, 256, 0, s>>>(Rt, ldr, m, qj, tv.as<double>(), st);
-    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T><<<ceil_div(m_pad, 256), 256, 0, s>>>(Rt, ldr, m, m_pad, k, tv.as<double>(), kq.as<double>(), y.as<double>(), st);
+    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<dim3(k, RS), 256, 0, s>>>(Rt, ldr, m, qj, tv.as<double>(), st);
+    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T><<<ceil_div(m_pad, 32), 256, nsub_smem, s>>>(Rt, ldr, m, m_pad, k, RS, tv.as<double>(), kq.as<double>(), y.as<double>(), st);
     LOVE_LAUNCH_CHECK();
     ta.j = j;
     LOVE_TRY(tile_run<double, MODE_DOT>(ta, s));
@@ -2189,8 +2400,9 @@ love_status mean_grid_gmres(love_ski* ski, double tol, int max_iter, double* a, 
   const int sblocks = (int)std::min<int64_t>((m * 32 + 255) / 256, (int64_t)num_sms() * 16);
   const int mblocks = (int)std::min<int64_t>(ceil_div(m_pad, 256), 1024);
   const int nblocks = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(n, 1), 256), 1024);
-  FftPlan pplan = kp;   // the same transform with the spectrum of P
+  FftPlan pplan = kp;   // the same transform with the spectrum of P (never the dense form)
   pplan.lam_d = sym;
+  pplan.col2 = pplan.coldl2 = nullptr;
   auto kmul = [&](const double* in, double* out) -> love_status {
     return kuu_apply<double>(gh, ski->fft, in, out, 1, m, fw.p, -1, s);
   };

@@ -43,6 +43,62 @@ __global__ void k_chol_tri(const double* alpha, const double* beta, int k, doubl
   }
 }
 
+// T' + delta I for a T' that is not numerically positive definite: the
+// smallest eigenvalue of the tridiagonal T' by multisection on Sturm counts
+// (the number of negative pivots of the LDL^T factorisation of T' - x I is the
+// number of eigenvalues below x), then delta = max(0, -lambda_min) plus 16
+// units of rounding of |T'|, so that the Cholesky factorisation of the
+// shifted matrix succeeds; alpha_s = alpha + delta.  One CTA: each round the
+// 256 threads count at 256 interior points of the bracket and the bracket
+// shrinks to the cell holding lambda_min (7 rounds reach FP64 resolution).
+__device__ int sturm_below(const double* alpha, const double* beta, int k, double x) {
+  const double tiny = 1e-300;
+  int neg = 0;
+  double dd = alpha[0] - x;
+  for (int j = 0;;) {
+    if (fabs(dd) < tiny) dd = -tiny;
+    if (dd < 0.0) ++neg;
+    if (++j == k) break;
+    dd = alpha[j] - x - beta[j - 1] * beta[j - 1] / dd;
+  }
+  return neg;
+}
+
+__global__ void k_tri_shift(const double* alpha, const double* beta, int k, double* alpha_s) {
+  __shared__ double br[2];
+  __shared__ int first;
+  const int t = threadIdx.x, nt = blockDim.x;
+  if (t == 0) {
+    double lo = 0.0, hi = 0.0;
+    for (int j = 0; j < k; ++j) {   // Gershgorin interval
+      const double r = (j > 0 ? fabs(beta[j - 1]) : 0.0) + (j + 1 < k ? fabs(beta[j]) : 0.0);
+      lo = j == 0 ? alpha[j] - r : fmin(lo, alpha[j] - r);
+      hi = j == 0 ? alpha[j] + r : fmax(hi, alpha[j] + r);
+    }
+    br[0] = lo;
+    br[1] = hi;
+  }
+  __syncthreads();
+  const double nrm = fmax(fabs(br[0]), fabs(br[1]));
+  for (int round = 0; round < 12; ++round) {
+    const double a = br[0], b = br[1];
+    if (!(b - a > 2.0 * 2.2204460492503131e-16 * nrm)) break;
+    if (t == 0) first = nt;
+    __syncthreads();
+    const double x = a + (b - a) * (double)(t + 1) / (double)(nt + 1);
+    if (sturm_below(alpha, beta, k, x) >= 1) atomicMin(&first, t);
+    __syncthreads();
+    if (t == 0) {
+      const double h = (b - a) / (double)(nt + 1);
+      br[0] = first == 0 ? a : a + h * (double)first;
+      br[1] = first == nt ? b : a + h * (double)(first + 1);
+    }
+    __syncthreads();
+  }
+  const double delta = fmax(0.0, -br[0]) + 16.0 * 2.2204460492503131e-16 * nrm;
+  for (int j = t; j < k; j += nt) alpha_s[j] = alpha[j] + delta;
+}
+
 // S[r, c] = d_c Q'[r, c] + e_c Q'[r, c+1]   (S = Q' L', L' lower bidiagonal), row-major ld_s
 template <typename T>
 __global__ void k_root_from_chol(const double* __restrict__ Q, int64_t ldq, int64_t m, int k, const double* d,
@@ -523,7 +579,7 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
   const int64_t m = g.m;
   const int64_t m_pad = (m + 255) / 256 * 256;
   Buf Qb(al, s), ab(al, s), okb(al, s);
-  if (!Qb.get(sizeof(double) * m_pad * ks) || !ab.get(sizeof(double) * 4 * (ks + 1)) || !okb.get(sizeof(int)))
+  if (!Qb.get(sizeof(double) * m_pad * ks) || !ab.get(sizeof(double) * 5 * (ks + 1)) || !okb.get(sizeof(int)))
     return LOVE_ERR_OOM;
   std::vector<double> alpha(ks + 1), beta(ks + 1);
   int keff = 0;
@@ -541,6 +597,18 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
   int ok = 0;
   LOVE_CUDA(cudaMemcpyAsync(&ok, okb.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
   LOVE_CUDA(cudaStreamSynchronize(s));
+  int shifted = 0;
+  if (!ok) {
+    // T' not numerically PD (K_UU - Rt Rt^T has eigenvalues at the rounding
+    // level): Cholesky of T' + delta I, delta = -lambda_min(T') + rounding
+    double* as = ed + (ks + 1);
+    LOVE_COUNT_LAUNCH(); k_tri_shift<<<1, 256, 0, s>>>(ad, bd, keff, as);
+    LOVE_COUNT_LAUNCH(); k_chol_tri<<<1, 32, 0, s>>>(as, bd, keff, dd, ed, okb.as<int>());
+    LOVE_LAUNCH_CHECK();
+    LOVE_CUDA(cudaMemcpyAsync(&ok, okb.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    shifted = ok;
+  }
   const int vec = 16 / (int)sizeof(T);
   c->ks = keff;
   c->ld_s = (keff + vec - 1) / vec * vec;
@@ -548,7 +616,7 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
   if (!c->S) return LOVE_ERR_OOM;
   if (ok) {
     LOVE_COUNT_LAUNCH(); k_root_from_chol<T><<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(Qb.as<double>(), m_pad, m, keff, dd, ed, (T*)c->S, c->ld_s);
-    c->sampler_fallback = 0;
+    c->sampler_fallback = shifted;
   } else {
     Buf A(al, s), V(al, s), B(al, s);
     const int64_t nn = (int64_t)keff * keff;

@@ -330,7 +330,8 @@ love_status ski_build(const love_ski_desc* desc, const void* x_train, const void
     return LOVE_ERR_OOM;
   }
   love_status rc = cuda_check(cudaMemsetAsync(ski->status, 0, sizeof(DevStatus), s));
-  for (int e = 0; e < g.dim && rc == LOVE_OK; ++e) rc = fft_plan_create(ski->fft[e], g, e, al, s);
+  for (int e = 0; e < g.dim && rc == LOVE_OK; ++e)
+    rc = fft_plan_create(ski->fft[e], g, e, al, s, ski->dtype == LOVE_F32);
   if (rc == LOVE_OK) rc = sort_training_points(ski, x_train, y_train, s);
   if (rc == LOVE_OK && g.additive) rc = sort_additive_dims(ski, s);
   DevStatus st{};
@@ -714,7 +715,8 @@ love_status love_cache_import(const love_ski_desc* desc, int k, love_dtype cache
     }
     if (rc == LOVE_OK) {
       FftPlan plans[LOVE_MAX_DIM];
-      for (int e = 0; e < g.dim && rc == LOVE_OK; ++e) rc = fft_plan_create(plans[e], g, e, al, s);
+      for (int e = 0; e < g.dim && rc == LOVE_OK; ++e)
+        rc = fft_plan_create(plans[e], g, e, al, s, desc->dtype == LOVE_F32);
       if (rc == LOVE_OK) rc = backward_tables(c, plans, c->P, k, s);
       for (int e = 0; e < g.dim; ++e) fft_plan_destroy(plans[e], al, s);
     }

@@ -263,7 +263,16 @@ struct FftPlan {
   void* tw_d = nullptr;   // N double2
   void* lamdl_f = nullptr;  // spectrum of dT/dl (for gradients), / N
   void* lamdl_d = nullptr;
+  // short modes (g <= TOEP_DENSE_MAX): the first column of T (and of dT/dl),
+  // outputscale folded in like the spectrum, as float pairs (hi, lo) for the
+  // dense double-float product; nullptr: the mode always takes the FFT
+  void* col2 = nullptr;    // g float2
+  void* coldl2 = nullptr;  // g float2
 };
+// modes up to this length apply T by a dense double-float product on the
+// FP32 pipes instead of the FFT (whose FP64 butterflies run at the part's
+// low FP64 rate)
+constexpr int64_t TOEP_DENSE_MAX = 384;
 
 struct Allocator {
   love_allocator a{};
@@ -365,7 +374,10 @@ love_status sort_training_points(love_ski* ski, const void* x_in, const void* y_
 love_status sort_additive_dims(love_ski* ski, cudaStream_t s);
 
 // k_fft.cu
-love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocator& al, cudaStream_t s);
+// dense: allow the double-float dense product on modes of up to TOEP_DENSE_MAX
+// (FP32 data; FP64 data keeps the FP64 FFT, whose rounding is ~100x smaller)
+love_status fft_plan_create(FftPlan& p, const GridHost& g, int e, const Allocator& al, cudaStream_t s,
+                            bool dense);
 void fft_plan_destroy(FftPlan& p, const Allocator& al, cudaStream_t s);
 // out = K_UU v (all modes) for `ncol` columns (column stride ldc elements); work
 // must hold fft_work_elems() complex values.  deriv_dim >= 0 selects dK/dl_e.
