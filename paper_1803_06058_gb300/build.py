@@ -22,8 +22,11 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblove.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# diagnostic 1886 (an extern __shared__ array redeclared with another alignment)
+# is an error: the first declaration's alignment wins for every kernel of the
+# file, and a TMA destination placed there must stay 128-byte aligned
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
-                     "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
+                     "--expt-relaxed-constexpr", "-Xcudafe", "--diag_error=1886", "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc() -> str:

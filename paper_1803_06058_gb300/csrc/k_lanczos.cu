@@ -247,6 +247,255 @@ __global__ void k_scatter(GridDev g, const T* __restrict__ xs, const int* __rest
   }
 }
 
+// u = W v on a 3-D grid, a CTA per 8 x 8 x 8 block of nodes and a thread per
+// node.  The points of the block's 11 x 11 x 11 halo cells (cells n - 2 ..
+// n + 1 feed node n) are 121 contiguous runs of the cell-sorted order; they
+// are staged once in shared memory as (cell, fractional coordinate, value),
+// and each thread then sums over the points of its 64 cells in a fixed order
+// (double-float), with the weights evaluated as in node_weight.  A block
+// whose halo holds more than SC3_CAP points reads them from global memory.
+constexpr int SC3_NB = 8, SC3_HC = SC3_NB + 3, SC3_RUNS = SC3_HC * SC3_HC, SC3_CAP = 4096;
+// dynamic shared memory: run offsets, per-run cell starts, run starts, then the
+// staged points (values, fractional coordinates, cells)
+constexpr size_t SC3_OFF_CS = 512, SC3_OFF_RG = 6400, SC3_OFF_PV = 6912;
+template <typename V>
+constexpr size_t sc3_smem() {
+  return SC3_OFF_PV + (size_t)SC3_CAP * sizeof(V) + (size_t)SC3_CAP * 3 * sizeof(float) + (size_t)SC3_CAP * 4;
+}
+
+template <typename T, typename V>
+__global__ void __launch_bounds__(512) k_scatter3_block(GridDev g, const T* __restrict__ xs,
+                                                        const int* __restrict__ cell_start, const V* __restrict__ v,
+                                                        const double* __restrict__ scal, V scale, V* __restrict__ u,
+                                                        const V* __restrict__ v2, const double* __restrict__ beta2,
+                                                        const int* __restrict__ skip) {
+  using Acc = typename AccOf<V>::type;
+  static_assert((SC3_RUNS + 1) * 4 <= SC3_OFF_CS && SC3_OFF_CS + SC3_RUNS * (SC3_HC + 1) * 4 <= SC3_OFF_RG &&
+                    SC3_OFF_RG + SC3_RUNS * 4 <= SC3_OFF_PV && SC3_OFF_PV % 16 == 0,
+                "shared-memory layout");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  int* run_off = reinterpret_cast<int*>(smem_raw);                                    // [SC3_RUNS + 1]
+  int (*cs_loc)[SC3_HC + 1] = reinterpret_cast<int (*)[SC3_HC + 1]>(smem_raw + SC3_OFF_CS);  // cell starts
+  int* run_g = reinterpret_cast<int*>(smem_raw + SC3_OFF_RG);                         // global run starts
+  V* pv = reinterpret_cast<V*>(smem_raw + SC3_OFF_PV);                                // values
+  float (*pf)[3] = reinterpret_cast<float (*)[3]>(smem_raw + SC3_OFF_PV + SC3_CAP * sizeof(V));  // fractions
+  unsigned char (*pc)[4] = reinterpret_cast<unsigned char (*)[4]>(
+      smem_raw + SC3_OFF_PV + SC3_CAP * sizeof(V) + SC3_CAP * 3 * sizeof(float));  // halo cells
+  if (skip && *skip) return;
+  const V b2 = v2 ? (V)(*beta2) : V(0);
+  const int t = threadIdx.x;
+  int N[3] = {(int)blockIdx.z * SC3_NB, (int)blockIdx.y * SC3_NB, (int)blockIdx.x * SC3_NB};
+  int c_lo[3], c_hi[3];   // halo cells, clipped to the grid
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    c_lo[e] = max(N[e] - 2, 0);
+    c_hi[e] = min(N[e] + SC3_NB, g.g[e] - 1);
+  }
+  const int h0 = c_hi[0] - c_lo[0] + 1, h1 = c_hi[1] - c_lo[1] + 1, h2 = c_hi[2] - c_lo[2] + 1;
+  // runs along the last dimension: lengths, then an exclusive scan
+  if (t < SC3_RUNS) {
+    const int a = t / SC3_HC, b = t % SC3_HC;
+    int len = 0, gs = 0;
+    if (a < h0 && b < h1) {
+      const int64_t base = (int64_t)(c_lo[0] + a) * g.stride[0] + (int64_t)(c_lo[1] + b) * g.stride[1];
+      gs = cell_start[base + c_lo[2]];
+      for (int z = 0; z <= h2; ++z) cs_loc[t][z] = cell_start[base + c_lo[2] + z] - gs;
+      len = cs_loc[t][h2];
+    }
+    run_g[t] = gs;
+    run_off[t + 1] = len;
+  }
+  if (t == 0) run_off[0] = 0;
+  __syncthreads();
+  if (t == 0)
+    for (int r = 0; r < SC3_RUNS; ++r) run_off[r + 1] += run_off[r];
+  __syncthreads();
+  const int P = run_off[SC3_RUNS];
+  const bool staged = P <= SC3_CAP;
+  if (staged) {
+    const int lane = t & 31, w = t >> 5;
+    for (int r = w; r < SC3_RUNS; r += 16) {
+      const int len = run_off[r + 1] - run_off[r];
+      for (int q = lane; q < len; q += 32) {
+        const int p = run_g[r] + q, slot = run_off[r] + q;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const T sc = grid_coord(xs[(int64_t)p * 3 + e], g, e);
+          int i = (int)floor(sc);
+          if (i > g.g[e] - 3) i = g.g[e] - 3;
+          pf[slot][e] = (float)(sc - T(i));
+          pc[slot][e] = (unsigned char)(i - c_lo[e]);
+        }
+        V val = v[p];
+        if (v2) val += b2 * v2[p];
+        pv[slot] = val;
+      }
+    }
+  }
+  __syncthreads();
+  const int nd[3] = {N[0] + t / 64, N[1] + (t / 8) % 8, N[2] + t % 8};
+  if (nd[0] >= g.g[0] || nd[1] >= g.g[1] || nd[2] >= g.g[2]) return;
+  Acc acc;
+  acc.zero();
+  const int zlo = max(nd[2] - 2, c_lo[2]) - c_lo[2], zhi = min(nd[2] + 1, c_hi[2]) - c_lo[2];
+  for (int dx = 0; dx < 4; ++dx) {
+    const int a = nd[0] - 2 + dx - c_lo[0];
+    if (a < 0 || a >= h0) continue;
+    for (int dy = 0; dy < 4; ++dy) {
+      const int b = nd[1] - 2 + dy - c_lo[1];
+      if (b < 0 || b >= h1 || zlo > zhi) continue;
+      const int r = a * SC3_HC + b;
+      const int q0 = cs_loc[r][zlo], q1 = cs_loc[r][zhi + 1];
+      for (int q = q0; q < q1; ++q) {
+        V wv;
+        if (staged) {
+          const int slot = run_off[r] + q;
+          float wt = 1.f;
+#pragma unroll
+          for (int e = 0; e < 3; ++e) {
+            const int rr = nd[e] - ((int)pc[slot][e] + c_lo[e] - 1);
+            wt *= keys_u(pf[slot][e] + 1.f - (float)rr);
+          }
+          wv = pv[slot];
+          acc.add_prod((V)wt, wv);
+        } else {
+          const int p = run_g[r] + q;
+          V val = v[p];
+          if (v2) val += b2 * v2[p];
+          acc.add_prod((V)node_weight<T, 3>(xs + (int64_t)p * 3, g, nd), val);
+        }
+      }
+    }
+  }
+  const double sc = (double)scale * (scal ? *scal : 1.0);
+  u[(int64_t)nd[0] * g.stride[0] + (int64_t)nd[1] * g.stride[1] + nd[2]] = (V)(acc.value() * sc);
+}
+
+// out[:, c] = W Q[:, c] on a 3-D grid: the block scheme of k_scatter3_block
+// for many columns.  The halo points' cells and fractional coordinates are
+// staged once; the columns pass through shared memory SC3M_CH at a time, and
+// each thread evaluates a point's weight once per chunk for all its columns.
+constexpr int SC3M_CH = 4;
+template <typename T>
+constexpr size_t sc3m_smem() {
+  return SC3_OFF_PV + (size_t)SC3_CAP * SC3M_CH * sizeof(T) + (size_t)SC3_CAP * 3 * sizeof(float) + (size_t)SC3_CAP * 4;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_scatter3_multi_block(GridDev g, const T* __restrict__ xs,
+                                                              const int* __restrict__ cell_start,
+                                                              const T* __restrict__ Q, int64_t ldq, int ncol,
+                                                              T* __restrict__ out, int64_t ldo) {
+  using Acc = typename AccOf<T>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  int* run_off = reinterpret_cast<int*>(smem_raw);
+  int (*cs_loc)[SC3_HC + 1] = reinterpret_cast<int (*)[SC3_HC + 1]>(smem_raw + SC3_OFF_CS);
+  int* run_g = reinterpret_cast<int*>(smem_raw + SC3_OFF_RG);
+  T* pv = reinterpret_cast<T*>(smem_raw + SC3_OFF_PV);   // [SC3M_CH][SC3_CAP]
+  float (*pf)[3] = reinterpret_cast<float (*)[3]>(smem_raw + SC3_OFF_PV + (size_t)SC3_CAP * SC3M_CH * sizeof(T));
+  unsigned char (*pc)[4] = reinterpret_cast<unsigned char (*)[4]>(
+      smem_raw + SC3_OFF_PV + (size_t)SC3_CAP * SC3M_CH * sizeof(T) + SC3_CAP * 3 * sizeof(float));
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int N[3] = {(int)blockIdx.z * SC3_NB, (int)blockIdx.y * SC3_NB, (int)blockIdx.x * SC3_NB};
+  int c_lo[3], c_hi[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    c_lo[e] = max(N[e] - 2, 0);
+    c_hi[e] = min(N[e] + SC3_NB, g.g[e] - 1);
+  }
+  const int h0 = c_hi[0] - c_lo[0] + 1, h1 = c_hi[1] - c_lo[1] + 1, h2 = c_hi[2] - c_lo[2] + 1;
+  if (t < SC3_RUNS) {
+    const int a = t / SC3_HC, b = t % SC3_HC;
+    int len = 0, gs = 0;
+    if (a < h0 && b < h1) {
+      const int64_t base = (int64_t)(c_lo[0] + a) * g.stride[0] + (int64_t)(c_lo[1] + b) * g.stride[1];
+      gs = cell_start[base + c_lo[2]];
+      for (int z = 0; z <= h2; ++z) cs_loc[t][z] = cell_start[base + c_lo[2] + z] - gs;
+      len = cs_loc[t][h2];
+    }
+    run_g[t] = gs;
+    run_off[t + 1] = len;
+  }
+  if (t == 0) run_off[0] = 0;
+  __syncthreads();
+  if (t == 0)
+    for (int r = 0; r < SC3_RUNS; ++r) run_off[r + 1] += run_off[r];
+  __syncthreads();
+  const int P = run_off[SC3_RUNS];
+  const bool staged = P <= SC3_CAP;
+  if (staged) {
+    for (int r = w; r < SC3_RUNS; r += 16) {
+      const int len = run_off[r + 1] - run_off[r];
+      for (int q = lane; q < len; q += 32) {
+        const int p = run_g[r] + q, slot = run_off[r] + q;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const T sc = grid_coord(xs[(int64_t)p * 3 + e], g, e);
+          int i = (int)floor(sc);
+          if (i > g.g[e] - 3) i = g.g[e] - 3;
+          pf[slot][e] = (float)(sc - T(i));
+          pc[slot][e] = (unsigned char)(i - c_lo[e]);
+        }
+      }
+    }
+  }
+  const int nd[3] = {N[0] + t / 64, N[1] + (t / 8) % 8, N[2] + t % 8};
+  const bool live = nd[0] < g.g[0] && nd[1] < g.g[1] && nd[2] < g.g[2];
+  const int zlo = max(nd[2] - 2, c_lo[2]) - c_lo[2], zhi = min(nd[2] + 1, c_hi[2]) - c_lo[2];
+  for (int c0 = 0; c0 < ncol; c0 += SC3M_CH) {
+    __syncthreads();   // the previous chunk's values are no longer read
+    if (staged) {
+      for (int r = w; r < SC3_RUNS; r += 16) {
+        const int len = run_off[r + 1] - run_off[r];
+        for (int q = lane; q < len; q += 32) {
+          const int p = run_g[r] + q, slot = run_off[r] + q;
+#pragma unroll
+          for (int c = 0; c < SC3M_CH; ++c)
+            pv[c * SC3_CAP + slot] = c0 + c < ncol ? Q[(int64_t)(c0 + c) * ldq + p] : T(0);
+        }
+      }
+    }
+    __syncthreads();
+    if (!live) continue;
+    Acc acc[SC3M_CH];
+#pragma unroll
+    for (int c = 0; c < SC3M_CH; ++c) acc[c].zero();
+    for (int dx = 0; dx < 4; ++dx) {
+      const int a = nd[0] - 2 + dx - c_lo[0];
+      if (a < 0 || a >= h0) continue;
+      for (int dy = 0; dy < 4; ++dy) {
+        const int b = nd[1] - 2 + dy - c_lo[1];
+        if (b < 0 || b >= h1 || zlo > zhi) continue;
+        const int r = a * SC3_HC + b;
+        const int q0 = cs_loc[r][zlo], q1 = cs_loc[r][zhi + 1];
+        for (int q = q0; q < q1; ++q) {
+          if (staged) {
+            const int slot = run_off[r] + q;
+            float wt = 1.f;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+              const int rr = nd[e] - ((int)pc[slot][e] + c_lo[e] - 1);
+              wt *= keys_u(pf[slot][e] + 1.f - (float)rr);
+            }
+#pragma unroll
+            for (int c = 0; c < SC3M_CH; ++c) acc[c].add_prod((T)wt, pv[c * SC3_CAP + slot]);
+          } else {
+            const int p = run_g[r] + q;
+            const T wt = node_weight<T, 3>(xs + (int64_t)p * 3, g, nd);
+#pragma unroll
+            for (int c = 0; c < SC3M_CH; ++c)
+              if (c0 + c < ncol) acc[c].add_prod(wt, Q[(int64_t)(c0 + c) * ldq + p]);
+          }
+        }
+      }
+    }
+    const int64_t node = (int64_t)nd[0] * g.stride[0] + (int64_t)nd[1] * g.stride[1] + nd[2];
+#pragma unroll
+    for (int c = 0; c < SC3M_CH; ++c)
+      if (c0 + c < ncol) out[(int64_t)(c0 + c) * ldo + node] = (T)acc[c].value();
+  }
+}
+
 // out[:, c] = W Q[:, c] for ncol columns (chunks of CH columns per pass),
 // double-float accumulation as in k_scatter
 template <typename T, int D, int CH>
@@ -1200,6 +1449,14 @@ template <typename T, int D, typename V>
 love_status scatter_launch(love_ski* ski, const V* v, const double* scal, V scale, V* u, cudaStream_t s,
                            const V* v2, const double* beta2, const int* skip) {
   GridDev g = ski->grid.dev();
+  if (D == 3 && sizeof(T) == 4) {
+    dim3 grid((unsigned)ceil_div(g.g[2], SC3_NB), (unsigned)ceil_div(g.g[1], SC3_NB), (unsigned)ceil_div(g.g[0], SC3_NB));
+    constexpr size_t sm = sc3_smem<V>();
+    LOVE_TRY(allow_smem(k_scatter3_block<T, V>, sm));
+    LOVE_COUNT_LAUNCH();
+    k_scatter3_block<T, V><<<grid, 512, sm, s>>>(g, (const T*)ski->xs, ski->cell_start, v, scal, scale, u, v2, beta2, skip);
+    return cuda_check(cudaGetLastError());
+  }
   int64_t warps = g.m;
   int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)num_sms() * 16);
   LOVE_COUNT_LAUNCH(); k_scatter<T, D, V><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, v, scal, scale, u, v2, beta2, skip, nullptr);
@@ -1470,7 +1727,16 @@ love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* o
   switch (g.dim) {
     case 1: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 1, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
     case 2: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 2, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
-    default: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 3, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr);
+    default:
+      if (sizeof(T) == 4) {
+        dim3 grid((unsigned)ceil_div(g.g[2], SC3_NB), (unsigned)ceil_div(g.g[1], SC3_NB), (unsigned)ceil_div(g.g[0], SC3_NB));
+        constexpr size_t sm = sc3m_smem<T>();
+        LOVE_TRY(allow_smem(k_scatter3_multi_block<T>, sm));
+        LOVE_COUNT_LAUNCH();
+        k_scatter3_multi_block<T><<<grid, 512, sm, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo);
+      } else {
+        LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 3, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr);
+      }
   }
   return cuda_check(cudaGetLastError());
 }
