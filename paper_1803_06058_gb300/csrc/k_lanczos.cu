@@ -739,7 +739,9 @@ __device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename Ac
   }
   double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
   const int nres = MODE == MODE_UPDATE_NORM ? 1 : ncols + (MODE == MODE_UPDATE_DOT && a.detect ? 1 : 0);
-  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, &st->counter, scratch);
+  // the norm sweep merges a single sum: the narrow form (lanes over CTAs)
+  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, &st->counter,
+                                   MODE == MODE_UPDATE_NORM ? nullptr : scratch);
   if (!last || tid != 0) return;
   if (MODE == MODE_DOT) {
     double al = st->coef[j];
