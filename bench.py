@@ -226,12 +226,12 @@ def run_gpu(args):
         ev[1].record()
         try:
             cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=sampler[0],
-                                         sampler_seed=seed)
+                                         sampler_seed=seed, time_reorth=True)
         except love.LoveError as e:
             if e.status != 9 or not sampler[0]:
                 raise
             sampler[0] = False
-            cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=False)
+            cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=False, time_reorth=True)
         ev[2].record()
         love.love_predict_mean_var(cache, xs_d, out_mean=mean_d, out_var=var_d)
         ev[3].record()
@@ -257,7 +257,7 @@ def run_gpu(args):
         ev, cache, smp = step(1000 + i)
         records.append(ev)
         inf_ = cache.info()
-        phases.append(inf_["phase_ms"])
+        phases.append(list(inf_["phase_ms"]) + [inf_["reorth_ms"]])
         cg_iters = inf_["cg_iters"]
     torch.cuda.synchronize()
     if world > 1:
@@ -273,7 +273,7 @@ def run_gpu(args):
         ph["sample"].append(ev[3].elapsed_time(ev[4]))
         ph["step"].append(ev[0].elapsed_time(ev[4]))
     mean_ms = {k: statistics.mean(v) for k, v in ph.items()}
-    pnames = ["lanczos", "mean_cg", "cache_build", "sampler"]
+    pnames = ["lanczos", "mean_cg", "cache_build", "sampler", "reorth_in_lanczos"]
     pre_split = {nm: statistics.mean(p[i] for p in phases) for i, nm in enumerate(pnames)}
     # ---- predict kernel alone, repeated, for the roofline (L2 flushed before each)
     pe = []
@@ -286,6 +286,19 @@ def run_gpu(args):
         torch.cuda.synchronize()
         pe.append(a.elapsed_time(b))
     pred_ms = statistics.median(pe)
+    # ---- the same 1e6 points sorted by x (a reported variant; the headline is unsorted):
+    # neighbouring points share cache rows, so more of the gather hits L1
+    xs_sorted = torch.sort(xs_d.view(-1))[0].view(-1, 1).contiguous()
+    pe_s = []
+    for _ in range(max(5, args.steps)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        love.love_predict_mean_var(cache, xs_sorted, out_mean=mean_d, out_var=var_d)
+        b.record()
+        torch.cuda.synchronize()
+        pe_s.append(a.elapsed_time(b))
+    pred_sorted_ms = statistics.median(pe_s)
     # ---- e2e through the public API with host buffers
     mean_h = torch.empty(t, dtype=torch.float32).pin_memory()
     var_h = torch.empty(t, dtype=torch.float32).pin_memory()
@@ -339,6 +352,12 @@ def run_gpu(args):
                "variance_precompute_ms": pre_split["lanczos"] + pre_split["cache_build"],
                "phase_ms": {k: red_max(v) if world > 1 else v for k, v in mean_ms.items()},
                "predict_kernel_ms": pred_ms,
+               "predict_sorted": {"kernel_ms": pred_sorted_ms, "vars_per_s": world * t / (pred_sorted_ms * 1e-3),
+                                  "note": "the same test points sorted by x"},
+               "sample": ({"ms": mean_ms["sample"], "samples": wl.s, "points": wl.t_sample,
+                           "sample_points_per_s": wl.s * wl.t_sample / (mean_ms["sample"] * 1e-3),
+                           "output_gb_per_s": 4.0 * wl.s * wl.t_sample / (mean_ms["sample"] * 1e-3) / 1e9}
+                          if sampler[0] else None),
                "from_scratch_vars_per_s": world * t / (step_ms * 1e-3),
                "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "k": wl.k, "k_eff": k_eff,
                           "t": t, "s": wl.s if sampler[0] else 0, "t_sample": wl.t_sample, "cg_iters": cg_iters,

@@ -129,6 +129,7 @@ LOVE_API love_status ski_mvm_kuu(love_ski_t ski, const void* v, void* out, love_
 #define LOVE_WANT_SAMPLER 0x2u  /* Lanczos on K_UU - R^T R', cache S          */
 #define LOVE_WANT_GRAD 0x4u     /* keep P = W Q L^{-T} for love_var_backward  */
 #define LOVE_PRIOR_EXACT 0x8u   /* prior k(x*,x*) = s_f instead of w^T K_UU w */
+#define LOVE_TIME_REORTH 0x10u  /* time the reorthogonalisation sweeps (love_cache_info.reorth_ms) */
 
 typedef struct {
   int k;                   /* Lanczos steps (1..200)                           */
@@ -242,6 +243,8 @@ typedef struct {
    * gradient tables), [3] sampler; 0 for a cache that was imported or loaded */
   float phase_ms[4];
   int reorth_skipped;      /* Lanczos steps that skipped the second pass (DETECT) */
+  float reorth_ms;         /* device time of the reorthogonalisation sweeps within phase_ms[0]
+                              (CUDA events around each step's sweeps; LOVE_TIME_REORTH, else 0) */
 } love_cache_info_t;
 
 LOVE_API love_status love_cache_info(love_cache_t cache, love_cache_info_t* info);

@@ -187,12 +187,15 @@ def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool =
                     want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
                     breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
                     sampler_k: int = 0, sampler_seed: int = 0, reorth: str = "always", reorth_eta: float = 0.0,
-                    cg_plain: bool = False, stream=None) -> Cache:
+                    cg_plain: bool = False, time_reorth: bool = False, stream=None) -> Cache:
     """reorth: "always" (two Gram-Schmidt passes every step) or "detect" (the
     second pass only where |Q_j^T y'| > reorth_eta |y'|).  cg_plain: mean CG
-    without the spectral preconditioner (1-D grids use it by default)."""
+    without the spectral preconditioner (1-D grids use it by default).
+    time_reorth: record the sweeps' device time (info()["reorth_ms"])."""
     o = _opts(ski.dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,
               cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta, cg_plain)
+    if time_reorth:
+        o.flags |= _lib.TIME_REORTH
     h = C.c_void_p()
     keff = C.c_int(0)
     check("love_precompute", lib().love_precompute(ski.handle, C.byref(o), _stream(stream),

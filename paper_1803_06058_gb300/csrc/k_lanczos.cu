@@ -1645,7 +1645,7 @@ love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaSt
 
 template <typename T>
 love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int64_t ldq, double* alpha_h,
-                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s) {
+                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s, float* reorth_ms) {
   const GridHost& gh = ski->grid;
   const int dim = gh.dim;
   if (k < 1 || k > LOVE_MAX_K) return LOVE_ERR_ARG;
@@ -1686,6 +1686,18 @@ love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int6
   ta.status = ski->status;
   ta.detect = eta > 0.0;
   ta.eta2 = eta * eta;
+  // optional CUDA events around each step's sweeps (reorth_ms)
+  std::vector<cudaEvent_t> rev;
+  struct EvFree {
+    std::vector<cudaEvent_t>& v;
+    ~EvFree() {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+  } rev_free{rev};
+  if (reorth_ms) {
+    rev.resize(2 * (size_t)k, nullptr);
+    for (auto& e : rev) LOVE_CUDA(cudaEventCreate(&e));
+  }
   for (int j = 0; j < k; ++j) {
     // u = W q_j (q_j stored unnormalised, scaled by scal[j])
     LOVE_TRY(scatter_any<T>(ski, Q + (int64_t)j * ldq, st->scal + j, T(1), u1, s));
@@ -1694,12 +1706,14 @@ love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int6
     LOVE_TRY(lanczos_gather_any<T>(ski, u2, Q + (int64_t)j * ldq, y.as<T>(), st, j, s));
     ta.j = j;
     ta.y = y.as<T>();
+    if (reorth_ms) LOVE_CUDA(cudaEventRecord(rev[2 * (size_t)j], s));
     LOVE_TRY(tile_run<T, MODE_DOT>(ta, s));
     LOVE_TRY(tile_run<T, MODE_UPDATE_DOT>(ta, s));
     // detection mode: y' sits in the slot of q_{j+1}; the second pass works
     // in place there (and returns at once when the step was finished)
     if (ta.detect && j + 1 < k) ta.y = Q + (int64_t)(j + 1) * ldq;
     LOVE_TRY(tile_run<T, MODE_UPDATE_NORM>(ta, s));
+    if (reorth_ms) LOVE_CUDA(cudaEventRecord(rev[2 * (size_t)j + 1], s));
   }
   int keff = 0, nskip = 0;
   LOVE_CUDA(cudaMemcpyAsync(&nskip, &st->n_skip, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1709,6 +1723,15 @@ love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int6
   LOVE_CUDA(cudaStreamSynchronize(s));
   *k_eff = keff;
   if (skipped) *skipped = nskip;
+  if (reorth_ms) {
+    float tot = 0.f;
+    for (int j = 0; j < k; ++j) {
+      float ms = 0.f;
+      LOVE_CUDA(cudaEventElapsedTime(&ms, rev[2 * (size_t)j], rev[2 * (size_t)j + 1]));
+      tot += ms;
+    }
+    *reorth_ms = tot;
+  }
   return LOVE_OK;
 }
 
@@ -2287,9 +2310,9 @@ love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, c
 template love_status ski_mvm_sorted<float>(love_ski*, const float*, float*, void*, cudaStream_t);
 template love_status ski_mvm_sorted<double>(love_ski*, const double*, double*, void*, cudaStream_t);
 template love_status lanczos_run<float>(love_ski*, int, double, double, float*, int64_t, double*, double*, int*,
-                                        int*, cudaStream_t);
+                                        int*, cudaStream_t, float*);
 template love_status lanczos_run<double>(love_ski*, int, double, double, double*, int64_t, double*, double*, int*,
-                                         int*, cudaStream_t);
+                                         int*, cudaStream_t, float*);
 template love_status scatter_multi<float>(love_ski*, const float*, int64_t, int, float*, int64_t, cudaStream_t);
 template love_status scatter_multi<double>(love_ski*, const double*, int64_t, int, double*, int64_t, cudaStream_t);
 template love_status cg_solve<float>(love_ski*, const float*, double*, double, int, int*, cudaStream_t);

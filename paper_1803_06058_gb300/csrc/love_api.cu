@@ -485,7 +485,9 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   int keff = 0, skipped = 0;
   PhaseEvents ev;
   ev.record(0, s);
-  love_status rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, s);
+  float reorth_ms = 0.f;
+  love_status rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, s,
+                                  (flags & LOVE_TIME_REORTH) ? &reorth_ms : nullptr);
   ev.record(1, s);
   if (rc != LOVE_OK) {
     join_mean();
@@ -515,6 +517,7 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     return LOVE_ERR_OOM;
   }
   c->reorth_skipped = skipped;
+  c->reorth_ms = reorth_ms;
   std::copy(alpha.begin(), alpha.begin() + keff, c->alpha);
   std::copy(beta.begin(), beta.begin() + std::max(keff - 1, 0), c->beta);
   // n-space mean CG (3-D grids), on this stream
@@ -654,6 +657,7 @@ love_status love_cache_info(love_cache_t c, love_cache_info_t* info) {
   info->flags = c->flags;
   for (int i = 0; i < 4; ++i) info->phase_ms[i] = c->phase_ms[i];
   info->reorth_skipped = c->reorth_skipped;
+  info->reorth_ms = c->reorth_ms;
   return LOVE_OK;
 }
 

@@ -357,6 +357,7 @@ struct love_cache {
   void* P = nullptr;           // m x k_eff column-major (dtype), kept for export
   int cg_iters = 0;
   int reorth_skipped = 0;
+  float reorth_ms = 0.f;
   int sampler_fallback = 0;
   float phase_ms[4] = {0, 0, 0, 0};
   DevStatus* status = nullptr;
@@ -390,7 +391,7 @@ love_status kuu_apply(const GridHost& g, const FftPlan* plans, const T* v, T* ou
 struct LanczosWork;
 template <typename T>
 love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int64_t ldq, double* alpha_h,
-                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s);
+                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s, float* reorth_ms = nullptr);
 template <typename T>
 love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaStream_t s);
 template <typename T>
