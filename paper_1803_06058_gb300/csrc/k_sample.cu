@@ -408,14 +408,12 @@ __global__ void __launch_bounds__(256) k_sample_gemm(const T* __restrict__ G, in
 }
 
 // ---------------------------------------------------------------------------
-// The same product on the tensor cores for FP32 data (Sec. 3.3, eq. sample:
-// F = mu + W*^T S Z is a dense t x k_s by k_s x s contraction).  Each FP32
-// operand is split into two TF32 parts, x = hi + lo (hi = x rounded to TF32,
-// lo = the rounded remainder), and each product is accumulated as
-// lo*hi + hi*lo + hi*hi in FP32 (the lo*lo term, ~2^-22 relative, is dropped):
-// close to FP32 accuracy on the TF32 tensor path.  mma.sync m16n8k8 (TF32 in,
-// FP32 accumulate); CTA tile 128 points x 64 samples, 8 warps of 32 x 32,
-// k in chunks of 32 staged through shared memory.
+// Split TF32 for the tensor-core form of the product below (Sec. 3.3, eq.
+// sample: F = mu + W*^T S Z is a dense t x k_s by k_s x s contraction).  Each
+// FP32 operand is split into two TF32 parts, x = hi + lo (hi = x rounded to
+// TF32, lo = the rounded remainder), and each product is accumulated as
+// hi*hi + hi*lo + lo*hi in FP32 (the lo*lo term, ~2^-22 relative, is dropped):
+// close to FP32 accuracy on the TF32 tensor path.
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -425,90 +423,225 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
   hi = to_tf32(x);
   lo = to_tf32(x - __uint_as_float(hi));
 }
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+
+// ---------------------------------------------------------------------------
+// The product on the 5th-generation tensor cores (tcgen05, kind::tf32,
+// one CTA, accumulator in tensor memory).  A CTA computes a 128-point x
+// 128-sample tile D[i][j] = sum_c G[i][c] Z[c][j]:
+//   * G (A, M = points) and Z^T (B, N = samples) pass through shared memory in
+//     K chunks of UKC columns (two buffers: the next chunk is staged while the
+//     tensor core works on the previous one), each FP32 value split into two TF32 parts
+//     (hi = x rounded to TF32, lo = the rounded remainder); both operands are
+//     K-major in the no-swizzle canonical layout: 8-row x 16-byte core matrices,
+//     the 16 row blocks of one 16-byte K slice contiguous (stride 128 B), the
+//     K slices 2 KB apart;
+//   * one thread issues, per K step of 8, the MMAs hi*hi, hi*lo and lo*hi into
+//     the 128 x 128 FP32 accumulator (128 tensor-memory columns; lane = point),
+//     then commits them to the buffer's mbarrier, which every thread waits on
+//     (bounded) before that buffer is staged again;
+//   * the epilogue reads the accumulator with tcgen05.ld (warp w: lanes
+//     32 (w mod 4) .., columns 64 (w / 4) ..), adds mu and writes
+//     F[j][i] (sample-major, consecutive points per store).
+constexpr int UM = 128, UN = 128, UKC = 24;   // tile and K chunk (3 K steps of 8)
+constexpr uint32_t U_TILE_BYTES = UM * UKC * 4;   // one operand part per chunk (12 KB)
+constexpr uint32_t U_SLICE_BYTES = UM * 16;       // one 16-byte K slice of 128 rows (2 KB)
+constexpr size_t U_SMEM = 2 * 4 * (size_t)U_TILE_BYTES + 64;   // two buffers of 4 parts + barriers
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
+  // start address >> 4 | leading (K) byte offset >> 4 | stride (M/N) byte offset >> 4 |
+  // descriptor version 1 (bit 46); no swizzle, base offset 0
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(U_SLICE_BYTES >> 4) << 16) |
+         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t U_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(UN >> 3) << 17) |
+                             ((uint32_t)(UM >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate) {
   asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(U_IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-constexpr int TCM = 128, TCN = 64, TCK = 32;
-__global__ void __launch_bounds__(256) k_sample_gemm_tc(const float* __restrict__ G, int ld_g,
-                                                        const float* __restrict__ Z, int s, int ks,
-                                                        const float* __restrict__ mu, int64_t t,
-                                                        float* __restrict__ F) {
-  __shared__ float Gs[TCM][TCK + 4];   // row stride 36: fragment loads hit 32 distinct banks
-  __shared__ float Zs[TCK][TCN + 8];   // row stride 72: likewise
-  const int64_t i0 = (int64_t)blockIdx.x * TCM;
-  const int j0 = blockIdx.y * TCN;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gid = lane >> 2, tig = lane & 3;
-  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;   // this warp's 32 x 32 sub-tile
-  float acc[2][4][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
-  for (int c0 = 0; c0 < ks; c0 += TCK) {
-    // stage G[i0 .. +128, c0 .. +32] and Z[c0 .. +32, j0 .. +64], zero outside
-    for (int idx = threadIdx.x; idx < TCM * TCK; idx += 256) {
-      const int ii = idx / TCK, cc = idx % TCK;
-      const int64_t i = i0 + ii;
-      Gs[ii][cc] = (i < t && c0 + cc < ks) ? G[i * ld_g + c0 + cc] : 0.f;
-    }
-    for (int idx = threadIdx.x; idx < TCK * TCN; idx += 256) {
-      const int cc = idx / TCN, jj = idx % TCN;
-      Zs[cc][jj] = (c0 + cc < ks && j0 + jj < s) ? Z[(int64_t)(c0 + cc) * s + j0 + jj] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k8 = 0; k8 < TCK; k8 += 8) {
-      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int r = wm + 16 * a + gid;
-        split_tf32(Gs[r][k8 + tig], ah[a][0], al[a][0]);
-        split_tf32(Gs[r + 8][k8 + tig], ah[a][1], al[a][1]);
-        split_tf32(Gs[r][k8 + tig + 4], ah[a][2], al[a][2]);
-        split_tf32(Gs[r + 8][k8 + tig + 4], ah[a][3], al[a][3]);
-      }
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int cidx = wn + 8 * b + gid;
-        split_tf32(Zs[k8 + tig][cidx], bh[b][0], bl[b][0]);
-        split_tf32(Zs[k8 + tig + 4][cidx], bh[b][1], bl[b][1]);
-      }
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          mma_tf32(acc[a][b], al[a], bh[b]);
-          mma_tf32(acc[a][b], ah[a], bl[b]);
-          mma_tf32(acc[a][b], ah[a], bh[b]);
-        }
-    }
-    __syncthreads();
-  }
-  // accumulator (row = point, column = sample): q = 0, 1 -> (gid, 2 tig + q), q = 2, 3 -> (gid + 8, 2 tig + q - 2)
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t i = i0 + wm + 16 * a + gid + 8 * h;
-      if (i >= t) continue;
-      const float m_ = mu[i];
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int j = j0 + wn + 8 * b + 2 * tig + q;
-          if (j < s) F[(int64_t)j * t + i] = m_ + acc[a][b][2 * h + q];
-        }
-    }
+// byte offset of element (row r, column k) of a chunk tile in the canonical layout
+__device__ __forceinline__ uint32_t umma_off(int r, int k) {
+  return (uint32_t)(k >> 2) * U_SLICE_BYTES + (uint32_t)(r >> 3) * 128u + (uint32_t)(r & 7) * 16u +
+         (uint32_t)(k & 3) * 4u;
 }
+
+__global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __restrict__ G, int ld_g,
+                                                              const float* __restrict__ Z, int s, int ks,
+                                                              const float* __restrict__ mu, int64_t t,
+                                                              float* __restrict__ F, DevStatus* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 8 * (size_t)U_TILE_BYTES);   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * UM;
+  const int j0 = blockIdx.y * UN;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(UN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  uint32_t uses[2] = {0u, 0u};   // commits made to each buffer's barrier
+  // the operands of one chunk, held in registers between their (early) global
+  // loads and their conversion into shared memory: thread -> G row tid / 2,
+  // 4-column groups (tid & 1) * 4 + 8 q; Z sample column tid % 128, 4-row
+  // groups (tid / 128) * 4 + 8 q (q < UKC / 8)
+  constexpr int QG = UKC / 8;
+  float4 greg[QG];
+  float zreg[QG][4];
+  const int gr = tid >> 1, gk = (tid & 1) * 4;
+  const int zn = tid & (UN - 1), zk = (tid >> 7) * 4;
+  const int64_t gi = i0 + gr;
+  const int zj = j0 + zn;
+  auto load_chunk = [&](int c0) {
+    const float* grow = G + gi * ld_g + c0;
+#pragma unroll
+    for (int q = 0; q < QG; ++q) {
+      const int k = gk + 8 * q;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gi < t && c0 + k < ks) {
+        if (c0 + k + 3 < ks) {
+          x = *reinterpret_cast<const float4*>(grow + k);
+        } else {
+          x.x = grow[k];
+          if (c0 + k + 1 < ks) x.y = grow[k + 1];
+          if (c0 + k + 2 < ks) x.z = grow[k + 2];
+        }
+      }
+      greg[q] = x;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kz = zk + 8 * q + u;
+        zreg[q][u] = (zj < s && c0 + kz < ks) ? Z[(int64_t)(c0 + kz) * s + zj] : 0.f;
+      }
+    }
+  };
+  load_chunk(0);
+  int chunk = 0;
+  for (int c0 = 0; c0 < ks; c0 += UKC, ++chunk) {
+    const int b = chunk & 1;
+    unsigned char* Ahi = smem_raw + (size_t)b * 4 * U_TILE_BYTES;
+    unsigned char* Alo = Ahi + U_TILE_BYTES;
+    unsigned char* Bhi = Alo + U_TILE_BYTES;
+    unsigned char* Blo = Bhi + U_TILE_BYTES;
+    // the tensor core must be done with this buffer (chunk - 2) before it is rewritten
+    if (uses[b] > 0) {
+      ok = ok && mbar_wait_bounded(&bar[b], (uses[b] - 1u) & 1u);
+      if (__syncthreads_or(!ok)) break;
+    }
+    const int kc = min(UKC, (ks - c0 + 7) & ~7);   // columns of this chunk, padded to 8
+    // the held operands as TF32 hi / lo parts, one 16-byte core-matrix row
+    // (4 consecutive K) per store; zero outside the matrices
+#pragma unroll
+    for (int q = 0; q < QG; ++q) {
+      if (8 * q + gk < kc) {
+        uint4 h, l;
+        split_tf32(greg[q].x, h.x, l.x);
+        split_tf32(greg[q].y, h.y, l.y);
+        split_tf32(greg[q].z, h.z, l.z);
+        split_tf32(greg[q].w, h.w, l.w);
+        const uint32_t o = umma_off(gr, gk + 8 * q);
+        *reinterpret_cast<uint4*>(Ahi + o) = h;
+        *reinterpret_cast<uint4*>(Alo + o) = l;
+      }
+      if (8 * q + zk < kc) {
+        uint4 h, l;
+        split_tf32(zreg[q][0], h.x, l.x);
+        split_tf32(zreg[q][1], h.y, l.y);
+        split_tf32(zreg[q][2], h.z, l.z);
+        split_tf32(zreg[q][3], h.w, l.w);
+        const uint32_t o = umma_off(zn, zk + 8 * q);
+        *reinterpret_cast<uint4*>(Bhi + o) = h;
+        *reinterpret_cast<uint4*>(Blo + o) = l;
+      }
+    }
+    // the next chunk's global loads are in flight during the MMAs of this one
+    if (c0 + UKC < ks) load_chunk(c0 + UKC);
+    fence_proxy_async();   // the generic-proxy stores become visible to the tensor core
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo), bhi = smem_u32(Bhi), blo = smem_u32(Blo);
+      for (int q = 0; q < kc / 8; ++q) {
+        const uint32_t off = (uint32_t)q * 2u * U_SLICE_BYTES;
+        const uint32_t acc0 = (c0 > 0 || q > 0) ? 1u : 0u;
+        umma_tf32(tmem, umma_smem_desc(ahi + off), umma_smem_desc(bhi + off), acc0);
+        umma_tf32(tmem, umma_smem_desc(ahi + off), umma_smem_desc(blo + off), 1u);
+        umma_tf32(tmem, umma_smem_desc(alo + off), umma_smem_desc(bhi + off), 1u);
+      }
+      umma_commit(&bar[b]);
+    }
+    uses[b] += 1u;
+  }
+  // the last commit covers every MMA issued before it
+  if (ok && chunk > 0) {
+    const int b = (chunk - 1) & 1;
+    ok = mbar_wait_bounded(&bar[b], (uses[b] - 1u) & 1u);
+    ok = !__syncthreads_or(!ok);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int lb = 32 * (warp & 3);            // this warp's tensor-memory lanes (points)
+    const int cb = 64 * (warp >> 2);           // and its 64 accumulator columns (samples)
+    const int64_t i = i0 + lb + lane;
+    const float m_ = i < t ? mu[i] : 0.f;
+#pragma unroll 1
+    for (int c = 0; c < 64; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)(cb + c), v);
+      if (i < t) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int j = j0 + cb + c + q;
+          if (j < s) F[(int64_t)j * t + i] = m_ + v[q];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    dev_flag(status, LOVE_ERR_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
+  }
+}
+
 
 // Philox4x32-10: 10 rounds of (hi0,lo0) = M0 x0, (hi1,lo1) = M1 x2,
 // x <- (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0), key += Weyl constants between rounds.
@@ -709,8 +842,10 @@ static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_co
     default: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 3><<<blocks, 256, 0, s>>>(a);
   }
   if constexpr (std::is_same<T, float>::value) {
-    dim3 grid((unsigned)((t + TCM - 1) / TCM), (unsigned)((s_count + TCN - 1) / TCN));
-    LOVE_COUNT_LAUNCH(); k_sample_gemm_tc<<<grid, 256, 0, s>>>(Gp, ld_g, Z, s_count, ks, mup, t, (float*)out);
+    dim3 grid((unsigned)((t + UM - 1) / UM), (unsigned)((s_count + UN - 1) / UN));
+    LOVE_TRY(allow_smem(k_sample_gemm_tc05, U_SMEM));
+    LOVE_COUNT_LAUNCH();
+    k_sample_gemm_tc05<<<grid, 256, U_SMEM, s>>>(Gp, ld_g, Z, s_count, ks, mup, t, (float*)out, c->status);
   } else {
     dim3 grid((unsigned)((t + 63) / 64), (unsigned)((s_count + 63) / 64));
     LOVE_COUNT_LAUNCH(); k_sample_gemm<T><<<grid, 256, 0, s>>>(Gp, ld_g, Z, s_count, ks, mup, t, (T*)out);
