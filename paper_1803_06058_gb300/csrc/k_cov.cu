@@ -7,15 +7,17 @@
 //
 //   k_cov_gather   warp per point: v = Rt^T w (lanes over columns, 4^d rows
 //                  of the packed cache) and the point's stencil (base, weights)
-//   k_cov_gemm_tc  FP32 data: V1 V2^T on the tensor cores (mma.sync TF32 with
-//                  each operand split in two TF32 parts, as the sample GEMM),
-//                  the prior and the subtraction in FP64 in the epilogue
+//   k_cov_gemm_tc05  FP32 data: V2 V1^T on the 5th-generation tensor cores
+//                  (tcgen05 kind::tf32, each operand split in two TF32 parts,
+//                  as the sample GEMM; accumulator in tensor memory), the prior
+//                  and the subtraction in FP64 in the epilogue
 //   k_cov_gemm     FP64 data: the same product in FP64 on the SIMT pipes
 #include <type_traits>
 #include <utility>
 #include <vector>
 
 #include "love_internal.cuh"
+#include "umma.cuh"
 
 namespace love {
 namespace {
@@ -166,98 +168,94 @@ __device__ __forceinline__ void cov_store(const CovPrior& cp, const CovPts& A, c
   out[i * B.t + j] = v;
 }
 
-// ---- FP32: V1 V2^T on the tensor cores, split TF32 ----
-__device__ __forceinline__ uint32_t cv_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void cv_split(float x, uint32_t& hi, uint32_t& lo) {
-  hi = cv_tf32(x);
-  lo = cv_tf32(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void cv_mma(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-constexpr int CM = 128, CN = 64, CK = 32;
+// ---- FP32: V2 V1^T on the tensor cores (tcgen05), split TF32 ----
+// A CTA computes 128 points of set 2 (tensor-memory lanes: A = V2 rows) by
+// 128 points of set 1 (accumulator columns: B = V1 rows), K chunks through two
+// shared-memory buffers with the next chunk's loads held in registers, one
+// thread issuing the MMAs and committing them to the buffer's mbarrier.  In
+// the epilogue lane j and column i give cov[i][j] (consecutive j per store).
 template <int D>
-__global__ void __launch_bounds__(256) k_cov_gemm_tc(CovPts A, CovPts B, int k, int ldv, CovPrior cp,
-                                                     float* __restrict__ out) {
-  __shared__ float As[CM][CK + 4];
-  __shared__ float Bs[CN][CK + 4];
+__global__ void __launch_bounds__(256, 1) k_cov_gemm_tc05(CovPts A, CovPts B, int k, int ldv, CovPrior cp,
+                                                           float* __restrict__ out, DevStatus* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 8 * (size_t)U_TILE_BYTES);   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
   const float* V1 = reinterpret_cast<const float*>(A.V);
   const float* V2 = reinterpret_cast<const float*>(B.V);
-  const int64_t i0 = (int64_t)blockIdx.x * CM;
-  const int64_t j0 = (int64_t)blockIdx.y * CN;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gid = lane >> 2, tig = lane & 3;
-  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
-  float acc[2][4][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
-  for (int c0 = 0; c0 < k; c0 += CK) {
-    for (int idx = threadIdx.x; idx < CM * CK; idx += 256) {
-      const int ii = idx / CK, cc = idx % CK;
-      const int64_t i = i0 + ii;
-      As[ii][cc] = (i < A.t && c0 + cc < k) ? V1[i * ldv + c0 + cc] : 0.f;
-    }
-    for (int idx = threadIdx.x; idx < CN * CK; idx += 256) {
-      const int jj = idx / CK, cc = idx % CK;
-      const int64_t j = j0 + jj;
-      Bs[jj][cc] = (j < B.t && c0 + cc < k) ? V2[j * ldv + c0 + cc] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k8 = 0; k8 < CK; k8 += 8) {
-      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int r = wm + 16 * a + gid;
-        cv_split(As[r][k8 + tig], ah[a][0], al[a][0]);
-        cv_split(As[r + 8][k8 + tig], ah[a][1], al[a][1]);
-        cv_split(As[r][k8 + tig + 4], ah[a][2], al[a][2]);
-        cv_split(As[r + 8][k8 + tig + 4], ah[a][3], al[a][3]);
-      }
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int cidx = wn + 8 * b + gid;
-        cv_split(Bs[cidx][k8 + tig], bh[b][0], bl[b][0]);
-        cv_split(Bs[cidx][k8 + tig + 4], bh[b][1], bl[b][1]);
-      }
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          cv_mma(acc[a][b], al[a], bh[b]);
-          cv_mma(acc[a][b], ah[a], bl[b]);
-          cv_mma(acc[a][b], ah[a], bh[b]);
-        }
-    }
-    __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t j0 = (int64_t)blockIdx.x * UM;   // set 2 (lanes)
+  const int64_t i0 = (int64_t)blockIdx.y * UN;   // set 1 (columns)
+  if (warp == 0) tmem_alloc_warp(tmem_slot, UN);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
   }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t i = i0 + wm + 16 * a + gid + 8 * h;
-      if (i >= A.t) continue;
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int64_t j = j0 + wn + 8 * b + 2 * tig + q;
-          if (j < B.t) cov_store<float, D>(cp, A, B, i, j, (double)acc[a][b][2 * h + q], out);
-        }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  uint32_t uses[2] = {0u, 0u};
+  RowTileRegs ra, rb;
+  ra.load(V2, ldv, j0, B.t, 0, k, tid);
+  rb.load(V1, ldv, i0, A.t, 0, k, tid);
+  int chunk = 0;
+  for (int c0 = 0; c0 < k; c0 += UKC, ++chunk) {
+    const int b = chunk & 1;
+    unsigned char* Ahi = smem_raw + (size_t)b * 4 * U_TILE_BYTES;
+    unsigned char* Alo = Ahi + U_TILE_BYTES;
+    unsigned char* Bhi = Alo + U_TILE_BYTES;
+    unsigned char* Blo = Bhi + U_TILE_BYTES;
+    if (uses[b] > 0) {
+      ok = ok && mbar_wait_bounded(&bar[b], (uses[b] - 1u) & 1u);
+      if (__syncthreads_or(!ok)) break;
     }
+    const int kc = min(UKC, (k - c0 + 7) & ~7);
+    ra.store(Ahi, Alo, kc, tid);
+    rb.store(Bhi, Blo, kc, tid);
+    if (c0 + UKC < k) {
+      ra.load(V2, ldv, j0, B.t, c0 + UKC, k, tid);
+      rb.load(V1, ldv, i0, A.t, c0 + UKC, k, tid);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      umma_chunk(tmem, Ahi, Alo, Bhi, Blo, kc, c0 == 0);
+      umma_commit(&bar[b]);
+    }
+    uses[b] += 1u;
+  }
+  if (ok && chunk > 0) {
+    const int b = (chunk - 1) & 1;
+    ok = mbar_wait_bounded(&bar[b], (uses[b] - 1u) & 1u);
+    ok = !__syncthreads_or(!ok);
+  }
+  tc_fence_after();
+  if (ok) {
+    const int lb = 32 * (warp & 3), cb = 64 * (warp >> 2);
+    const int64_t j = j0 + lb + lane;
+#pragma unroll 1
+    for (int c = 0; c < 64; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)(cb + c), v);
+      if (j < B.t) {
+        for (int q = 0; q < 16; ++q) {
+          const int64_t i = i0 + cb + c + q;
+          if (i < A.t) cov_store<float, D>(cp, A, B, i, j, (double)v[q], out);
+        }
+      }
+    }
+  } else if (tid == 0) {
+    dev_flag(status, LOVE_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc_warp(tmem, UN);
+  }
 }
 
 // ---- FP64: SIMT tiles of 64 x 64, 4 x 4 per thread ----
@@ -381,11 +379,17 @@ love_status cov_launch(love_cache* c, int64_t t1, const void* x1, int64_t t2, co
       LOVE_TRY((gather_any<float, float>(c, ldv, A, s)));
       LOVE_TRY((gather_any<float, float>(c, ldv, B, s)));
     }
-    dim3 grid((unsigned)((t1 + CM - 1) / CM), (unsigned)((t2 + CN - 1) / CN));
-    LOVE_COUNT_LAUNCH();
-    if (D == 1) k_cov_gemm_tc<1><<<grid, 256, 0, s>>>(A, B, k, ldv, cp, (float*)out);
-    else if (D == 2) k_cov_gemm_tc<2><<<grid, 256, 0, s>>>(A, B, k, ldv, cp, (float*)out);
-    else k_cov_gemm_tc<3><<<grid, 256, 0, s>>>(A, B, k, ldv, cp, (float*)out);
+    dim3 g5((unsigned)((t2 + UM - 1) / UM), (unsigned)((t1 + UN - 1) / UN));
+    if (D == 1) {
+      LOVE_TRY(allow_smem(k_cov_gemm_tc05<1>, U_SMEM));
+      LOVE_COUNT_LAUNCH(); k_cov_gemm_tc05<1><<<g5, 256, U_SMEM, s>>>(A, B, k, ldv, cp, (float*)out, c->status);
+    } else if (D == 2) {
+      LOVE_TRY(allow_smem(k_cov_gemm_tc05<2>, U_SMEM));
+      LOVE_COUNT_LAUNCH(); k_cov_gemm_tc05<2><<<g5, 256, U_SMEM, s>>>(A, B, k, ldv, cp, (float*)out, c->status);
+    } else {
+      LOVE_TRY(allow_smem(k_cov_gemm_tc05<3>, U_SMEM));
+      LOVE_COUNT_LAUNCH(); k_cov_gemm_tc05<3><<<g5, 256, U_SMEM, s>>>(A, B, k, ldv, cp, (float*)out, c->status);
+    }
   }
   return cuda_check(cudaGetLastError());
 }

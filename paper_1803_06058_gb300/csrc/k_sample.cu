@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "love_internal.cuh"
+#include "umma.cuh"
 
 namespace love {
 namespace {
@@ -408,23 +409,6 @@ __global__ void __launch_bounds__(256) k_sample_gemm(const T* __restrict__ G, in
 }
 
 // ---------------------------------------------------------------------------
-// Split TF32 for the tensor-core form of the product below (Sec. 3.3, eq.
-// sample: F = mu + W*^T S Z is a dense t x k_s by k_s x s contraction).  Each
-// FP32 operand is split into two TF32 parts, x = hi + lo (hi = x rounded to
-// TF32, lo = the rounded remainder), and each product is accumulated as
-// hi*hi + hi*lo + lo*hi in FP32 (the lo*lo term, ~2^-22 relative, is dropped):
-// close to FP32 accuracy on the TF32 tensor path.
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-
-// ---------------------------------------------------------------------------
 // The product on the 5th-generation tensor cores (tcgen05, kind::tf32,
 // one CTA, accumulator in tensor memory).  A CTA computes a 128-point x
 // 128-sample tile D[i][j] = sum_c G[i][c] Z[c][j]:
@@ -442,53 +426,6 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w: lanes
 //     32 (w mod 4) .., columns 64 (w / 4) ..), adds mu and writes
 //     F[j][i] (sample-major, consecutive points per store).
-constexpr int UM = 128, UN = 128, UKC = 24;   // tile and K chunk (3 K steps of 8)
-constexpr uint32_t U_TILE_BYTES = UM * UKC * 4;   // one operand part per chunk (12 KB)
-constexpr uint32_t U_SLICE_BYTES = UM * 16;       // one 16-byte K slice of 128 rows (2 KB)
-constexpr size_t U_SMEM = 2 * 4 * (size_t)U_TILE_BYTES + 64;   // two buffers of 4 parts + barriers
-
-__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr) {
-  // start address >> 4 | leading (K) byte offset >> 4 | stride (M/N) byte offset >> 4 |
-  // descriptor version 1 (bit 46); no swizzle, base offset 0
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(U_SLICE_BYTES >> 4) << 16) |
-         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
-}
-// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
-// (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t U_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(UN >> 3) << 17) |
-                             ((uint32_t)(UM >> 4) << 24);
-
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(U_IDESC), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// byte offset of element (row r, column k) of a chunk tile in the canonical layout
-__device__ __forceinline__ uint32_t umma_off(int r, int k) {
-  return (uint32_t)(k >> 2) * U_SLICE_BYTES + (uint32_t)(r >> 3) * 128u + (uint32_t)(r & 7) * 16u +
-         (uint32_t)(k & 3) * 4u;
-}
-
 __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __restrict__ G, int ld_g,
                                                               const float* __restrict__ Z, int s, int ks,
                                                               const float* __restrict__ mu, int64_t t,
@@ -499,58 +436,38 @@ __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __rest
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t i0 = (int64_t)blockIdx.x * UM;
   const int j0 = blockIdx.y * UN;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(UN)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 0) tmem_alloc_warp(tmem_slot, UN);
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tc_fence_before();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
   uint32_t uses[2] = {0u, 0u};   // commits made to each buffer's barrier
-  // the operands of one chunk, held in registers between their (early) global
-  // loads and their conversion into shared memory: thread -> G row tid / 2,
-  // 4-column groups (tid & 1) * 4 + 8 q; Z sample column tid % 128, 4-row
+  // the operands of one chunk held in registers between their (early) global
+  // loads and their conversion into shared memory: G as a row-major tile;
+  // Z^T by sample column tid % 128 (coalesced along the samples) and 4-row
   // groups (tid / 128) * 4 + 8 q (q < UKC / 8)
   constexpr int QG = UKC / 8;
-  float4 greg[QG];
+  RowTileRegs greg;
   float zreg[QG][4];
-  const int gr = tid >> 1, gk = (tid & 1) * 4;
   const int zn = tid & (UN - 1), zk = (tid >> 7) * 4;
-  const int64_t gi = i0 + gr;
   const int zj = j0 + zn;
-  auto load_chunk = [&](int c0) {
-    const float* grow = G + gi * ld_g + c0;
+  auto load_z = [&](int c0) {
 #pragma unroll
-    for (int q = 0; q < QG; ++q) {
-      const int k = gk + 8 * q;
-      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gi < t && c0 + k < ks) {
-        if (c0 + k + 3 < ks) {
-          x = *reinterpret_cast<const float4*>(grow + k);
-        } else {
-          x.x = grow[k];
-          if (c0 + k + 1 < ks) x.y = grow[k + 1];
-          if (c0 + k + 2 < ks) x.z = grow[k + 2];
-        }
-      }
-      greg[q] = x;
+    for (int q = 0; q < QG; ++q)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int kz = zk + 8 * q + u;
         zreg[q][u] = (zj < s && c0 + kz < ks) ? Z[(int64_t)(c0 + kz) * s + zj] : 0.f;
       }
-    }
   };
-  load_chunk(0);
+  greg.load(G, ld_g, i0, t, 0, ks, tid);
+  load_z(0);
   int chunk = 0;
   for (int c0 = 0; c0 < ks; c0 += UKC, ++chunk) {
     const int b = chunk & 1;
@@ -566,18 +483,9 @@ __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __rest
     const int kc = min(UKC, (ks - c0 + 7) & ~7);   // columns of this chunk, padded to 8
     // the held operands as TF32 hi / lo parts, one 16-byte core-matrix row
     // (4 consecutive K) per store; zero outside the matrices
+    greg.store(Ahi, Alo, kc, tid);
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
-      if (8 * q + gk < kc) {
-        uint4 h, l;
-        split_tf32(greg[q].x, h.x, l.x);
-        split_tf32(greg[q].y, h.y, l.y);
-        split_tf32(greg[q].z, h.z, l.z);
-        split_tf32(greg[q].w, h.w, l.w);
-        const uint32_t o = umma_off(gr, gk + 8 * q);
-        *reinterpret_cast<uint4*>(Ahi + o) = h;
-        *reinterpret_cast<uint4*>(Alo + o) = l;
-      }
       if (8 * q + zk < kc) {
         uint4 h, l;
         split_tf32(zreg[q][0], h.x, l.x);
@@ -590,19 +498,15 @@ __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __rest
       }
     }
     // the next chunk's global loads are in flight during the MMAs of this one
-    if (c0 + UKC < ks) load_chunk(c0 + UKC);
+    if (c0 + UKC < ks) {
+      greg.load(G, ld_g, i0, t, c0 + UKC, ks, tid);
+      load_z(c0 + UKC);
+    }
     fence_proxy_async();   // the generic-proxy stores become visible to the tensor core
     __syncthreads();
     if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo), bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-      for (int q = 0; q < kc / 8; ++q) {
-        const uint32_t off = (uint32_t)q * 2u * U_SLICE_BYTES;
-        const uint32_t acc0 = (c0 > 0 || q > 0) ? 1u : 0u;
-        umma_tf32(tmem, umma_smem_desc(ahi + off), umma_smem_desc(bhi + off), acc0);
-        umma_tf32(tmem, umma_smem_desc(ahi + off), umma_smem_desc(blo + off), 1u);
-        umma_tf32(tmem, umma_smem_desc(alo + off), umma_smem_desc(bhi + off), 1u);
-      }
+      tc_fence_after();
+      umma_chunk(tmem, Ahi, Alo, Bhi, Blo, kc, c0 == 0);
       umma_commit(&bar[b]);
     }
     uses[b] += 1u;
@@ -613,7 +517,7 @@ __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __rest
     ok = mbar_wait_bounded(&bar[b], (uses[b] - 1u) & 1u);
     ok = !__syncthreads_or(!ok);
   }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tc_fence_after();
   if (ok) {
     const int lb = 32 * (warp & 3);            // this warp's tensor-memory lanes (points)
     const int cb = 64 * (warp >> 2);           // and its 64 accumulator columns (samples)
@@ -634,11 +538,11 @@ __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __rest
   } else if (tid == 0) {
     dev_flag(status, LOVE_ERR_TIMEOUT);
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UN) : "memory");
+    tc_fence_after();
+    tmem_dealloc_warp(tmem, UN);
   }
 }
 
