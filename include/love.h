@@ -181,6 +181,18 @@ LOVE_API love_status love_cache_destroy(love_cache_t cache);
 LOVE_API love_status love_predict_mean_var(love_cache_t cache, int64_t t, const void* x_test,
                                   void* mean, void* var, love_stream_t stream);
 
+/* love_predict_mean_var_host -- love_predict_mean_var on HOST buffers: x_test
+ * (t x dim), mean (t, or NULL) and var (t) in host memory, ski dtype.  Page-
+ * locked buffers (cudaHostAlloc, cudaHostRegister, torch pin_memory) are read
+ * and written by the predict kernel itself through their device mapping, over
+ * the CPU-GPU link, with no separate copies; any other host buffer goes
+ * through device staging buffers in chunks of 2^20 points (taken from the
+ * cache's allocator and released before returning).  Synchronises `stream`:
+ * the results are in the host buffers when the call returns.  t = 0 is a
+ * no-op; errors as love_predict_mean_var. */
+LOVE_API love_status love_predict_mean_var_host(love_cache_t cache, int64_t t, const void* x_test, void* mean,
+                                                void* var, love_stream_t stream);
+
 /* love_predict_covariance -- posterior cross-covariances between two sets of
  * test points (Sec. 3: eq. pred_covar_ski_fast for i != j, Algorithm 1 with
  * two point sets):  cov[i, j] = p(x1_i, x2_j) - (Rt^T w1_i) . (Rt^T w2_j), with

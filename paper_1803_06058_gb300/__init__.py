@@ -345,6 +345,26 @@ def love_predict_mean_var(cache: Cache, x_test: torch.Tensor, want_mean: bool = 
     return mean, var
 
 
+def love_predict_mean_var_host(cache: Cache, x_test: torch.Tensor, want_mean: bool = True,
+                               stream=None, out_mean=None, out_var=None):
+    """love_predict_mean_var on host (CPU) tensors; pinned tensors are read and
+    written by the kernel directly.  Outputs are pinned CPU tensors unless given.
+    Returns when the results are in the host tensors."""
+    dt = _TORCH[cache.dtype]
+    if x_test.is_cuda:
+        raise ValueError("love_predict_mean_var_host takes host tensors")
+    x_test = x_test.to(dt).reshape(-1, cache.dim).contiguous()
+    t = x_test.shape[0]
+    pin = x_test.is_pinned()
+    var = out_var if out_var is not None else torch.empty(t, dtype=dt, pin_memory=pin)
+    mean = None
+    if want_mean:
+        mean = out_mean if out_mean is not None else torch.empty(t, dtype=dt, pin_memory=pin)
+    check("love_predict_mean_var_host",
+          lib().love_predict_mean_var_host(cache.handle, t, _ptr(x_test), _ptr(mean), _ptr(var), _stream(stream)))
+    return mean, var
+
+
 def love_predict_covariance(cache: Cache, x1: torch.Tensor, x2: Optional[torch.Tensor] = None,
                             stream=None) -> torch.Tensor:
     """t1 x t2 posterior cross-covariances (x2 defaults to x1)."""

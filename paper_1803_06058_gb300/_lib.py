@@ -72,6 +72,7 @@ SIGNATURES = {
                                   C.POINTER(C.c_int)]),
     "love_cache_destroy": (C.c_int, [VP]),
     "love_predict_mean_var": (C.c_int, [VP, C.c_int64, VP, VP, VP, VP]),
+    "love_predict_mean_var_host": (C.c_int, [VP, C.c_int64, VP, VP, VP, VP]),
     "love_sample": (C.c_int, [VP, C.c_int64, VP, C.c_int, VP, C.c_uint64, VP, VP]),
     "love_predict_var_root": (C.c_int, [VP, C.c_int64, VP, VP, VP]),
     "love_predict_covariance": (C.c_int, [VP, C.c_int64, VP, C.c_int64, VP, VP, VP]),

@@ -167,16 +167,31 @@ __device__ __forceinline__ void predict_groups(const PredArgs& a, int64_t warp_f
   const int NG = a.ld / VC;
   const V* __restrict__ base_ptr = reinterpret_cast<const V*>(a.Rc);
   const R* __restrict__ xs = reinterpret_cast<const R*>(a.x);
+  // the coordinates of the group's next point are loaded one iteration ahead
+  // (they may live in host memory, read over the CPU-GPU link)
+  R xnext[D];
+  {
+    const int64_t pt = warp_first + lane / G;
+#pragma unroll
+    for (int e = 0; e < D; ++e) xnext[e] = pt < a.t ? xs[pt * D + e] : R(0);
+  }
   for (int64_t pt0 = warp_first; pt0 < a.t; pt0 += gstride) {
     const int64_t pt = pt0 + lane / G;
     const bool live = pt < a.t;
+    R xcur[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) xcur[e] = xnext[e];
+    {
+      const int64_t pn = pt + gstride;
+#pragma unroll
+      for (int e = 0; e < D; ++e) xnext[e] = pn < a.t ? xs[pn * D + e] : R(0);
+    }
     R w[D][4];
     int base[D];
     bool ok = live;
 #pragma unroll
     for (int e = 0; e < D; ++e) {
-      R xv = live ? xs[pt * D + e] : R(0);
-      R s = grid_coord(xv, a.g, e);
+      R s = grid_coord(live ? xcur[e] : R(0), a.g, e);
       ok &= keys_weights(s, a.g.g[e], base[e], w[e]);
     }
     // row index of stencil row q (0 <= q < 4^D), weight

@@ -598,6 +598,56 @@ love_status love_predict_mean_var(love_cache_t c, int64_t t, const void* x_test,
   return predict_launch(c, t, x_test, mean, var, cs(stream));
 }
 
+// device address of a page-locked host buffer, or nullptr (pageable memory)
+static void* host_mapped(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+love_status love_predict_mean_var_host(love_cache_t c, int64_t t, const void* x_test, void* mean, void* var,
+                                       love_stream_t stream) {
+  if (!c || t < 0) return LOVE_ERR_ARG;
+  if (t == 0) return LOVE_OK;
+  if (!x_test || !var) return LOVE_ERR_ARG;
+  if (mean && !(c->flags & LOVE_WANT_MEAN)) return LOVE_ERR_STATE;
+  cudaStream_t s = cs(stream);
+  void* dx = host_mapped(x_test);
+  void* dv = host_mapped(var);
+  void* dm = mean ? host_mapped(mean) : nullptr;
+  if (dx && dv && (!mean || dm)) {
+    // page-locked: the kernel reads x and writes the results over the link
+    LOVE_TRY(predict_launch(c, t, dx, dm, dv, s));
+    return cuda_check(cudaStreamSynchronize(s));
+  }
+  const size_t es = dtype_size(c->dtype);
+  const int dim = c->grid.dim;
+  const int64_t chunk = std::min<int64_t>(t, int64_t(1) << 20);
+  const size_t xb = es * (size_t)chunk * dim, ob = es * (size_t)chunk;
+  void* bx = c->alloc.alloc(xb, s);
+  void* bv = c->alloc.alloc(ob, s);
+  void* bm = mean ? c->alloc.alloc(ob, s) : nullptr;
+  love_status rc = (bx && bv && (!mean || bm)) ? LOVE_OK : LOVE_ERR_OOM;
+  for (int64_t o = 0; o < t && rc == LOVE_OK; o += chunk) {
+    const int64_t n = std::min(chunk, t - o);
+    rc = cuda_check(cudaMemcpyAsync(bx, (const char*)x_test + es * (size_t)o * dim, es * (size_t)n * dim,
+                                    cudaMemcpyHostToDevice, s));
+    if (rc == LOVE_OK) rc = predict_launch(c, n, bx, bm, bv, s);
+    if (rc == LOVE_OK)
+      rc = cuda_check(cudaMemcpyAsync((char*)var + es * (size_t)o, bv, es * (size_t)n, cudaMemcpyDeviceToHost, s));
+    if (rc == LOVE_OK && mean)
+      rc = cuda_check(cudaMemcpyAsync((char*)mean + es * (size_t)o, bm, es * (size_t)n, cudaMemcpyDeviceToHost, s));
+  }
+  if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
+  c->alloc.free(bx, xb, s);
+  c->alloc.free(bv, ob, s);
+  if (bm) c->alloc.free(bm, ob, s);
+  return rc;
+}
+
 love_status love_predict_covariance(love_cache_t c, int64_t t1, const void* x1, int64_t t2, const void* x2,
                                     void* cov, love_stream_t stream) {
   if (!c || t1 < 0 || t2 < 0) return LOVE_ERR_ARG;
