@@ -2375,17 +2375,26 @@ __device__ __forceinline__ uint64_t splitmix64_output(uint64_t seed, uint64_t i)
   return z ^ (z >> 31);
 }
 
-__global__ void k_rademacher(int64_t m, int64_t m_pad, uint64_t seed, double* __restrict__ q0, LanczosState* st) {
+template <typename QT>
+__global__ void k_rademacher(int64_t m, int64_t m_pad, uint64_t seed, QT* __restrict__ q0, LanczosState* st) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m_pad) q0[i] = i < m ? ((splitmix64_output(seed, (uint64_t)i) & 1ull) ? 1.0 : -1.0) : 0.0;
+  if (i < m_pad) q0[i] = i < m ? ((splitmix64_output(seed, (uint64_t)i) & 1ull) ? QT(1) : QT(-1)) : QT(0);
   if (i == 0) st->scal[0] = 1.0 / sqrt((double)m);
 }
-__global__ void k_normalize_col(double* __restrict__ q, int64_t n_pad, const double* __restrict__ scal,
+template <typename QT>
+__global__ void k_normalize_col(QT* __restrict__ q, int64_t n_pad, const double* __restrict__ scal,
                                 const LanczosState* st) {
   if (st->done) return;
-  const double sc = *scal;
+  const QT sc = (QT)*scal;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x)
     q[i] *= sc;
+}
+// q (stored Lanczos vector) as FP64 for the operator product
+template <typename QT>
+__global__ void k_to_double(const QT* __restrict__ q, int64_t m, double* __restrict__ qd, const LanczosState* st) {
+  if (st->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    qd[i] = (double)q[i];
 }
 // Partial products of the sampler operator's low-rank term (R = Rt, m x k,
 // column-major): tp[c * RS + rs] = sum over rows of slice rs of R[r, c] q[r],
@@ -2411,9 +2420,10 @@ __global__ void k_gemv_t(const T* __restrict__ R, int64_t ldr, int64_t m, const 
 // y[r] = Kq[r] - sum_c R[r, c] t[c]  (0 on padding rows); t[c] = the sum of
 // the RS slice partials (fixed order).  A block covers 32 rows: warp w takes
 // the columns w, w + 8, ..., lane l row l, then the 8 warp sums are added.
-template <typename T>
+// (y in the storage type of the Lanczos vectors: the FP64 difference rounded once)
+template <typename T, typename YT>
 __global__ void k_gemv_n_sub(const T* __restrict__ R, int64_t ldr, int64_t m, int64_t m_pad, int k, int RS,
-                             const double* __restrict__ tp, const double* __restrict__ Kq, double* __restrict__ y,
+                             const double* __restrict__ tp, const double* __restrict__ Kq, YT* __restrict__ y,
                              const LanczosState* st) {
   extern __shared__ double t_s[];   // [k] then [8][32]
   if (st->done) return;
@@ -2437,56 +2447,68 @@ __global__ void k_gemv_n_sub(const T* __restrict__ R, int64_t ldr, int64_t m, in
     double sum = 0.0;
 #pragma unroll
     for (int v = 0; v < 8; ++v) sum += ws[v * 32 + lane];
-    y[r] = r < m ? Kq[r] - sum : 0.0;
+    y[r] = r < m ? (YT)(Kq[r] - sum) : YT(0);
   }
 }
 
 }  // namespace
 
+// The Lanczos vectors Q' are stored in T (FP32 for an FP32 ski): the operator
+// product M q is formed in FP64 (K_UU q and Rt (Rt^T q) cancel to ~1e-7 of
+// their size) and rounded once to T, and the reorthogonalisation sweeps run on
+// T with double-float (FP32) or FP64 sums -- on this part FP64 arithmetic runs
+// at ~1/64 of the FP32 rate, and FP32 storage keeps Q' orthonormal to the
+// accuracy of an FP32 root.
 template <typename T>
 love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
-                            int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
+                            int k, int ks, uint64_t seed, double tau, T* Q, int64_t ldq, double* alpha_h,
                             double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s) {
   const int64_t m = gh.m, m_pad = ldq;
   if (ks < 1 || ks > LOVE_MAX_K || m_pad % TILE_R) return LOVE_ERR_ARG;
-  const int bc = box_cols(sizeof(double));
+  const int bc = box_cols(sizeof(T));
   const int max_grid = std::max(TILE_CTAS_PER_SM * num_sms(), 1024);
-  DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s);
+  constexpr bool conv = sizeof(T) != sizeof(double);
+  DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s), qdb(al, s);
   size_t fwb = fft_work_bytes(gh, fft, 1, true);
   if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)max_grid * (ks + 1)) ||
-      !kq.get(sizeof(double) * m) || !y.get(sizeof(double) * m_pad) ||
+      !kq.get(sizeof(double) * m) || !y.get(sizeof(T) * m_pad) ||
       !tv.get(sizeof(double) * (size_t)(k + 1) * (size_t)ceil_div(m, GEMV_SLICE)) ||
-      !fw.get(std::max<size_t>(fwb, 16)))
+      !fw.get(std::max<size_t>(fwb, 16)) || (conv && !qdb.get(sizeof(double) * m)))
     return LOVE_ERR_OOM;
   LanczosState* st = stb.as<LanczosState>();
   LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, ks, tau);
-  LOVE_COUNT_LAUNCH(); k_rademacher<<<ceil_div(m_pad, 256), 256, 0, s>>>(m, m_pad, seed, Q, st);
+  LOVE_COUNT_LAUNCH(); k_rademacher<T><<<ceil_div(m_pad, 256), 256, 0, s>>>(m, m_pad, seed, Q, st);
   LOVE_LAUNCH_CHECK();
-  TileArgs<double> ta{};
+  TileArgs<T> ta{};
   ta.n_pad = m_pad;
   ta.kcols = ks;
   ta.bc = bc;
   ta.Q = Q;
   ta.ldq = ldq;
-  ta.y = y.as<double>();
+  ta.y = y.as<T>();
   ta.partial = part.as<double2>();
   ta.st = st;
   ta.status = status;
   const int nb = std::min(4 * num_sms(), ceil_div(m_pad, 256));
   const int RS = ceil_div(m, GEMV_SLICE);
   const size_t nsub_smem = sizeof(double) * ((size_t)k + 8 * 32);
-  LOVE_TRY(allow_smem(k_gemv_n_sub<T>, nsub_smem));
+  LOVE_TRY(allow_smem(k_gemv_n_sub<T, T>, nsub_smem));
   for (int j = 0; j < ks; ++j) {
-    double* qj = Q + (int64_t)j * ldq;
-    LOVE_COUNT_LAUNCH(); k_normalize_col<<<nb, 256, 0, s>>>(qj, m_pad, st->scal + j, st);
-    LOVE_TRY(kuu_apply<double>(gh, fft, qj, kq.as<double>(), 1, m, fw.p, -1, s));
-    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<dim3(k, RS), 256, 0, s>>>(Rt, ldr, m, qj, tv.as<double>(), st);
-    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T><<<ceil_div(m_pad, 32), 256, nsub_smem, s>>>(Rt, ldr, m, m_pad, k, RS, tv.as<double>(), kq.as<double>(), y.as<double>(), st);
+    T* qj = Q + (int64_t)j * ldq;
+    LOVE_COUNT_LAUNCH(); k_normalize_col<T><<<nb, 256, 0, s>>>(qj, m_pad, st->scal + j, st);
+    const double* qd = reinterpret_cast<const double*>(qj);
+    if (conv) {
+      LOVE_COUNT_LAUNCH(); k_to_double<T><<<nb, 256, 0, s>>>(qj, m, qdb.as<double>(), st);
+      qd = qdb.as<double>();
+    }
+    LOVE_TRY(kuu_apply<double>(gh, fft, qd, kq.as<double>(), 1, m, fw.p, -1, s));
+    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<dim3(k, RS), 256, 0, s>>>(Rt, ldr, m, qd, tv.as<double>(), st);
+    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T, T><<<ceil_div(m_pad, 32), 256, nsub_smem, s>>>(Rt, ldr, m, m_pad, k, RS, tv.as<double>(), kq.as<double>(), y.as<T>(), st);
     LOVE_LAUNCH_CHECK();
     ta.j = j;
-    LOVE_TRY(tile_run<double, MODE_DOT>(ta, s));
-    LOVE_TRY(tile_run<double, MODE_UPDATE_DOT>(ta, s));
-    LOVE_TRY(tile_run<double, MODE_UPDATE_NORM>(ta, s));
+    LOVE_TRY(tile_run<T, MODE_DOT>(ta, s));
+    LOVE_TRY(tile_run<T, MODE_UPDATE_DOT>(ta, s));
+    LOVE_TRY(tile_run<T, MODE_UPDATE_NORM>(ta, s));
   }
   int keff = 0;
   LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -2498,7 +2520,7 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
 }
 
 template love_status sampler_lanczos<float>(const GridHost&, const FftPlan*, const Allocator&, const float*, int64_t,
-                                            int, int, uint64_t, double, double*, int64_t, double*, double*, int*,
+                                            int, int, uint64_t, double, float*, int64_t, double*, double*, int*,
                                             DevStatus*, cudaStream_t);
 template love_status sampler_lanczos<double>(const GridHost&, const FftPlan*, const Allocator&, const double*,
                                              int64_t, int, int, uint64_t, double, double*, int64_t, double*, double*,
@@ -2744,7 +2766,7 @@ love_status mean_grid_gmres(love_ski* ski, double tol, int max_iter, double* a, 
     const int steps = std::min(GM_R, max_iter - total);
     for (int j = 0; j < steps; ++j) {
       double* vj = V + (int64_t)j * m_pad;
-      LOVE_COUNT_LAUNCH(); k_normalize_col<<<nb, 256, 0, s>>>(vj, m_pad, st->scal + j, st);
+      LOVE_COUNT_LAUNCH(); k_normalize_col<double><<<nb, 256, 0, s>>>(vj, m_pad, st->scal + j, st);
       LOVE_TRY(pmul(vj, pv));
       LOVE_TRY(kmul(pv, kv));
       LOVE_COUNT_LAUNCH(); k_gm_band<<<mblocks, 256, 0, s>>>(m, m_pad, Gb.as<double>(), kv, pv, gh.noise, yv, st);

@@ -4,9 +4,11 @@
 // k' Lanczos steps on M = K_UU - R^T R' (k_lanczos.cu: sampler_lanczos) give
 // Q', T'; with T' = L' L'^T the root is S = Q' L' (m x k').  When T' is not
 // positive definite (M is a difference of two nearly equal PSD matrices, so
-// rounding can push small eigenvalues below zero) the root is taken from the
-// eigendecomposition T' = V diag(lam) V^T instead: S = Q' V diag(sqrt(max(lam, 0))),
-// with the eigenpairs from cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5).
+// rounding can push small eigenvalues below zero) the root is the Cholesky
+// factor of T' + delta I, delta = -lambda_min(T') plus rounding (Sturm-count
+// multisection); should that fail too, it is taken from the eigendecomposition
+// T' = V diag(lam) V^T: S = Q' V diag(sqrt(max(lam, 0))), with the eigenpairs
+// from cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5).
 //
 // Test phase (eq. sample): F = mu 1^T + (W*^T S Z)^T, F sample-major (s x t):
 //   gather   G = W*^T S (t x k') and mu = W*^T a     (4^d rows of S per point)
@@ -102,7 +104,7 @@ __global__ void k_tri_shift(const double* alpha, const double* beta, int k, doub
 
 // S[r, c] = d_c Q'[r, c] + e_c Q'[r, c+1]   (S = Q' L', L' lower bidiagonal), row-major ld_s
 template <typename T>
-__global__ void k_root_from_chol(const double* __restrict__ Q, int64_t ldq, int64_t m, int k, const double* d,
+__global__ void k_root_from_chol(const T* __restrict__ Q, int64_t ldq, int64_t m, int k, const double* d,
                                  const double* e, T* __restrict__ S, int ld_s) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * ld_s) return;
@@ -243,7 +245,7 @@ __global__ void k_scale_eig(const double* lam, const double* V, int n, double* B
 
 // S[r, c] = sum_j Q'[r, j] B[j, c]  (arithmetic in T; S row-major ld_s)
 template <typename T>
-__global__ void k_root_from_eig(const double* __restrict__ Q, int64_t ldq, int64_t m, int k,
+__global__ void k_root_from_eig(const T* __restrict__ Q, int64_t ldq, int64_t m, int k,
                                 const double* __restrict__ B, T* __restrict__ S, int ld_s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Bs = reinterpret_cast<T*>(smem_raw);  // k x k
@@ -616,11 +618,11 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
   const int64_t m = g.m;
   const int64_t m_pad = (m + 255) / 256 * 256;
   Buf Qb(al, s), ab(al, s), okb(al, s);
-  if (!Qb.get(sizeof(double) * m_pad * ks) || !ab.get(sizeof(double) * 5 * (ks + 1)) || !okb.get(sizeof(int)))
+  if (!Qb.get(sizeof(T) * m_pad * ks) || !ab.get(sizeof(double) * 5 * (ks + 1)) || !okb.get(sizeof(int)))
     return LOVE_ERR_OOM;
   std::vector<double> alpha(ks + 1), beta(ks + 1);
   int keff = 0;
-  LOVE_TRY(sampler_lanczos<T>(g, ski->fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<double>(), m_pad, alpha.data(),
+  LOVE_TRY(sampler_lanczos<T>(g, ski->fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<T>(), m_pad, alpha.data(),
                               beta.data(), &keff, c->status, s));
   if (keff < 1) return LOVE_ERR_NAN;
   double* ad = ab.as<double>();
@@ -652,7 +654,7 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
   c->S = al.alloc(sizeof(T) * (size_t)m * c->ld_s, s);
   if (!c->S) return LOVE_ERR_OOM;
   if (ok) {
-    LOVE_COUNT_LAUNCH(); k_root_from_chol<T><<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(Qb.as<double>(), m_pad, m, keff, dd, ed, (T*)c->S, c->ld_s);
+    LOVE_COUNT_LAUNCH(); k_root_from_chol<T><<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(Qb.as<T>(), m_pad, m, keff, dd, ed, (T*)c->S, c->ld_s);
     c->sampler_fallback = shifted;
   } else {
     Buf A(al, s), V(al, s), B(al, s);
@@ -671,7 +673,7 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
     (void)lam;
     size_t smb = sizeof(T) * nn;
     LOVE_TRY(allow_smem(k_root_from_eig<T>, smb));
-    LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<double>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);
+    LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<T>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);
     LOVE_LAUNCH_CHECK();
     LOVE_CUDA(cudaStreamSynchronize(s));
     c->sampler_fallback = 1;

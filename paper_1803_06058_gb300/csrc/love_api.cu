@@ -547,7 +547,8 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   if (rc == LOVE_OK && (flags & LOVE_WANT_SAMPLER)) {
     int ks = o->sampler_k > 0 ? o->sampler_k : o->k;
     ks = std::min<int64_t>(ks, g.m);
-    rc = sampler_build<T>(ski, c, rt_keep, ks, o->sampler_seed, 1e-12, s);
+    // breakdown tolerance of the sampler's Lanczos run: its vectors are stored in T
+    rc = sampler_build<T>(ski, c, rt_keep, ks, o->sampler_seed, sizeof(T) == 8 ? 1e-12 : 1e-8, s);
   }
   if (rt_keep) al.free(rt_keep, rtb, s);
   ev.record(4, s);

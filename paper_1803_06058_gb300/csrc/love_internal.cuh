@@ -415,7 +415,7 @@ love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, c
 // sampler Lanczos on M = K_UU - Rt Rt^T (FP64); Rt: m x k column-major (ldr)
 template <typename T>
 love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
-                            int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
+                            int k, int ks, uint64_t seed, double tau, T* Q, int64_t ldq, double* alpha_h,
                             double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s);
 // k_sample.cu: S = Q' L' (or the eigen fallback), stored in the cache
 template <typename T>
