@@ -41,6 +41,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "predictive variances/sec at 1M test pts + precompute ms; % HBM roofline"
+# the pre-compute's reorthogonalisation: both Gram-Schmidt passes per step, the
+# second folded into the first through Q^T Q and checked (a real second pass
+# where the check fails)
+REORTH = "lowsync"
 UNIT = "variances/s"
 
 
@@ -226,12 +230,13 @@ def run_gpu(args):
         ev[1].record()
         try:
             cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=sampler[0],
-                                         sampler_seed=seed, time_reorth=True)
+                                         sampler_seed=seed, time_reorth=True, reorth=REORTH)
         except love.LoveError as e:
             if e.status != 9 or not sampler[0]:
                 raise
             sampler[0] = False
-            cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=False, time_reorth=True)
+            cache = love.love_precompute(ski, k=wl.k, want_mean=True, want_sampler=False, time_reorth=True,
+                                         reorth=REORTH)
         ev[2].record()
         love.love_predict_mean_var(cache, xs_d, out_mean=mean_d, out_var=var_d)
         ev[3].record()
@@ -360,7 +365,7 @@ def run_gpu(args):
                "from_scratch_vars_per_s": world * t / (step_ms * 1e-3),
                "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "k": wl.k, "k_eff": k_eff,
                           "t": t, "s": wl.s if sampler[0] else 0, "t_sample": wl.t_sample, "cg_iters": cg_iters,
-                          "cache_dtype": "f32",
+                          "cache_dtype": "f32", "reorth": REORTH,
                           "l2": "flushed before every step and every predict timing (256 MB write)",
                           "parallelism": f"replicas x{world} (each rank: full step on its own copy)"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -140,7 +140,7 @@ typedef struct {
   int cg_max_iter;         /* <=0: 4000                                        */
   int sampler_k;           /* Lanczos steps for S; <=0: k                      */
   uint64_t sampler_seed;   /* SplitMix64 seed of the Rademacher probe          */
-  int reorth;              /* LOVE_REORTH_ALWAYS (0) or LOVE_REORTH_DETECT (1) */
+  int reorth;              /* LOVE_REORTH_ALWAYS (0), _DETECT (1) or _LOWSYNC (2) */
   double reorth_eta;       /* DETECT threshold on |Q_j^T y'| / |y'|; <=0: 2^-22 (F32) / 2^-51 (F64) */
   int cg_plain;            /* 1: the mean CG without preconditioner (Sec. 2.1); 0: on a 1-D grid
                               the grid-space CG is preconditioned by the spectral inverse of
@@ -153,9 +153,16 @@ typedef struct {
  * |Q_j^T y'| > eta |y'| with y' = y - Q_j Q_j^T y (measured in the same sweep
  * that applies the first pass), so a healthy step reads Q_j twice instead of
  * three times; the number of steps that skipped it is reported by
- * love_cache_info.  The sampler's Lanczos run always takes both passes. */
+ * love_cache_info.  LOWSYNC: the second pass folded into the first through
+ * the Gram matrix G = Q_j^T Q_j (kept from the measured dots of each new
+ * vector): c = c1 + (c1 - G c1) with c1 = Q_j^T y, so one update sweep
+ * y - Q_j c (which also measures Q_j^T y' for the next row of G) replaces the
+ * two; the DETECT test then decides whether a real second pass is still
+ * needed.  Two reads of Q_j per step instead of three.  The sampler's Lanczos
+ * run always takes both passes. */
 #define LOVE_REORTH_ALWAYS 0
 #define LOVE_REORTH_DETECT 1
+#define LOVE_REORTH_LOWSYNC 2
 
 /* love_precompute -- the LOVE pre-compute phase (Sec. 3.2, Algorithm 1):
  * k Lanczos steps with full reorthogonalisation (Sec. 5) on K^ from the probe

@@ -188,8 +188,9 @@ def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool =
                     breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
                     sampler_k: int = 0, sampler_seed: int = 0, reorth: str = "always", reorth_eta: float = 0.0,
                     cg_plain: bool = False, time_reorth: bool = False, stream=None) -> Cache:
-    """reorth: "always" (two Gram-Schmidt passes every step) or "detect" (the
-    second pass only where |Q_j^T y'| > reorth_eta |y'|).  cg_plain: mean CG
+    """reorth: "always" (two Gram-Schmidt passes every step), "detect" (the
+    second pass only where |Q_j^T y'| > reorth_eta |y'|) or "lowsync" (the second
+    pass folded into the first through Q^T Q, checked like "detect").  cg_plain: mean CG
     without the spectral preconditioner (1-D grids use it by default).
     time_reorth: record the sweeps' device time (info()["reorth_ms"])."""
     o = _opts(ski.dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,
@@ -203,7 +204,7 @@ def love_precompute(ski: Ski, k: int, cache_dtype: str = None, want_mean: bool =
     return Cache(h, ski.dtype, ski.dim)
 
 
-_REORTH = {"always": 0, "detect": 1}
+_REORTH = {"always": 0, "detect": 1, "lowsync": 2}
 
 
 def _opts(dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol, cg_tol,

@@ -663,6 +663,7 @@ struct TileArgs {
   DevStatus* status;
   int detect;         // skip the second pass when |Q_j^T y'| <= eta |y'|
   double eta2;        // eta^2
+  double* gram;       // low-synchronisation mode: Q^T Q (kcols x kcols, FP64), else nullptr
 };
 
 // 4 consecutive rows of one column in shared memory (one 16-byte access for
@@ -742,7 +743,35 @@ __device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename Ac
   // the norm sweep merges a single sum: the narrow form (lanes over CTAs)
   bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, &st->counter,
                                    MODE == MODE_UPDATE_NORM ? nullptr : scratch);
-  if (!last || tid != 0) return;
+  if (!last) return;
+  if (MODE == MODE_DOT && a.gram != nullptr) {
+    // low-synchronisation form: the second Gram-Schmidt pass folded into the
+    // first through the Gram matrix G = Q_j^T Q_j, c <- c + (c - G c) (the
+    // coefficients CGS2's second pass would find on y - Q_j c); the last CTA
+    // computes them (rows over threads), alpha_j keeps the first-pass c_j
+    double* cs = reinterpret_cast<double*>(scratch);
+    const double* G = a.gram;
+    for (int i = tid; i < ncols; i += blockDim.x) {
+      double v = 2.0 * st->coef[i];
+      for (int l = 0; l < ncols; ++l) v = fma(-G[(int64_t)i * a.kcols + l], st->coef[l], v);
+      cs[i] = v;
+    }
+    __syncthreads();
+    const double c1j = st->coef[j];
+    __syncthreads();
+    for (int i = tid; i < ncols; i += blockDim.x) st->coef[i] = cs[i];
+    __syncthreads();
+    if (tid != 0) return;
+    st->alpha[j] = c1j;
+    if (!isfinite(c1j)) {
+      dev_flag(a.status, LOVE_ERR_NAN);
+      st->done = 1;
+      st->k_eff = j;
+    }
+    st->maxabs = fmax(st->maxabs, fabs(c1j));
+    return;
+  }
+  if (tid != 0) return;
   if (MODE == MODE_DOT) {
     double al = st->coef[j];
     st->alpha[j] = al;
@@ -758,6 +787,19 @@ __device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename Ac
       for (int i = 0; i < ncols; ++i) c2 += st->coef2[i] * st->coef2[i];
       const double yn = st->coef2[ncols];
       st->skip = c2 <= a.eta2 * yn;   // false for NaN: the second pass reports it
+      if (a.gram != nullptr && j + 1 < a.kcols) {
+        // row and column j + 1 of G: the measured dots of q_{j+1} = y'/|y'| with
+        // Q_j (zero when the second pass runs and removes them)
+        double* G = a.gram;
+        const int64_t ld = a.kcols;
+        const double inv = st->skip && yn > 0.0 ? 1.0 / sqrt(yn) : 0.0;
+        for (int i = 0; i < ncols; ++i) {
+          const double g = st->coef2[i] * inv;
+          G[(int64_t)(j + 1) * ld + i] = g;
+          G[(int64_t)i * ld + (j + 1)] = g;
+        }
+        G[(int64_t)(j + 1) * ld + (j + 1)] = 1.0;
+      }
       if (st->skip) {
         st->n_skip += 1;
         st->norm2 = yn;
@@ -1645,7 +1687,7 @@ love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaSt
 
 template <typename T>
 love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int64_t ldq, double* alpha_h,
-                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s, float* reorth_ms) {
+                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s, float* reorth_ms, bool lowsync) {
   const GridHost& gh = ski->grid;
   const int dim = gh.dim;
   if (k < 1 || k > LOVE_MAX_K) return LOVE_ERR_ARG;
@@ -1686,6 +1728,16 @@ love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int6
   ta.status = ski->status;
   ta.detect = eta > 0.0;
   ta.eta2 = eta * eta;
+  DevBuf gb(ski->alloc, s);
+  if (lowsync) {
+    // G = Q^T Q, starting from |q_0|^2 = 1
+    if (!ta.detect || !gb.get(sizeof(double) * (size_t)k * k)) return LOVE_ERR_OOM;
+    LOVE_CUDA(cudaMemsetAsync(gb.p, 0, sizeof(double) * (size_t)k * k, s));
+    const double one = 1.0;
+    LOVE_CUDA(cudaMemcpyAsync(gb.p, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    LOVE_CUDA(cudaStreamSynchronize(s));
+    ta.gram = gb.as<double>();
+  }
   // optional CUDA events around each step's sweeps (reorth_ms)
   std::vector<cudaEvent_t> rev;
   struct EvFree {
@@ -2310,9 +2362,9 @@ love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, c
 template love_status ski_mvm_sorted<float>(love_ski*, const float*, float*, void*, cudaStream_t);
 template love_status ski_mvm_sorted<double>(love_ski*, const double*, double*, void*, cudaStream_t);
 template love_status lanczos_run<float>(love_ski*, int, double, double, float*, int64_t, double*, double*, int*,
-                                        int*, cudaStream_t, float*);
+                                        int*, cudaStream_t, float*, bool);
 template love_status lanczos_run<double>(love_ski*, int, double, double, double*, int64_t, double*, double*, int*,
-                                         int*, cudaStream_t, float*);
+                                         int*, cudaStream_t, float*, bool);
 template love_status scatter_multi<float>(love_ski*, const float*, int64_t, int, float*, int64_t, cudaStream_t);
 template love_status scatter_multi<double>(love_ski*, const double*, int64_t, int, double*, int64_t, cudaStream_t);
 template love_status cg_solve<float>(love_ski*, const float*, double*, double, int, int*, cudaStream_t);

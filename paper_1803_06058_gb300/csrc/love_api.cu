@@ -423,10 +423,12 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   const Allocator& al = ski->alloc;
   int k = std::min<int64_t>(o->k, std::min<int64_t>(ski->n, g.m));
   double tau = o->breakdown_tol > 0 ? o->breakdown_tol : (sizeof(T) == 8 ? 1e-12 : 1e-8);
-  if (o->reorth != LOVE_REORTH_ALWAYS && o->reorth != LOVE_REORTH_DETECT) return LOVE_ERR_ARG;
-  // DETECT: skip the second pass while |Q_j^T y'| <= eta |y'|, eta = 4 units
-  // of rounding of the Q storage type unless given
-  const double eta = o->reorth != LOVE_REORTH_DETECT
+  if (o->reorth != LOVE_REORTH_ALWAYS && o->reorth != LOVE_REORTH_DETECT && o->reorth != LOVE_REORTH_LOWSYNC)
+    return LOVE_ERR_ARG;
+  // DETECT / LOWSYNC: skip the second pass while |Q_j^T y'| <= eta |y'|, eta =
+  // 4 units of rounding of the Q storage type unless given
+  const bool lowsync = o->reorth == LOVE_REORTH_LOWSYNC;
+  const double eta = o->reorth == LOVE_REORTH_ALWAYS
                          ? 0.0
                          : (o->reorth_eta > 0 ? o->reorth_eta : (sizeof(T) == 8 ? 0x1p-51 : 0x1p-22));
   unsigned flags = o->flags;
@@ -487,7 +489,7 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   ev.record(0, s);
   float reorth_ms = 0.f;
   love_status rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, s,
-                                  (flags & LOVE_TIME_REORTH) ? &reorth_ms : nullptr);
+                                  (flags & LOVE_TIME_REORTH) ? &reorth_ms : nullptr, lowsync);
   ev.record(1, s);
   if (rc != LOVE_OK) {
     join_mean();

@@ -391,7 +391,8 @@ love_status kuu_apply(const GridHost& g, const FftPlan* plans, const T* v, T* ou
 struct LanczosWork;
 template <typename T>
 love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int64_t ldq, double* alpha_h,
-                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s, float* reorth_ms = nullptr);
+                        double* beta_h, int* k_eff, int* skipped, cudaStream_t s, float* reorth_ms = nullptr,
+                        bool lowsync = false);
 template <typename T>
 love_status ski_mvm_sorted(love_ski* ski, const T* v, T* out, void* work, cudaStream_t s);
 template <typename T>

@@ -1,6 +1,8 @@
 """GPU checks of the detection-triggered reorthogonalisation (reorth="detect"):
 the Lanczos run of Sec. 3.2 with the second Gram-Schmidt pass of Sec. 5 taken
-only where the first pass left |Q_j^T y'| > eta |y'|.
+only where the first pass left |Q_j^T y'| > eta |y'|; and of its
+low-synchronisation form (reorth="lowsync"), which folds the second pass into
+the first through the Gram matrix Q_j^T Q_j and checks the result the same way.
 
 * With eta below any measurable component the second pass runs at every step
   and the arithmetic is the same as reorth="always" (the first-pass vector is
@@ -50,13 +52,15 @@ def test_detect_with_tiny_eta_is_the_two_pass_run(love, dim, g, dtype):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("dim,g,n,k", [(1, 200, 20000, 40), (2, 32, 20000, 40), (3, 14, 20000, 40)])
-def test_detect_fp32_matches_oracle(love, dim, g, n, k):
+@pytest.mark.parametrize("mode", ["detect", "lowsync"])
+@pytest.mark.parametrize("dim,g,n,k", [(1, 200, 20000, 40), (2, 32, 20000, 40), (3, 14, 20000, 40),
+                                       (1, 2000, 200000, 60)])
+def test_detect_fp32_matches_oracle(love, dim, g, n, k, mode):
     from oracle import love as ol
     wl = small_workload(dim=dim, g=g, n=n, k=k, t=2000, ls=0.1 if dim == 1 else 0.2, noise=0.0025)
     ski_o, c_o = oracle_cache(wl)
     ski = gpu_ski(love, torch, wl)
-    cache = love.love_precompute(ski, k=k, reorth="detect")
+    cache = love.love_precompute(ski, k=k, reorth=mode)
     inf = cache.info()
     assert 0 <= inf["reorth_skipped"] <= inf["k_eff"]
     xs = np.asarray(wl.x_test(), np.float32).astype(np.float64)
@@ -68,12 +72,13 @@ def test_detect_fp32_matches_oracle(love, dim, g, n, k):
     assert np.max(np.abs(m - m_ref)) <= 1e-4 * np.std(ski_o.y)
 
 
-def test_detect_fp64_matches_oracle(love):
+@pytest.mark.parametrize("mode", ["detect", "lowsync"])
+def test_detect_fp64_matches_oracle(love, mode):
     from oracle import love as ol
     wl = workloads.C1
     _, c_o = oracle_cache(wl, cg_tol=1e-12)
     ski = gpu_ski(love, torch, wl)
-    cache = love.love_precompute(ski, k=wl.k, reorth="detect")
+    cache = love.love_precompute(ski, k=wl.k, reorth=mode)
     xs = wl.x_test()
     m, v = _var(love, cache, xs, "f64")
     m_ref, v_ref = ol.predict(c_o, xs)
@@ -81,8 +86,9 @@ def test_detect_fp64_matches_oracle(love):
     np.testing.assert_allclose(m, m_ref, atol=1e-9)
 
 
+@pytest.mark.parametrize("mode", ["detect", "lowsync"])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_detect_calls_the_second_pass_near_exhaustion(love, dtype):
+def test_detect_calls_the_second_pass_near_exhaustion(love, dtype, mode):
     """m = 30 grid points, k = 30 steps: beta_j falls by orders of magnitude
     as the Krylov space fills, the first pass cancels most of y and the
     detection must run the second pass at some steps; the result still meets
@@ -92,7 +98,7 @@ def test_detect_calls_the_second_pass_near_exhaustion(love, dtype):
     _, c_o = oracle_cache(wl)
     ski = gpu_ski(love, torch, wl)
     c2 = love.love_precompute(ski, k=30, reorth="always")
-    cd = love.love_precompute(ski, k=30, reorth="detect")
+    cd = love.love_precompute(ski, k=30, reorth=mode)
     inf = cd.info()
     assert inf["reorth_skipped"] < inf["k_eff"]
     xs = np.asarray(wl.x_test(), np.float64)
