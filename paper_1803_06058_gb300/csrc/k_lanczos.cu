@@ -35,6 +35,9 @@
 
 namespace love {
 
+constexpr int MERGE_GS = 20;     // partial rows per level-1 merge group and per batch of loads
+constexpr int MERGE_MAXG = 64;   // level-1 merge groups (a group grows past MERGE_GS beyond 1280 CTAs)
+
 // device-side Lanczos / CG scalars
 struct LanczosState {
   double alpha[LOVE_MAX_K + 1];
@@ -48,13 +51,13 @@ struct LanczosState {
   int done;
   int k_eff;
   int kmax;
-  unsigned counter;
+  unsigned counter[1 + MERGE_MAXG];    // merge counters of the Lanczos sweeps (all groups, then per group)
   int skip;        // detection mode: the second pass of this step is not needed
   int n_skip;      // second passes skipped so far
   // CG
   double rr, rr0, pap, cg_alpha, cg_beta, tol2;
   int cg_done, cg_iters;
-  unsigned counter2;
+  unsigned counter2[1 + MERGE_MAXG];   // merge counters of the CG reductions
 };
 
 namespace {
@@ -69,8 +72,17 @@ template <typename T> struct AccOf;
 template <> struct AccOf<float> { using type = DotAccF; };
 template <> struct AccOf<double> { using type = DotAccD; };
 
-__device__ __forceinline__ void acc_store(double2* p, const DotAccF& a) { *p = make_double2(a.s, a.c); }
-__device__ __forceinline__ void acc_store(double2* p, const DotAccD& a) { *p = make_double2(a.s, 0.0); }
+// A partial sum in a 16-byte slot of a partial table, stored exactly in its
+// first 8 bytes: the two floats of a double-float sum, or the double
+template <typename Acc> struct SlotOf;
+template <> struct SlotOf<DotAccF> { using type = float2; };
+template <> struct SlotOf<DotAccD> { using type = double; };
+__device__ __forceinline__ void acc_store(double2* p, const DotAccF& a) {
+  *reinterpret_cast<float2*>(p) = make_float2(a.s, a.c);
+}
+__device__ __forceinline__ void acc_store(double2* p, const DotAccD& a) { *reinterpret_cast<double*>(p) = a.s; }
+__device__ __forceinline__ void acc_merge(DotAccF& a, float2 v) { a.merge(v.x, v.y); }
+__device__ __forceinline__ void acc_merge(DotAccD& a, double v) { a.merge(v, 0.0); }
 
 // ---------------------------------------------------------------------------
 // per-point interpolation (4^D nonzeros)
@@ -551,9 +563,8 @@ __global__ void k_gather(GridDev g, const T* __restrict__ xs, int64_t n, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// block reduction of a DotAcc into partial[blockIdx.x]; then the last CTA
-// merges all partials into result[0..ncols) (fixed order).  Returns true in
-// the last CTA (after the merge), so the caller can finish scalar work.
+// block reduction of a DotAcc into partial[blockIdx.x]; then the merge of all
+// CTA partials into result[0..ncols) (fixed order).
 template <typename Acc>
 __device__ __forceinline__ void block_merge(Acc& a, Acc* sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -572,64 +583,68 @@ __device__ __forceinline__ void block_merge(Acc& a, Acc* sm) {
   a = sm[0];
 }
 
-// scratch: 8 x 32 double2 of shared memory for the wide form, or nullptr for
-// the narrow form (a given caller always takes the same form, so a sum's merge
-// order does not depend on how many sums are merged with it)
+// The per-CTA partial rows (sums in columns 0..ncols) are merged in two levels
+// so that no CTA walks the whole table through a chain of L2 round trips: the
+// CTAs form groups of `gs` consecutive indices; the last CTA of a group to
+// arrive merges the group's rows (in index order) into the group's first row;
+// the last group to arrive merges those rows (in group order) into result.  A
+// thread owns a column and keeps a batch of MERGE_GS row loads in flight, so a
+// sum's merge order never depends on how many sums are merged beside it.
+// counters: [0] the group count, [1 + g] group g's count; all are zero between
+// launches (each is reset by the CTA that saw it complete).
 template <typename Acc>
-__device__ bool last_cta_reduce(const double2* __restrict__ partial, int stride, int ncols, double* result,
-                                unsigned* counter, double2* scratch = nullptr) {
+__device__ __forceinline__ Acc merge_column(const double2* p, int64_t rstride, int nrows) {
+  using Slot = typename SlotOf<Acc>::type;
+  Acc a;
+  a.zero();
+  for (int r0 = 0; r0 < nrows; r0 += MERGE_GS) {
+    Slot v[MERGE_GS];
+#pragma unroll
+    for (int u = 0; u < MERGE_GS; ++u)
+      if (r0 + u < nrows) v[u] = __ldcg(reinterpret_cast<const Slot*>(p + (int64_t)(r0 + u) * rstride));
+#pragma unroll
+    for (int u = 0; u < MERGE_GS; ++u)
+      if (r0 + u < nrows) acc_merge(a, v[u]);
+  }
+  return a;
+}
+
+// Returns true in the one CTA that formed result (after the merge, with a copy
+// in sh_result when given), so the caller can finish scalar work there.
+template <typename Acc>
+__device__ bool last_cta_reduce(double2* partial, int stride, int ncols, double* result, unsigned* counters,
+                                double* sh_result = nullptr) {
   __shared__ int is_last;
+  const int G = gridDim.x;
+  const int gs = max(MERGE_GS, (G + MERGE_MAXG - 1) / MERGE_MAXG);
+  const int ng = (G + gs - 1) / gs;
+  const int grp = (int)blockIdx.x / gs;
+  const int r0 = grp * gs, nr = min(gs, G - r0);
+  const int tid = threadIdx.x, nthr = blockDim.x;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (tid == 0) is_last = (atomicAdd(&counters[1 + grp], 1u) == (unsigned)(nr - 1));
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int G = gridDim.x;
-  if (scratch == nullptr) {
-    // narrow: a warp per sum, lanes over the CTA partials
-    for (int i = w; i < ncols; i += nw) {
-      Acc a;
-      a.zero();
-#pragma unroll 8
-      for (int c = lane; c < G; c += 32) {
-        const double2 p = __ldcg(partial + (int64_t)c * stride + i);
-        a.merge(p.x, p.y);
-      }
-      warp_merge(a);
-      if (lane == 0) result[i] = a.value();
-    }
-  } else {
-    // wide: lanes over 32 consecutive sums (coalesced rows of the partial
-    // table), the first 8 warps over fixed eighths of the CTAs, then the eight
-    // warp sums in order
-    for (int i0 = 0; i0 < ncols; i0 += 32) {
-      const int i = i0 + lane;
-      Acc a;
-      a.zero();
-      if (w < 8 && i < ncols) {
-        const int cb = w * G / 8, ce = (w + 1) * G / 8;
-#pragma unroll 16
-        for (int c = cb; c < ce; ++c) {
-          const double2 p = __ldcg(partial + (int64_t)c * stride + i);
-          a.merge(p.x, p.y);
-        }
-      }
-      if (w < 8) scratch[w * 32 + lane] = make_double2((double)a.s, (double)a.c);
-      __syncthreads();
-      if (w == 0 && i < ncols) {
-        Acc t;
-        t.zero();
-#pragma unroll
-        for (int v = 0; v < 8; ++v) t.merge(scratch[v * 32 + lane].x, scratch[v * 32 + lane].y);
-        result[i] = t.value();
-      }
-      __syncthreads();
-    }
+  double2* rows = partial + (int64_t)r0 * stride;
+  for (int i = tid; i < ncols; i += nthr) acc_store(rows + i, merge_column<Acc>(rows + i, stride, nr));
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    counters[1 + grp] = 0u;
+    is_last = (atomicAdd(&counters[0], 1u) == (unsigned)(ng - 1));
   }
   __syncthreads();
-  if (threadIdx.x == 0) *counter = 0u;
+  if (!is_last) return false;
+  __threadfence();
+  for (int i = tid; i < ncols; i += nthr) {
+    const double v = merge_column<Acc>(partial + i, (int64_t)gs * stride, ng).value();
+    result[i] = v;
+    if (sh_result) sh_result[i] = v;
+  }
+  __syncthreads();
+  if (tid == 0) counters[0] = 0u;
   return true;
 }
 
@@ -740,28 +755,47 @@ __device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename Ac
   }
   double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
   const int nres = MODE == MODE_UPDATE_NORM ? 1 : ncols + (MODE == MODE_UPDATE_DOT && a.detect ? 1 : 0);
-  // the norm sweep merges a single sum: the narrow form (lanes over CTAs)
-  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, &st->counter,
-                                   MODE == MODE_UPDATE_NORM ? nullptr : scratch);
+  // scratch (shared memory, at least j + 1 + blockDim.x doubles): the merged
+  // sums, then the pieces of the low-synchronisation product
+  double* cm = reinterpret_cast<double*>(scratch);
+  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, st->counter,
+                                   MODE == MODE_UPDATE_NORM ? nullptr : cm);
   if (!last) return;
   if (MODE == MODE_DOT && a.gram != nullptr) {
     // low-synchronisation form: the second Gram-Schmidt pass folded into the
     // first through the Gram matrix G = Q_j^T Q_j, c <- c + (c - G c) (the
-    // coefficients CGS2's second pass would find on y - Q_j c); the last CTA
-    // computes them (rows over threads), alpha_j keeps the first-pass c_j
-    double* cs = reinterpret_cast<double*>(scratch);
+    // coefficients CGS2's second pass would find on y - Q_j c); alpha_j keeps
+    // the first-pass c_j.  G is stored symmetric, so row i of G is read as
+    // column i (coalesced across a warp); the threads split the l range of
+    // every row into `parts` pieces (16 loads in flight each), then add the
+    // pieces in a fixed order.
     const double* G = a.gram;
-    for (int i = tid; i < ncols; i += blockDim.x) {
-      double v = 2.0 * st->coef[i];
-      for (int l = 0; l < ncols; ++l) v = fma(-G[(int64_t)i * a.kcols + l], st->coef[l], v);
-      cs[i] = v;
+    double* pp = cm + ncols;   // [parts][ncols], parts * ncols <= blockDim.x
+    const int parts = max(1, (int)blockDim.x / ncols);
+    const int span = (ncols + parts - 1) / parts;
+    for (int t = tid; t < parts * ncols; t += blockDim.x) {
+      const int part = t / ncols, i = t - part * ncols;
+      const int lb = part * span, le = min(ncols, lb + span);
+      double v = 0.0;
+      for (int l0 = lb; l0 < le; l0 += 16) {
+        double gl[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          gl[u] = l0 + u < le ? __ldcg(G + (int64_t)(l0 + u) * a.kcols + i) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (l0 + u < le) v = fma(gl[u], cm[l0 + u], v);
+      }
+      pp[t] = v;
     }
     __syncthreads();
-    const double c1j = st->coef[j];
-    __syncthreads();
-    for (int i = tid; i < ncols; i += blockDim.x) st->coef[i] = cs[i];
-    __syncthreads();
+    for (int i = tid; i < ncols; i += blockDim.x) {
+      double v = 0.0;
+      for (int p = 0; p < parts; ++p) v += pp[p * ncols + i];
+      st->coef[i] = 2.0 * cm[i] - v;
+    }
     if (tid != 0) return;
+    const double c1j = cm[j];
     st->alpha[j] = c1j;
     if (!isfinite(c1j)) {
       dev_flag(a.status, LOVE_ERR_NAN);
@@ -771,9 +805,44 @@ __device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename Ac
     st->maxabs = fmax(st->maxabs, fabs(c1j));
     return;
   }
+  if (MODE == MODE_UPDATE_DOT && a.detect) {
+    // the detection test on the measured c' = Q_j^T y' (warp 0, fixed order)
+    __shared__ int skip_sh;
+    if (warp == 0) {
+      double c2 = 0.0;
+      for (int i = lane; i < ncols; i += 32) c2 = fma(cm[i], cm[i], c2);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+      if (lane == 0) skip_sh = c2 <= a.eta2 * cm[ncols];   // false for NaN: the second pass reports it
+    }
+    __syncthreads();
+    const bool skip = skip_sh != 0;
+    const double yn = cm[ncols];
+    if (a.gram != nullptr && j + 1 < a.kcols) {
+      // row and column j + 1 of G: the measured dots of q_{j+1} = y'/|y'| with
+      // Q_j (zero when the second pass runs and removes them)
+      double* G = a.gram;
+      const int64_t ld = a.kcols;
+      const double inv = skip && yn > 0.0 ? 1.0 / sqrt(yn) : 0.0;
+      for (int i = tid; i < ncols; i += blockDim.x) {
+        const double g = cm[i] * inv;
+        G[(int64_t)(j + 1) * ld + i] = g;
+        G[(int64_t)i * ld + (j + 1)] = g;
+      }
+      if (tid == 0) G[(int64_t)(j + 1) * ld + (j + 1)] = 1.0;
+    }
+    if (tid != 0) return;
+    st->skip = skip;
+    if (skip) {
+      st->n_skip += 1;
+      st->norm2 = yn;
+      finish_step(st, a.status, j);
+    }
+    return;
+  }
   if (tid != 0) return;
   if (MODE == MODE_DOT) {
-    double al = st->coef[j];
+    double al = cm[j];
     st->alpha[j] = al;
     if (!isfinite(al)) {
       dev_flag(a.status, LOVE_ERR_NAN);
@@ -781,32 +850,7 @@ __device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename Ac
       st->k_eff = j;
     }
     st->maxabs = fmax(st->maxabs, fabs(al));
-  } else if (MODE == MODE_UPDATE_DOT) {
-    if (a.detect) {
-      double c2 = 0.0;
-      for (int i = 0; i < ncols; ++i) c2 += st->coef2[i] * st->coef2[i];
-      const double yn = st->coef2[ncols];
-      st->skip = c2 <= a.eta2 * yn;   // false for NaN: the second pass reports it
-      if (a.gram != nullptr && j + 1 < a.kcols) {
-        // row and column j + 1 of G: the measured dots of q_{j+1} = y'/|y'| with
-        // Q_j (zero when the second pass runs and removes them)
-        double* G = a.gram;
-        const int64_t ld = a.kcols;
-        const double inv = st->skip && yn > 0.0 ? 1.0 / sqrt(yn) : 0.0;
-        for (int i = 0; i < ncols; ++i) {
-          const double g = st->coef2[i] * inv;
-          G[(int64_t)(j + 1) * ld + i] = g;
-          G[(int64_t)i * ld + (j + 1)] = g;
-        }
-        G[(int64_t)(j + 1) * ld + (j + 1)] = 1.0;
-      }
-      if (st->skip) {
-        st->n_skip += 1;
-        st->norm2 = yn;
-        finish_step(st, a.status, j);
-      }
-    }
-  } else {
+  } else if (MODE == MODE_UPDATE_NORM) {
     finish_step(st, a.status, j);
   }
 }
@@ -1127,7 +1171,7 @@ __global__ void k_probe(GridDev g, const T* __restrict__ xs, int64_t n, int64_t 
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<Acc>(partial, 1, 1, &st->norm2, &st->counter);
+  bool last = last_cta_reduce<Acc>(partial, 1, 1, &st->norm2, st->counter);
   if (last && threadIdx.x == 0) st->scal[0] = 1.0 / sqrt(st->norm2);
 }
 
@@ -1138,8 +1182,7 @@ __global__ void k_state_init(LanczosState* st, int kmax, double tau) {
   st->done = 0;
   st->k_eff = kmax;
   st->kmax = kmax;
-  st->counter = 0;
-  st->counter2 = 0;
+  for (int i = 0; i <= MERGE_MAXG; ++i) st->counter[i] = st->counter2[i] = 0u;
   st->cg_done = 0;
   st->cg_iters = 0;
   st->skip = 0;
@@ -1176,7 +1219,7 @@ __global__ void k_cg_gather_dot(GridDev g, const T* __restrict__ xs, int64_t n, 
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->pap, &st->counter2);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->pap, st->counter2);
   if (last && threadIdx.x == 0) st->cg_alpha = st->rr / st->pap;
 }
 // x += a p ; r -= a Ap ; rr' = r.r
@@ -1196,7 +1239,7 @@ __global__ void k_cg_update(int64_t n_pad, double* __restrict__ x, double* __res
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, st->counter2);
   if (last && threadIdx.x == 0) {
     double rrn = st->norm2;
     st->cg_beta = rrn / st->rr;
@@ -1225,7 +1268,7 @@ __global__ void k_cg_init(int64_t n_pad, const T* __restrict__ b, double* __rest
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, st->counter2);
   if (last && threadIdx.x == 0) {
     st->rr = st->norm2;
     st->rr0 = st->norm2;
@@ -1332,7 +1375,7 @@ __global__ void k_cgdf_gather_dot(GridDev g, const float* __restrict__ xs, int64
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->pap, &st->counter2);
+  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->pap, st->counter2);
   if (last && threadIdx.x == 0) st->cg_alpha = st->rr / st->pap;
 }
 // x += a p ; r -= a Ap ; rr' = r.r
@@ -1353,7 +1396,7 @@ __global__ void k_cgdf_update(int64_t n_pad, df* __restrict__ x, df* __restrict_
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->norm2, &st->counter2);
+  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->norm2, st->counter2);
   if (last && threadIdx.x == 0) {
     double rrn = st->norm2;
     st->cg_beta = rrn / st->rr;
@@ -1381,7 +1424,7 @@ __global__ void k_cgdf_init(int64_t n_pad, const float* __restrict__ b, df* __re
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->norm2, &st->counter2);
+  bool last = last_cta_reduce<DotAccF>(partial, 1, 1, &st->norm2, st->counter2);
   if (last && threadIdx.x == 0) {
     st->rr = st->norm2;
     st->rr0 = st->norm2;
@@ -2037,7 +2080,7 @@ __global__ void k_mcg_band(GridDev g, const double* __restrict__ G, const double
   }
   block_merge(api, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, api);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->pap, &st->counter2);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->pap, st->counter2);
   if (last && threadIdx.x == 0) {
     const double pi = st->pap;
     if (!isfinite(pi)) {
@@ -2070,7 +2113,7 @@ __global__ void k_mcg_update(int64_t m, double* __restrict__ w, double* __restri
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, st->counter2);
   if (last && threadIdx.x == 0) {
     const double rho = st->norm2;
     st->cg_beta = rho / st->rr;
@@ -2099,7 +2142,7 @@ __global__ void k_mcg_ynorm(int64_t n, const T* __restrict__ y, double* __restri
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, st->counter2);
   if (last && threadIdx.x == 0) {
     st->rr0 = st->norm2;
     st->tol2 = tol * tol * st->norm2 * noise;
@@ -2127,7 +2170,7 @@ __global__ void k_mcg_start(int64_t m, const double* __restrict__ b, const doubl
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter2);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, st->counter2);
   if (last && threadIdx.x == 0) {
     st->rr = st->norm2;
     if (!(st->norm2 > st->tol2)) st->cg_done = 1;
@@ -2620,7 +2663,7 @@ __global__ void k_gm_start(int64_t m, int64_t m_pad, const double* __restrict__ 
   }
   block_merge(a, red);
   if (threadIdx.x == 0) acc_store(partial + blockIdx.x, a);
-  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, &st->counter);
+  bool last = last_cta_reduce<DotAccD>(partial, 1, 1, &st->norm2, st->counter);
   if (last && threadIdx.x == 0) {
     const double b2 = st->norm2, b = sqrt(b2);
     gm->g[0] = b;
