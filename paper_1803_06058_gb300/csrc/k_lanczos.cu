@@ -26,6 +26,8 @@
 // fixed order (deterministic, no floating-point atomics).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda.h>
@@ -1044,7 +1046,7 @@ __global__ void __launch_bounds__(TILE_T) k_lanczos_small(const __grid_constant_
   __shared__ T hp[NWARP][SMALL_R];
   __shared__ T ys[SMALL_R];
   __shared__ T cf[LOVE_MAX_K + 8];
-  __shared__ double2 wsum[8 * 32];
+  __shared__ double2 wsum[8 * 32];   // epilogue scratch: 512 doubles >= (j + 1) + blockDim.x
   LanczosState* st = a.st;
   if (st->done || (MODE == MODE_UPDATE_NORM && a.detect && st->skip)) return;
   const int j = a.j;
@@ -1683,16 +1685,16 @@ love_status lanczos_gather_any(love_ski* ski, const T* u, T* qj, T* y, const Lan
 inline int box_cols(size_t elem) { return elem == 4 ? 8 : 4; }
 template <typename T>
 love_status make_qmap(T* Q, int64_t ldq, int kcols, int bc, CUtensorMap* out) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // resolved once (thread-safe static initialisation: the mean solve's host
+  // thread builds tensor maps beside the caller's)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000,
-                                                     cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !encode) {
-      encode = nullptr;
-      return e != cudaSuccess ? cuda_check(e) : LOVE_ERR_UNSUPPORTED;
-    }
-  }
+    const cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+    return e == cudaSuccess && q == cudaDriverEntryPointSuccess ? (PFN_cuTensorMapEncodeTiled_v12000)f : nullptr;
+  }();
+  if (!encode) return LOVE_ERR_UNSUPPORTED;
   cuuint64_t dims[2] = {(cuuint64_t)ldq, (cuuint64_t)kcols};
   cuuint64_t strides[1] = {(cuuint64_t)ldq * sizeof(T)};
   cuuint32_t box[2] = {(cuuint32_t)TILE_R, (cuuint32_t)bc};
@@ -1705,14 +1707,29 @@ love_status make_qmap(T* Q, int64_t ldq, int kcols, int bc, CUtensorMap* out) {
 
 }  // namespace
 
+int smem_limit(const void* kernel) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> limits;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = limits.find(kernel);
+  if (it != limits.end()) return it->second;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return -1;
+  const int l = std::max(optin - (int)fa.sharedSizeBytes, 48 * 1024);
+  limits.emplace(kernel, l);
+  return l;
+}
+
 int num_sms() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
+  static const int cached = [] {   // thread-safe static initialisation
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached <= 0) cached = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   return cached;
 }
 

@@ -472,25 +472,20 @@ inline love_status cuda_check(cudaError_t e) {
   return LOVE_ERR_CUDA;
 }
 
+// the most dynamic shared memory a kernel can take (the device's opt-in
+// maximum less the kernel's static shared memory), looked up once per kernel;
+// -1 when the attributes cannot be read
+int smem_limit(const void* kernel);
+
 // raise a kernel's dynamic shared-memory limit (above the 48 KB default)
 template <typename K>
 inline love_status allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return LOVE_OK;
-  // always raise the kernel's limit to the most it can take (the device's
-  // opt-in maximum less the kernel's static shared memory), not to `bytes`:
+  // always raise the kernel's limit to the most it can take, not to `bytes`:
   // concurrent host threads launching the same kernel with different sizes
   // then never lower the limit under one another
-  static int limit = 0;
-  if (limit == 0) {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
-    if (e != cudaSuccess) return cuda_check(e);
-    const int l = optin - (int)fa.sharedSizeBytes;
-    limit = l > 48 * 1024 ? l : 48 * 1024;
-  }
+  const int limit = smem_limit(reinterpret_cast<const void*>(kernel));
+  if (limit < 0) return LOVE_ERR_CUDA;
   if (bytes > (size_t)limit) return LOVE_ERR_UNSUPPORTED;
   return cuda_check(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
 }
