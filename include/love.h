@@ -54,7 +54,7 @@ typedef enum {
   LOVE_ERR_DOMAIN = 2,     /* a point whose 4-point stencil leaves the grid, or NaN */
   LOVE_ERR_NOT_PD = 3,     /* non-positive pivot in the tridiagonal Cholesky        */
   LOVE_ERR_NAN = 4,        /* NaN/Inf met in a reduction                            */
-  LOVE_ERR_OOM = 5,        /* allocation failed                                     */
+  LOVE_ERR_OOM = 5,        /* allocation failed (device or host memory, host thread) */
   LOVE_ERR_CUDA = 6,       /* a CUDA runtime error (see love_last_cuda_error)       */
   LOVE_ERR_TIMEOUT = 7,    /* a bounded device wait expired                         */
   LOVE_ERR_STATE = 8,      /* the handle lacks what the call needs                  */

@@ -280,7 +280,7 @@ int love_last_cuda_error(void) { return g_last_cuda_error; }
 uint64_t love_launch_count(void) { return g_launches.load(); }
 const char* love_version(void) { return "love-gb300 1.0 (sm_103a)"; }
 
-love_status ski_destroy(love_ski_t ski) {
+love_status ski_destroy(love_ski_t ski) try {
   if (!ski) return LOVE_ERR_ARG;
   cudaStream_t s = 0;
   const Allocator& al = ski->alloc;
@@ -300,9 +300,10 @@ love_status ski_destroy(love_ski_t ski) {
   delete ski;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 love_status ski_build(const love_ski_desc* desc, const void* x_train, const void* y_train, love_stream_t stream,
-                      love_ski_t* out) {
+                      love_ski_t* out) try {
   if (!desc || !x_train || !out) return LOVE_ERR_ARG;
   *out = nullptr;
   if (desc->n < 1 || desc->n > (int64_t(1) << 31) - 1024) return LOVE_ERR_ARG;
@@ -345,8 +346,9 @@ love_status ski_build(const love_ski_desc* desc, const void* x_train, const void
   *out = ski;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
-love_status ski_mvm(love_ski_t ski, const void* v, void* out, love_stream_t stream) {
+love_status ski_mvm(love_ski_t ski, const void* v, void* out, love_stream_t stream) try {
   if (!ski || !v || !out || v == out) return LOVE_ERR_ARG;
   cudaStream_t s = cs(stream);
   const Allocator& al = ski->alloc;
@@ -375,8 +377,9 @@ love_status ski_mvm(love_ski_t ski, const void* v, void* out, love_stream_t stre
   al.free(ys, vb, s);
   return rc;
 }
+LOVE_ENTRY_CATCH
 
-love_status ski_mvm_kuu(love_ski_t ski, const void* v, void* out, love_stream_t stream) {
+love_status ski_mvm_kuu(love_ski_t ski, const void* v, void* out, love_stream_t stream) try {
   if (!ski || !v || !out) return LOVE_ERR_ARG;
   cudaStream_t s = cs(stream);
   const GridHost& g = ski->grid;
@@ -391,14 +394,16 @@ love_status ski_mvm_kuu(love_ski_t ski, const void* v, void* out, love_stream_t 
   if (fw) ski->alloc.free(fw, fwb, s);
   return rc;
 }
+LOVE_ENTRY_CATCH
 
-love_status love_cache_destroy(love_cache_t c) {
+love_status love_cache_destroy(love_cache_t c) try {
   if (!c) return LOVE_ERR_ARG;
   destroy_cache_buffers(c, 0);
   cudaStreamSynchronize(0);
   delete c;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 }  // extern "C"
 
@@ -466,19 +471,29 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     int dev = 0;
     cudaGetDevice(&dev);
     const bool precond = o->cg_plain == 0;
-    mj.th = std::thread([ski, cg_tol, cg_maxit, am, s2, dev, precond, &mj] {
-      cudaSetDevice(dev);
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      cudaEventRecord(e0, s2);
-      mj.rc = mean_grid_cg<T>(ski, cg_tol, cg_maxit, am, &mj.iters, s2, precond);
-      cudaEventRecord(e1, s2);
-      cudaEventSynchronize(e1);
-      cudaEventElapsedTime(&mj.ms, e0, e1);
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-    });
+    try {
+      mj.th = std::thread([ski, cg_tol, cg_maxit, am, s2, dev, precond, &mj] {
+        cudaSetDevice(dev);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s2);
+        try {
+          mj.rc = mean_grid_cg<T>(ski, cg_tol, cg_maxit, am, &mj.iters, s2, precond);
+        } catch (...) {   // host memory ran out: an exception must not leave the thread
+          mj.rc = LOVE_ERR_OOM;
+        }
+        cudaEventRecord(e1, s2);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&mj.ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+      });
+    } catch (...) {   // no host thread to be had
+      al.free(Q, qb, s);
+      al.free(am, amb, s);
+      return LOVE_ERR_OOM;
+    }
   }
   auto join_mean = [&]() {
     if (mj.th.joinable()) mj.th.join();
@@ -579,7 +594,7 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
 extern "C" {
 
 love_status love_precompute(love_ski_t ski, const love_precompute_opts* opts, love_stream_t stream,
-                            love_cache_t* out, int* k_eff) {
+                            love_cache_t* out, int* k_eff) try {
   if (!ski || !opts || !out) return LOVE_ERR_ARG;
   *out = nullptr;
   if (opts->k < 1 || opts->k > LOVE_MAX_K) return LOVE_ERR_ARG;
@@ -591,15 +606,17 @@ love_status love_precompute(love_ski_t ski, const love_precompute_opts* opts, lo
   if (ski->dtype == LOVE_F64) return precompute_impl<double>(ski, opts, s, out, k_eff);
   return precompute_impl<float>(ski, opts, s, out, k_eff);
 }
+LOVE_ENTRY_CATCH
 
 love_status love_predict_mean_var(love_cache_t c, int64_t t, const void* x_test, void* mean, void* var,
-                                  love_stream_t stream) {
+                                  love_stream_t stream) try {
   if (!c || t < 0) return LOVE_ERR_ARG;
   if (t == 0) return LOVE_OK;
   if (!x_test || !var) return LOVE_ERR_ARG;
   if (mean && !(c->flags & LOVE_WANT_MEAN)) return LOVE_ERR_STATE;
   return predict_launch(c, t, x_test, mean, var, cs(stream));
 }
+LOVE_ENTRY_CATCH
 
 // device address of a page-locked host buffer, or nullptr (pageable memory)
 static void* host_mapped(const void* p) {
@@ -612,7 +629,7 @@ static void* host_mapped(const void* p) {
 }
 
 love_status love_predict_mean_var_host(love_cache_t c, int64_t t, const void* x_test, void* mean, void* var,
-                                       love_stream_t stream) {
+                                       love_stream_t stream) try {
   if (!c || t < 0) return LOVE_ERR_ARG;
   if (t == 0) return LOVE_OK;
   if (!x_test || !var) return LOVE_ERR_ARG;
@@ -650,26 +667,29 @@ love_status love_predict_mean_var_host(love_cache_t c, int64_t t, const void* x_
   if (bm) c->alloc.free(bm, ob, s);
   return rc;
 }
+LOVE_ENTRY_CATCH
 
 love_status love_predict_covariance(love_cache_t c, int64_t t1, const void* x1, int64_t t2, const void* x2,
-                                    void* cov, love_stream_t stream) {
+                                    void* cov, love_stream_t stream) try {
   if (!c || t1 < 0 || t2 < 0) return LOVE_ERR_ARG;
   if (c->grid.additive) return LOVE_ERR_UNSUPPORTED;
   if (t1 == 0 || t2 == 0) return LOVE_OK;
   if (!x1 || !x2 || !cov) return LOVE_ERR_ARG;
   return cov_launch(c, t1, x1, t2, x2, cov, cs(stream));
 }
+LOVE_ENTRY_CATCH
 
-love_status love_predict_var_root(love_cache_t c, int64_t t, const void* x_test, void* var, love_stream_t stream) {
+love_status love_predict_var_root(love_cache_t c, int64_t t, const void* x_test, void* var, love_stream_t stream) try {
   if (!c || t < 0) return LOVE_ERR_ARG;
   if (!c->S) return LOVE_ERR_STATE;
   if (t == 0) return LOVE_OK;
   if (!x_test || !var) return LOVE_ERR_ARG;
   return predict_root_launch(c, t, x_test, var, cs(stream));
 }
+LOVE_ENTRY_CATCH
 
 love_status love_sample(love_cache_t c, int64_t t, const void* x_test, int s_count, const void* z, uint64_t seed,
-                        void* out, love_stream_t stream) {
+                        void* out, love_stream_t stream) try {
   if (!c || t < 0 || s_count < 0) return LOVE_ERR_ARG;
   if (!c->S) return LOVE_ERR_STATE;
   if (t == 0 || s_count == 0) return LOVE_OK;
@@ -684,17 +704,19 @@ love_status love_sample(love_cache_t c, int64_t t, const void* x_test, int s_cou
   }
   return sample_launch_z_ws(c, t, x_test, s_count, z, seed, out, c->sws, cs(stream));
 }
+LOVE_ENTRY_CATCH
 
 love_status love_var_backward(love_cache_t c, int64_t t, const void* x_test, const void* grad_var, void* grad_x,
-                              double* grad_lengthscale, double* grad_noise, love_stream_t stream) {
+                              double* grad_lengthscale, double* grad_noise, love_stream_t stream) try {
   if (!c || t < 0) return LOVE_ERR_ARG;
   if (c->grid.additive) return LOVE_ERR_UNSUPPORTED;
   if (!(c->flags & LOVE_WANT_GRAD) || !c->KdP) return LOVE_ERR_STATE;
   if (t > 0 && (!x_test || !grad_var)) return LOVE_ERR_ARG;
   return backward_launch(c, t, x_test, grad_var, grad_x, grad_lengthscale, grad_noise, cs(stream));
 }
+LOVE_ENTRY_CATCH
 
-love_status love_cache_info(love_cache_t c, love_cache_info_t* info) {
+love_status love_cache_info(love_cache_t c, love_cache_info_t* info) try {
   if (!c || !info) return LOVE_ERR_ARG;
   std::memset(info, 0, sizeof(*info));
   info->dim = c->grid.dim;
@@ -713,10 +735,11 @@ love_status love_cache_info(love_cache_t c, love_cache_info_t* info) {
   info->reorth_ms = c->reorth_ms;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 love_status love_cache_import(const love_ski_desc* desc, int k, love_dtype cache_dtype, unsigned flags,
                               const double* Rt, const double* a, int ks, const double* S, const double* alpha,
-                              const double* beta, const double* P, love_stream_t stream, love_cache_t* out) {
+                              const double* beta, const double* P, love_stream_t stream, love_cache_t* out) try {
   if (!desc || !Rt || !out || k < 1 || k > LOVE_MAX_K || ks < 0 || ks > LOVE_MAX_K) return LOVE_ERR_ARG;
   if (desc->dtype != LOVE_F32 && desc->dtype != LOVE_F64) return LOVE_ERR_ARG;
   if (desc->dtype == LOVE_F64 && cache_dtype != LOVE_F64) return LOVE_ERR_ARG;
@@ -787,9 +810,10 @@ love_status love_cache_import(const love_ski_desc* desc, int k, love_dtype cache
   *out = c;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 love_status love_cache_export(love_cache_t c, double* Rt, double* a, double* S, double* P, double* alpha,
-                              double* beta, love_stream_t stream) {
+                              double* beta, love_stream_t stream) try {
   if (!c) return LOVE_ERR_ARG;
   cudaStream_t s = cs(stream);
   const int64_t m = c->grid.m;
@@ -835,8 +859,9 @@ love_status love_cache_export(love_cache_t c, double* Rt, double* a, double* S, 
   if (beta && k > 1) std::copy(c->beta, c->beta + k - 1, beta);
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
-love_status love_get_device_status(love_cache_t c, int reset, love_device_status_t* st, love_stream_t stream) {
+love_status love_get_device_status(love_cache_t c, int reset, love_device_status_t* st, love_stream_t stream) try {
   if (!c || !st) return LOVE_ERR_ARG;
   cudaStream_t s = cs(stream);
   DevStatus d{};
@@ -848,6 +873,7 @@ love_status love_get_device_status(love_cache_t c, int reset, love_device_status
   st->clamped = (int64_t)d.clamped;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 // ---- checkpoint ---------------------------------------------------------------
 static const char kMagic[8] = {'L', 'O', 'V', 'E', 'C', 'A', 'C', 'H'};
@@ -884,7 +910,7 @@ static love_status read_dev(FILE* f, void** dptr, size_t bytes, const Allocator&
   return cuda_check(cudaStreamSynchronize(s));
 }
 
-love_status love_cache_save(love_cache_t c, const char* path, love_stream_t stream) {
+love_status love_cache_save(love_cache_t c, const char* path, love_stream_t stream) try {
   if (!c || !path) return LOVE_ERR_ARG;
   cudaStream_t s = cs(stream);
   CacheHeader hd{};
@@ -932,9 +958,10 @@ love_status love_cache_save(love_cache_t c, const char* path, love_stream_t stre
   std::fclose(f);
   return rc;
 }
+LOVE_ENTRY_CATCH
 
 love_status love_cache_load(const char* path, const love_allocator* allocator, love_stream_t stream,
-                            love_cache_t* out) {
+                            love_cache_t* out) try {
   if (!path || !out) return LOVE_ERR_ARG;
   *out = nullptr;
   cudaStream_t s = cs(stream);
@@ -1019,5 +1046,6 @@ love_status love_cache_load(const char* path, const love_allocator* allocator, l
   *out = c;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 }  // extern "C"

@@ -220,7 +220,7 @@ void batch_free(love_batch* b, cudaStream_t s) {
 extern "C" {
 
 love_status love_precompute_batched(int B, const love_ski_t* skis, const love_precompute_opts* opts, int workers,
-                                    love_stream_t stream, love_cache_t* caches, int* k_eff) {
+                                    love_stream_t stream, love_cache_t* caches, int* k_eff) try {
   if (B < 0 || (B > 0 && (!skis || !opts || !caches))) return LOVE_ERR_ARG;
   for (int b = 0; b < B; ++b) caches[b] = nullptr;
   for (int b = 0; b < B; ++b)
@@ -248,7 +248,13 @@ love_status love_precompute_batched(int B, const love_ski_t* skis, const love_pr
     }
   };
   std::vector<std::thread> th;
-  for (int w = 1; w < nw; ++w) th.emplace_back(work, w);
+  for (int w = 1; w < nw; ++w) {
+    try {
+      th.emplace_back(work, w);
+    } catch (...) {   // no more host threads: the started workers take the rest
+      break;
+    }
+  }
   work(0);
   for (auto& t : th) t.join();
   cudaEventDestroy(fork);
@@ -269,9 +275,10 @@ love_status love_precompute_batched(int B, const love_ski_t* skis, const love_pr
     for (int b = 0; b < B; ++b) k_eff[b] = ke[b];
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 love_status love_batch_create(int B, const love_cache_t* caches, const int64_t* t_off, love_stream_t stream,
-                              love_batch_t* out) {
+                              love_batch_t* out) try {
   if (!out) return LOVE_ERR_ARG;
   *out = nullptr;
   if (B < 1 || !caches || !t_off || t_off[0] != 0) return LOVE_ERR_ARG;
@@ -323,14 +330,16 @@ love_status love_batch_create(int B, const love_cache_t* caches, const int64_t* 
   *out = bt;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
-love_status love_batch_destroy(love_batch_t b) {
+love_status love_batch_destroy(love_batch_t b) try {
   if (!b) return LOVE_ERR_ARG;
   batch_free(b, 0);
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
-love_status love_predict_batched(love_batch_t b, const void* x, void* mean, void* var, love_stream_t stream) {
+love_status love_predict_batched(love_batch_t b, const void* x, void* mean, void* var, love_stream_t stream) try {
   if (!b) return LOVE_ERR_ARG;
   if (b->t_off[b->B] == 0) return LOVE_OK;
   if (!x || !var) return LOVE_ERR_ARG;
@@ -339,9 +348,10 @@ love_status love_predict_batched(love_batch_t b, const void* x, void* mean, void
       if (!(c->flags & LOVE_WANT_MEAN)) return LOVE_ERR_STATE;
   return batch_predict(b, x, mean, var, b->lanes, b->ctas, (cudaStream_t)stream);
 }
+LOVE_ENTRY_CATCH
 
 love_status love_sample_batched(love_batch_t b, const void* x, int s_count, uint64_t seed, void* out,
-                                love_stream_t stream) {
+                                love_stream_t stream) try {
   if (!b || s_count < 0) return LOVE_ERR_ARG;
   if (s_count == 0 || b->t_off[b->B] == 0) return LOVE_OK;
   if (!x || !out) return LOVE_ERR_ARG;
@@ -351,9 +361,10 @@ love_status love_sample_batched(love_batch_t b, const void* x, int s_count, uint
   LOVE_TRY(ensure_ws(b, s_count, s));
   return batch_sample(b, x, s_count, seed, out, s);
 }
+LOVE_ENTRY_CATCH
 
 love_status love_batch_serve(love_batch_t b, const void* x, void* mean, void* var, int s_count, uint64_t seed,
-                             void* samples, int use_graph, love_stream_t stream) {
+                             void* samples, int use_graph, love_stream_t stream) try {
   if (!b || s_count < 0 || (s_count > 0 && !samples)) return LOVE_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (!use_graph) {
@@ -401,8 +412,9 @@ love_status love_batch_serve(love_batch_t b, const void* x, void* mean, void* va
   LOVE_CUDA(cudaEventRecord(b->gev_out, b->gstream));
   return cuda_check(cudaStreamWaitEvent(s, b->gev_out, 0));
 }
+LOVE_ENTRY_CATCH
 
-love_status love_batch_info(love_batch_t b, love_batch_info_t* info) {
+love_status love_batch_info(love_batch_t b, love_batch_info_t* info) try {
   if (!b || !info) return LOVE_ERR_ARG;
   std::memset(info, 0, sizeof(*info));
   info->lanes_per_point = b->lanes;
@@ -412,5 +424,6 @@ love_status love_batch_info(love_batch_t b, love_batch_info_t* info) {
   info->chunks = b->nchunks;
   return LOVE_OK;
 }
+LOVE_ENTRY_CATCH
 
 }  // extern "C"

@@ -494,6 +494,15 @@ int num_sms();
 
 }  // namespace love
 
+// The C-ABI entry points are function-try-blocks closed by LOVE_ENTRY_CATCH:
+// the library throws only when host resources run out (std::bad_alloc from a
+// container, std::system_error from starting a host thread), and no exception
+// may cross the C boundary, so any exception becomes LOVE_ERR_OOM
+#define LOVE_ENTRY_CATCH \
+  catch (...) {          \
+    return LOVE_ERR_OOM; \
+  }
+
 #define LOVE_TRY(...)                      \
   do {                                     \
     love_status _st = (__VA_ARGS__);       \

@@ -47,7 +47,7 @@ love_status scratch_address(void** out) {
 }  // namespace
 
 extern "C" LOVE_API love_status ski_mvm_kuu_noalloc(love_ski_t ski, const void* v, void* out,
-                                                    love_stream_t stream) {
+                                                    love_stream_t stream) try {
   if (!ski || !v || !out) return LOVE_ERR_ARG;
   const GridHost& g = ski->grid;
   const size_t need = love::fft_work_bytes(g, ski->fft, 1, true);
@@ -59,3 +59,4 @@ extern "C" LOVE_API love_status ski_mvm_kuu_noalloc(love_ski_t ski, const void* 
     return love::kuu_apply<double>(g, ski->fft, (const double*)v, (double*)out, 1, g.m, scratch, -1, s);
   return love::kuu_apply<float>(g, ski->fft, (const float*)v, (float*)out, 1, g.m, scratch, -1, s);
 }
+LOVE_ENTRY_CATCH
