@@ -117,3 +117,23 @@ def test_reorth_mode_is_validated(love):
     ski = gpu_ski(love, torch, wl)
     with pytest.raises(KeyError):
         love.love_precompute(ski, k=8, reorth="sometimes")
+
+
+@pytest.mark.parametrize("mode", ["always", "lowsync"])
+def test_precompute_is_bitwise_reproducible(love, mode):
+    """Every reduction of the pre-compute merges its per-CTA partials in an
+    order fixed by the CTA indices (groups of CTAs, then the groups), not by
+    the order in which the CTAs finish: two pre-computes of the same problem
+    give the same cache bit for bit.  1-D, n = 2e5: the n-space sweeps run a
+    full grid of CTAs (16 merge groups); the sampler and the mean solve run
+    their own reductions on the 2,000-point grid."""
+    wl = small_workload(dim=1, g=2000, n=200000, k=60, t=2000, ls=0.1, noise=0.0025)
+    ski = gpu_ski(love, torch, wl)
+    caches = [love.love_precompute(ski, k=60, reorth=mode, want_mean=True, want_sampler=True) for _ in range(2)]
+    e = [love.love_cache_export(c) for c in caches]
+    for key in ("alpha", "beta", "Rt", "a", "S"):
+        assert np.array_equal(e[0][key], e[1][key]), key
+    xs = torch.tensor(wl.x_test(), dtype=torch.float32, device="cuda")
+    r = [love.love_predict_mean_var(c, xs) for c in caches]
+    for a, b in zip(r[0], r[1]):
+        assert torch.equal(a, b)
