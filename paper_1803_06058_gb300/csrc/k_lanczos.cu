@@ -1855,15 +1855,15 @@ love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* o
       const GridDev ge = component_dev(ski->grid, e);
       int blocks = (int)std::min<int64_t>(((int64_t)ge.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
       LOVE_COUNT_LAUNCH();
-      k_scatter_multi<T, 1, 8><<<blocks, 256, 0, s>>>(ge, (const T*)ski->xs1[e], ski->cs1[e], Q, ldq, ncol,
+      k_scatter_multi<T, 1, 16><<<blocks, 256, 0, s>>>(ge, (const T*)ski->xs1[e], ski->cs1[e], Q, ldq, ncol,
                                                       out + ski->grid.off[e], ldo, ski->map1[e]);
     }
     return cuda_check(cudaGetLastError());
   }
   int blocks = (int)std::min<int64_t>((g.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
   switch (g.dim) {
-    case 1: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 1, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
-    case 2: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 2, 8><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
+    case 1: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 1, 16><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
+    case 2: LOVE_COUNT_LAUNCH(); k_scatter_multi<T, 2, 16><<<blocks, 256, 0, s>>>(g, (const T*)ski->xs, ski->cell_start, Q, ldq, ncol, out, ldo, nullptr); break;
     default:
       if (sizeof(T) == 4) {
         dim3 grid((unsigned)ceil_div(g.g[2], SC3_NB), (unsigned)ceil_div(g.g[1], SC3_NB), (unsigned)ceil_div(g.g[0], SC3_NB));

@@ -49,11 +49,18 @@ __global__ void k_chol_tri(const double* alpha, const double* beta, int k, doubl
 // T' + delta I for a T' that is not numerically positive definite: the
 // smallest eigenvalue of the tridiagonal T' by multisection on Sturm counts
 // (the number of negative pivots of the LDL^T factorisation of T' - x I is the
-// number of eigenvalues below x), then delta = max(0, -lambda_min) plus 16
-// units of rounding of |T'|, so that the Cholesky factorisation of the
-// shifted matrix succeeds; alpha_s = alpha + delta.  One CTA: each round the
-// 256 threads count at 256 interior points of the bracket and the bracket
-// shrinks to the cell holding lambda_min (7 rounds reach FP64 resolution).
+// number of eigenvalues below x), then delta = max(0, -lo) plus 16 units of
+// rounding of |T'|, lo the lower end of the final bracket of lambda_min (so
+// delta >= -lambda_min: the Cholesky factorisation of the shifted matrix
+// succeeds, and delta exceeds -lambda_min by at most the bracket's width);
+// alpha_s = alpha + delta.  One CTA: each round its threads count at as many
+// interior points of the bracket, and the bracket shrinks to the cell holding
+// lambda_min until its width is rel_res |T'| (FP64 resolution for an FP64
+// root; rel_res = 2^-30 for an FP32 root: the extra shift, at most 2^-30 |T'|,
+// is far below the FP32 rounding of S).  The counts are FP64 divisions, which
+// this part runs at a small fraction of its FP32 rate, so a round costs in
+// proportion to the warps per SM sub-partition: it is launched with four warps
+// (128 points, 7 bits of the bracket per round).
 __device__ int sturm_below(const double* alpha, const double* beta, int k, double x) {
   const double tiny = 1e-300;
   int neg = 0;
@@ -67,7 +74,7 @@ __device__ int sturm_below(const double* alpha, const double* beta, int k, doubl
   return neg;
 }
 
-__global__ void k_tri_shift(const double* alpha, const double* beta, int k, double* alpha_s) {
+__global__ void k_tri_shift(const double* alpha, const double* beta, int k, double* alpha_s, double rel_res) {
   __shared__ double br[2];
   __shared__ int first;
   const int t = threadIdx.x, nt = blockDim.x;
@@ -85,7 +92,7 @@ __global__ void k_tri_shift(const double* alpha, const double* beta, int k, doub
   const double nrm = fmax(fabs(br[0]), fabs(br[1]));
   for (int round = 0; round < 12; ++round) {
     const double a = br[0], b = br[1];
-    if (!(b - a > 2.0 * 2.2204460492503131e-16 * nrm)) break;
+    if (!(b - a > rel_res * nrm)) break;
     if (t == 0) first = nt;
     __syncthreads();
     const double x = a + (b - a) * (double)(t + 1) / (double)(nt + 1);
@@ -641,7 +648,8 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
     // T' not numerically PD (K_UU - Rt Rt^T has eigenvalues at the rounding
     // level): Cholesky of T' + delta I, delta = -lambda_min(T') + rounding
     double* as = ed + (ks + 1);
-    LOVE_COUNT_LAUNCH(); k_tri_shift<<<1, 256, 0, s>>>(ad, bd, keff, as);
+    const double rel_res = sizeof(T) == 8 ? 2.0 * 2.2204460492503131e-16 : 0x1p-30;
+    LOVE_COUNT_LAUNCH(); k_tri_shift<<<1, 128, 0, s>>>(ad, bd, keff, as, rel_res);
     LOVE_COUNT_LAUNCH(); k_chol_tri<<<1, 32, 0, s>>>(as, bd, keff, dd, ed, okb.as<int>());
     LOVE_LAUNCH_CHECK();
     LOVE_CUDA(cudaMemcpyAsync(&ok, okb.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
