@@ -102,7 +102,7 @@ def test_device_normals_match_philox_oracle(love, dtype):
 
 def test_fp32_pipeline_sample_covariance(love):
     """FP32 pipeline: samples' empirical covariance converges to W*^T S S^T W*, and the
-    root's diagonal matches the LOVE variance within the FP32 tolerance."""
+    root's diagonal matches the LOVE variance (Sec. 3.3, eq. pred_covar_ski_interp_form12) within the FP32 tolerance."""
     wl = small_workload(dim=1, g=60, n=3000, k=30, t=40, ls=0.1, noise=0.01)
     ski = gpu_ski(love, torch, wl)
     cache = love.love_precompute(ski, k=30, want_mean=True, want_sampler=True, sampler_k=40, sampler_seed=3)
