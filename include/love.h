@@ -58,7 +58,7 @@ typedef enum {
   LOVE_ERR_CUDA = 6,       /* a CUDA runtime error (see love_last_cuda_error)       */
   LOVE_ERR_TIMEOUT = 7,    /* a bounded device wait expired                         */
   LOVE_ERR_STATE = 8,      /* the handle lacks what the call needs                  */
-  LOVE_ERR_UNSUPPORTED = 9 /* configuration outside what this build implements      */
+  LOVE_ERR_UNSUPPORTED = 9 /* configuration outside what this library implements    */
 } love_status;
 
 typedef enum { LOVE_F32 = 0, LOVE_F64 = 1, LOVE_BF16 = 2 } love_dtype;

@@ -2,7 +2,7 @@
 
 Sec. 2.3: the m inducing points lie on a regular grid, so for a stationary
 kernel K_UU is Toeplitz (1-D) or a Kronecker product of Toeplitz factors (a
-product kernel over dimensions).  The kernel used throughout this build is the
+product kernel over dimensions).  The kernel used throughout is the
 RBF kernel k(x, x') = s_f * exp(-|x - x'|^2 / (2 l^2)); for d > 1 it is the
 product over dimensions with one lengthscale per dimension, so
 

@@ -2,7 +2,7 @@
 
 Sec. 2.3 of the paper expresses a point x through its 4 closest inducing points
 with cubic interpolation (Keys 1981); the paper does not state Keys' free
-parameter, and this build takes a = -0.5 (the value for which the
+parameter; a = -0.5 is taken here (the value for which the
 interpolation reproduces quadratics).
 
 Keys' kernel, with s = |distance| in grid units:

@@ -6,7 +6,7 @@ Lanczos (Sec. 2.2): from a probe b, q_1 = b/|b|; each step multiplies the
 newest basis vector by A and orthogonalises the result against the basis; the
 coefficients form the symmetric tridiagonal T_k, with A ~ Q_k T_k Q_k^T.
 
-Full reorthogonalisation (Sec. 5, "Numerical stability of Lanczos"): this build
+Full reorthogonalisation (Sec. 5, "Numerical stability of Lanczos"): the oracle
 always reorthogonalises (the paper's detection criterion is not stated) and
 uses classical Gram-Schmidt applied twice (CGS2) to the raw product A q_j:
 

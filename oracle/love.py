@@ -7,7 +7,7 @@ Pre-compute (Sec. 3.2, Algorithm 1):
   Q_k, T_k = lanczos(K^, b)               k steps, full reorthogonalisation
   T_k = L L^T                             tridiagonal Cholesky (O(k))
   R^T = K_UU W Q_k,  R' = T_k^{-1} R       so that  R^T R' ~ C  (eq. pred_covar_ski_cache)
-This build stores one symmetric factor  Rt = K_UU W Q_k L^{-T}  (m x k):
+The cache stores one symmetric factor  Rt = K_UU W Q_k L^{-T}  (m x k):
   Rt Rt^T = K_UU W Q_k T_k^{-1} Q_k^T W^T K_UU = R^T R',
 so the variance of eq. pred_covar_ski_fast (i = j) is  p(x*) - |Rt^T w*|^2.
 

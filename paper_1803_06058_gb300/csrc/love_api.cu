@@ -271,7 +271,7 @@ const char* love_status_string(love_status s) {
     case LOVE_ERR_CUDA: return "CUDA runtime error";
     case LOVE_ERR_TIMEOUT: return "bounded device wait expired";
     case LOVE_ERR_STATE: return "handle lacks what the call needs";
-    case LOVE_ERR_UNSUPPORTED: return "configuration not supported by this build";
+    case LOVE_ERR_UNSUPPORTED: return "configuration not supported by this library";
   }
   return "unknown status";
 }

@@ -4,7 +4,7 @@ This module is the only code shared by the FP64 oracle and the CUDA path's
 tests and benchmark.  It holds configuration values and seeded random draws
 only: no interpolation, kernel, Lanczos or variance arithmetic lives here.
 
-Five workloads (C1..C5) follow the configurations the build is measured on:
+Five workloads (C1..C5), each shaped like one of the paper's settings:
 
   C1  1-D, n = 1,000, grid of 100 points on [-0.05, 1.05], k = 50, FP64
   C2  1-D, n = 1,000,000, grid of 10,000 points, k = 100, FP32 (headline)
