@@ -386,8 +386,13 @@ love_status love_batch_serve(love_batch_t b, const void* x, void* mean, void* va
     LOVE_CUDA(cudaStreamSynchronize(s));
     if (b->t_off[b->B] == 0) return LOVE_OK;
     LOVE_CUDA(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeRelaxed));
-    love_status rc = batch_predict(b, x, mean, var, b->lanes, b->ctas, b->gstream);
-    if (rc == LOVE_OK && s_count) rc = batch_sample(b, x, s_count, seed, samples, b->gstream);
+    love_status rc = LOVE_OK;
+    try {   // whatever happens, the capture is ended below
+      rc = batch_predict(b, x, mean, var, b->lanes, b->ctas, b->gstream);
+      if (rc == LOVE_OK && s_count) rc = batch_sample(b, x, s_count, seed, samples, b->gstream);
+    } catch (...) {
+      rc = LOVE_ERR_OOM;
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->gstream, &graph);
     if (rc == LOVE_OK && e != cudaSuccess) rc = cuda_check(e);
