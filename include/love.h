@@ -290,7 +290,12 @@ LOVE_API love_status love_cache_export(love_cache_t cache, double* Rt, double* a
 /* love_cache_save / love_cache_load -- a versioned, self-describing binary file
  * holding the grid, hyperparameters, alpha, beta and the cached matrices
  * (checkpoint of the pre-compute, which the paper runs as part of training).
- * Save/load round-trips bit-exactly.  Both synchronise `stream`. */
+ * Save/load round-trips bit-exactly.  Both synchronise `stream`.  load
+ * returns LOVE_ERR_ARG, before allocating or copying anything, for a missing
+ * file or one whose header does not describe exactly the buffers the library
+ * writes for such a cache (grid, dtypes, k_eff and every buffer's size, the
+ * gradient tables all present or all absent) or whose length differs from the
+ * header's total; an allocation failure returns LOVE_ERR_OOM. */
 LOVE_API love_status love_cache_save(love_cache_t cache, const char* path, love_stream_t stream);
 LOVE_API love_status love_cache_load(const char* path, const love_allocator* allocator,
                             love_stream_t stream, love_cache_t* out);

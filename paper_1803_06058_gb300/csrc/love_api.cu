@@ -893,6 +893,52 @@ struct CacheHeader {
   int32_t additive, pad;     // version 2
 };
 
+// A cache file is accepted only if its header describes exactly the buffers
+// the library writes for such a cache (sizes from the grid, k_eff and the
+// dtypes; the gradient tables all present or all absent) and the file holds
+// exactly those bytes: any other file could make a kernel read past a buffer.
+static bool header_ok(const CacheHeader& hd, uint64_t file_bytes) {
+  if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != kVersion) return false;
+  if (hd.dim < 1 || hd.dim > LOVE_MAX_DIM || hd.k_eff < 1 || hd.k_eff > LOVE_MAX_K) return false;
+  if (hd.additive != 0 && hd.additive != 1) return false;
+  if (hd.dtype != LOVE_F32 && hd.dtype != LOVE_F64) return false;
+  if (hd.dtype == LOVE_F64 ? hd.cache_dtype != LOVE_F64
+                           : (hd.cache_dtype != LOVE_F32 && hd.cache_dtype != LOVE_BF16))
+    return false;
+  if (!(hd.sf > 0) || !(hd.noise > 0) || !std::isfinite(hd.sf) || !std::isfinite(hd.noise)) return false;
+  uint64_t m = hd.additive ? 0 : 1;
+  for (int e = 0; e < LOVE_MAX_DIM; ++e) {
+    if (e >= hd.dim) {
+      if (hd.g[e] != 1) return false;
+      continue;
+    }
+    if (hd.g[e] < 4 || hd.g[e] > (int64_t(1) << 30) || !std::isfinite(hd.lo[e]) || !(hd.h[e] > 0) ||
+        !std::isfinite(hd.h[e]) || !(hd.ls[e] > 0) || !std::isfinite(hd.ls[e]))
+      return false;
+    m = hd.additive ? m + (uint64_t)hd.g[e] : m * (uint64_t)hd.g[e];
+    if (m > (uint64_t(1) << 34)) return false;
+  }
+  const uint64_t k = (uint64_t)hd.k_eff;
+  const uint64_t cb = dtype_size((love_dtype)hd.cache_dtype), eb = dtype_size((love_dtype)hd.dtype);
+  if (hd.ld != round_up(hd.k_eff + 1, (int)(16 / cb)) || hd.bytes_rc != m * (uint64_t)hd.ld * cb) return false;
+  if (hd.bytes_s == 0 ? hd.ks != 0
+                      : (hd.ks < 1 || hd.ks > LOVE_MAX_K || hd.ld_s != round_up(hd.ks, (int)(16 / eb)) ||
+                         hd.bytes_s != m * (uint64_t)hd.ld_s * eb))
+    return false;
+  const bool grad = hd.bytes_p != 0;
+  if (grad) {
+    if (hd.ld_g != round_up(hd.k_eff, (int)(16 / eb)) || hd.bytes_p != m * k * eb ||
+        hd.bytes_kdp != (uint64_t)hd.dim * m * (uint64_t)hd.ld_g * eb || hd.bytes_b != (uint64_t)hd.dim * k * k * eb ||
+        hd.bytes_minv != k * k * eb)
+      return false;
+  } else if (hd.bytes_kdp != 0 || hd.bytes_b != 0 || hd.bytes_minv != 0) {
+    return false;
+  }
+  const uint64_t total = sizeof(CacheHeader) + 2 * sizeof(double) * k + hd.bytes_rc + hd.bytes_s + hd.bytes_p +
+                         hd.bytes_kdp + hd.bytes_b + hd.bytes_minv;
+  return total == file_bytes;
+}
+
 static love_status write_dev(FILE* f, const void* dptr, size_t bytes, cudaStream_t s) {
   if (!bytes) return LOVE_OK;
   std::vector<unsigned char> buf(bytes);
@@ -968,8 +1014,10 @@ love_status love_cache_load(const char* path, const love_allocator* allocator, l
   FILE* f = std::fopen(path, "rb");
   if (!f) return LOVE_ERR_ARG;
   CacheHeader hd{};
-  if (fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0 || hd.version != kVersion ||
-      hd.dim < 1 || hd.dim > 3 || hd.k_eff < 1 || hd.k_eff > LOVE_MAX_K) {
+  bool ok = fread(&hd, sizeof(hd), 1, f) == 1 && std::fseek(f, 0, SEEK_END) == 0;
+  const long fb = ok ? std::ftell(f) : -1;
+  ok = ok && fb >= 0 && header_ok(hd, (uint64_t)fb) && std::fseek(f, (long)sizeof(hd), SEEK_SET) == 0;
+  if (!ok) {
     std::fclose(f);
     return LOVE_ERR_ARG;
   }
@@ -978,73 +1026,80 @@ love_status love_cache_load(const char* path, const love_allocator* allocator, l
     std::fclose(f);
     return LOVE_ERR_OOM;
   }
-  GridHost& g = c->grid;
-  g.dim = hd.dim;
-  g.additive = hd.additive != 0;
-  g.m = 1;
-  for (int e = 0; e < 3; ++e) {
-    g.g[e] = hd.g[e];
-    g.lo[e] = hd.lo[e];
-    g.h[e] = hd.h[e];
-    g.ls[e] = hd.ls[e];
-    g.m *= g.g[e];
-  }
-  if (g.additive) {
-    g.m = 0;
-    for (int e = 0; e < g.dim; ++e) {
-      g.off[e] = g.m;
-      g.m += g.g[e];
+  try {   // a host allocation that throws below must not leak the file or the cache
+    GridHost& g = c->grid;
+    g.dim = hd.dim;
+    g.additive = hd.additive != 0;
+    g.m = 1;
+    for (int e = 0; e < 3; ++e) {
+      g.g[e] = hd.g[e];
+      g.lo[e] = hd.lo[e];
+      g.h[e] = hd.h[e];
+      g.ls[e] = hd.ls[e];
+      g.m *= g.g[e];
     }
-  }
-  int64_t st = 1;
-  for (int e = g.dim - 1; e >= 0; --e) {
-    g.stride[e] = g.additive ? 1 : st;
-    st *= g.g[e];
-  }
-  g.sf = hd.sf;
-  g.noise = hd.noise;
-  for (int e = 0; e < g.dim; ++e)
-    for (int q = 0; q < 4; ++q) {
-      double r = q * g.h[e], ls = g.ls[e];
-      double v = std::exp(-(r * r) / (2 * ls * ls));
-      g.cloc[e][q] = v;
-      g.cloc_dl[e][q] = v * r * r / (ls * ls * ls);
+    if (g.additive) {
+      g.m = 0;
+      for (int e = 0; e < g.dim; ++e) {
+        g.off[e] = g.m;
+        g.m += g.g[e];
+      }
     }
-  c->dtype = (love_dtype)hd.dtype;
-  c->cache_dtype = (love_dtype)hd.cache_dtype;
-  c->flags = hd.flags;
-  c->k_eff = hd.k_eff;
-  c->ld = hd.ld;
-  c->ks = hd.ks;
-  c->ld_s = hd.ld_s;
-  c->ld_g = hd.ld_g;
-  c->cg_iters = hd.cg_iters;
-  c->sampler_fallback = hd.sampler_fallback;
-  c->alloc = make_alloc(allocator);
-  c->alpha = new double[c->k_eff + 1]();
-  c->beta = new double[c->k_eff + 1]();
-  love_status rc = LOVE_OK;
-  if (fread(c->alpha, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
-  if (rc == LOVE_OK && fread(c->beta, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
-  if (rc == LOVE_OK) rc = read_dev(f, &c->Rc, hd.bytes_rc, c->alloc, s);
-  if (rc == LOVE_OK) rc = read_dev(f, &c->S, hd.bytes_s, c->alloc, s);
-  if (rc == LOVE_OK) rc = read_dev(f, &c->P, hd.bytes_p, c->alloc, s);
-  if (rc == LOVE_OK) rc = read_dev(f, &c->KdP, hd.bytes_kdp, c->alloc, s);
-  if (rc == LOVE_OK) rc = read_dev(f, &c->B, hd.bytes_b, c->alloc, s);
-  if (rc == LOVE_OK) rc = read_dev(f, &c->Minv, hd.bytes_minv, c->alloc, s);
-  std::fclose(f);
-  if (rc == LOVE_OK) {
-    c->status = (DevStatus*)c->alloc.alloc(sizeof(DevStatus), s);
-    if (!c->status) rc = LOVE_ERR_OOM;
-    else rc = cuda_check(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
-  }
-  if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
-  if (rc != LOVE_OK) {
+    int64_t st = 1;
+    for (int e = g.dim - 1; e >= 0; --e) {
+      g.stride[e] = g.additive ? 1 : st;
+      st *= g.g[e];
+    }
+    g.sf = hd.sf;
+    g.noise = hd.noise;
+    for (int e = 0; e < g.dim; ++e)
+      for (int q = 0; q < 4; ++q) {
+        double r = q * g.h[e], ls = g.ls[e];
+        double v = std::exp(-(r * r) / (2 * ls * ls));
+        g.cloc[e][q] = v;
+        g.cloc_dl[e][q] = v * r * r / (ls * ls * ls);
+      }
+    c->dtype = (love_dtype)hd.dtype;
+    c->cache_dtype = (love_dtype)hd.cache_dtype;
+    c->flags = hd.flags;
+    c->k_eff = hd.k_eff;
+    c->ld = hd.ld;
+    c->ks = hd.ks;
+    c->ld_s = hd.ld_s;
+    c->ld_g = hd.ld_g;
+    c->cg_iters = hd.cg_iters;
+    c->sampler_fallback = hd.sampler_fallback;
+    c->alloc = make_alloc(allocator);
+    c->alpha = new double[c->k_eff + 1]();
+    c->beta = new double[c->k_eff + 1]();
+    love_status rc = LOVE_OK;
+    if (fread(c->alpha, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
+    if (rc == LOVE_OK && fread(c->beta, sizeof(double), c->k_eff, f) != (size_t)c->k_eff) rc = LOVE_ERR_ARG;
+    if (rc == LOVE_OK) rc = read_dev(f, &c->Rc, hd.bytes_rc, c->alloc, s);
+    if (rc == LOVE_OK) rc = read_dev(f, &c->S, hd.bytes_s, c->alloc, s);
+    if (rc == LOVE_OK) rc = read_dev(f, &c->P, hd.bytes_p, c->alloc, s);
+    if (rc == LOVE_OK) rc = read_dev(f, &c->KdP, hd.bytes_kdp, c->alloc, s);
+    if (rc == LOVE_OK) rc = read_dev(f, &c->B, hd.bytes_b, c->alloc, s);
+    if (rc == LOVE_OK) rc = read_dev(f, &c->Minv, hd.bytes_minv, c->alloc, s);
+    std::fclose(f);
+    f = nullptr;
+    if (rc == LOVE_OK) {
+      c->status = (DevStatus*)c->alloc.alloc(sizeof(DevStatus), s);
+      if (!c->status) rc = LOVE_ERR_OOM;
+      else rc = cuda_check(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+    }
+    if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
+    if (rc != LOVE_OK) {
+      love_cache_destroy(c);
+      return rc;
+    }
+    *out = c;
+    return LOVE_OK;
+  } catch (...) {
+    if (f) std::fclose(f);
     love_cache_destroy(c);
-    return rc;
+    return LOVE_ERR_OOM;
   }
-  *out = c;
-  return LOVE_OK;
 }
 LOVE_ENTRY_CATCH
 

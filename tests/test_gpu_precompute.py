@@ -134,3 +134,29 @@ def test_cache_save_load_roundtrip(love, tmp_path):
     m1, v1 = love.love_predict_mean_var(cache, xs)
     m2, v2 = love.love_predict_mean_var(c2, xs)
     assert torch.equal(v1, v2) and torch.equal(m1, m2)
+
+
+def test_cache_load_refuses_a_corrupted_header(love, tmp_path):
+    """A saved cache whose leading dimension field is changed (offset 144 of the
+    224-byte header) no longer matches its buffer sizes: the load is refused
+    before anything reaches the device, and the intact file (mean, sampler root
+    and gradient tables) still loads."""
+    import struct
+    wl = small_workload(dim=1, g=40, n=2000, k=10, t=100)
+    ski = gpu_ski(love, torch, wl)
+    cache = love.love_precompute(ski, k=10, want_mean=True, want_sampler=True, want_grad=True)
+    path = tmp_path / "c.love"
+    love.love_cache_save(cache, str(path))
+    raw = bytearray(path.read_bytes())
+    assert raw[:8] == b"LOVECACH"
+    ld = struct.unpack_from("<i", raw, 144)[0]
+    assert ld == -(-(cache.info()["k_eff"] + 1) // 4) * 4
+    bad = tmp_path / "bad.love"
+    struct.pack_into("<i", raw, 144, ld + 4)
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(love.LoveError):
+        love.love_cache_load(str(bad))
+    c2 = love.love_cache_load(str(path))
+    a, b = love.love_cache_export(cache), love.love_cache_export(c2)
+    for key in ("Rt", "a", "S", "P", "alpha"):
+        np.testing.assert_array_equal(a[key], b[key])
