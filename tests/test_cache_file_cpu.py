@@ -110,3 +110,34 @@ def test_base_header_describes_its_payload():
     assert b["bytes_rc"] == m * b["ld"] * 4
     assert _payload_bytes(b) == 16 * b["k_eff"] + b["bytes_rc"]
     assert np.all(np.isfinite(b["h"]))
+
+
+def _consistent():
+    b = _base()
+
+    def v(**kw):
+        h = dict(b)
+        h.update(kw)
+        return h
+    return {
+        "mean only": b,
+        "sampler root and gradient tables": v(flags=7, ks=7, ld_s=8, bytes_s=40 * 8 * 4, ld_g=12,
+                                              bytes_p=40 * 10 * 4, bytes_kdp=40 * 12 * 4, bytes_b=10 * 10 * 4,
+                                              bytes_minv=10 * 10 * 4),
+        "FP64 additive 2-D": v(dim=2, g=[40, 30, 1], additive=1, h=[1 / 35, 1 / 25, 1.0], ls=[0.2, 0.2, 1.0],
+                               dtype=1, cache_dtype=1, ld=12, bytes_rc=70 * 12 * 8),
+        "BF16 cache": v(cache_dtype=2, ld=16, bytes_rc=40 * 16 * 2),
+    }
+
+
+@pytest.mark.parametrize("name", sorted(_consistent()))
+def test_consistent_cache_file_passes_the_checks(lib, tmp_path, name):
+    """A header that matches its payload gets past the checks: without a GPU
+    the load then fails at the first device allocation (LOVE_ERR_OOM or a CUDA
+    error), with one it loads; it is never refused as an argument error."""
+    p = tmp_path / "c.love"
+    _write(p, _consistent()[name])
+    rc, handle = _load(lib, p)
+    if handle:
+        lib.love_cache_destroy(C.c_void_p(handle))
+    assert rc != LOVE_ERR_ARG, name
