@@ -52,6 +52,66 @@ def test_root_variance_is_the_exact_variance_at_exhaustion():
     np.testing.assert_allclose(vr, v_exact, rtol=1e-6, atol=1e-9 * np.max(v_exact))
 
 
+def _positive_part(M, iters=100):
+    """M_+ = (M + M sign(M)) / 2, with sign(M) from the Newton iteration
+    X <- (X + X^{-1}) / 2 started at M (Higham, Functions of Matrices, Ch. 5):
+    no eigensolver, so it shares no step with the sampler's eigen fallback."""
+    X = M.copy()
+    for _ in range(iters):
+        Xn = 0.5 * (X + np.linalg.inv(X))
+        done = np.max(np.abs(Xn - X)) <= 1e-15 * np.max(np.abs(Xn))
+        X = Xn
+        if done:
+            break
+    return 0.5 * (M + M @ X)
+
+
+def test_sampler_eigen_fallback_gives_the_positive_part():
+    """Sec. 3.3 with T' indefinite: the oracle's fallback root S = Q' V diag(sqrt(max(lam, 0)))
+    satisfies S S^T = M_+ (the positive part of M = K_UU - Rt Rt^T) at Krylov exhaustion.
+    M is made clearly indefinite by one extra cache column along the eigenvector of
+    K_UU - Rt Rt^T's smallest eigenvalue; the grid's lengthscale is short (K_UU
+    well conditioned) so M_+ from the Newton sign iteration is accurate to rounding.
+    A clamp taken after the square root, |lam| in place of max(lam, 0), or V^T in
+    place of V each break the equality."""
+    import dataclasses
+    g = 24
+    ski, _ = _small(g=g, n=400, ls=0.6 / (g - 5), noise=0.05)
+    c = L.precompute(ski, k=400)
+    K = ski.grid.dense_kuu()
+    lam, V = np.linalg.eigh(K - c.Rt @ c.Rt.T)
+    shift = 3 * lam[:5].mean() + 0.3 * lam[-1]             # pushes one eigenvalue well below 0
+    c2 = dataclasses.replace(c)
+    c2.Rt = np.hstack([c.Rt, np.sqrt(shift) * V[:, :1]])
+    M = K - c2.Rt @ c2.Rt.T
+    assert np.linalg.eigvalsh(M)[0] < -0.1 * lam[-1]
+    S_, fb = L.sampler_precompute(c2, k=g, seed=5, tau=1e-14)
+    assert fb and S_.shape == (g, g)
+    Mp = _positive_part(M)
+    # exhaustion: S S^T = Q' T'_+ Q'^T with Q' orthonormal and complete; rounding of
+    # the Lanczos run and the eigensolve, ~g eps |M|
+    assert np.max(np.abs(S_ @ S_.T - Mp)) <= 1e-12 * np.max(np.abs(Mp))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_sampler_eigen_fallback_at_rounding_level_matches_exact_posterior(seed):
+    """Sec. 3.3 where T' is indefinite only by rounding (K_UU - Rt Rt^T has eigenvalues
+    near -1e-15 |K_UU|, as the root of a real workload does): at Krylov exhaustion
+    the fallback root's covariance W*^T S S^T W* equals the exact SKI posterior
+    covariance W*^T (K_UU - C) W* of the push-through solve (eq.
+    pred_covar_ski_interp_form12), to the same 1e-9 as the positive definite case."""
+    ski, xs = _small(g=30, n=3000, ls=0.3, noise=0.01, seed=seed)
+    c = L.precompute(ski, k=ski.grid.m, tau=1e-13)
+    S_, fb = L.sampler_precompute(c, k=ski.grid.m, seed=7, tau=1e-14)
+    assert fb, "this case is meant to take the eigen fallback"
+    C = E.pushthrough_C(ski)
+    Ws = ski.grid.W(xs).toarray()
+    target = Ws.T @ (ski.grid.dense_kuu() - C) @ Ws
+    got = Ws.T @ S_ @ S_.T @ Ws
+    assert np.all(np.isfinite(S_))
+    assert np.max(np.abs(got - target)) < 1e-9 * np.max(np.abs(np.diag(target)))
+
+
 def test_sample_covariance_converges_and_sample_is_deterministic():
     ski, xs = _small(g=16, n=200, noise=0.1)
     c = L.precompute(ski, k=200)
