@@ -231,6 +231,23 @@ LOVE_API love_status love_predict_var_root(love_cache_t cache, int64_t t, const 
 LOVE_API love_status love_sample(love_cache_t cache, int64_t t, const void* x_test, int s,
                         const void* z, uint64_t seed, void* out, love_stream_t stream);
 
+/* love_sampler_precompute -- the sampler pre-compute of Sec. 3.3 (eqs.
+ * lancapprox, sampling_pre_cholesky, pred_covar_ski_interp_form) on an
+ * existing cache: ks Lanczos steps (0 -> k_eff; at most 200 and m) with full
+ * reorthogonalisation on M = K_UU - Rt Rt^T from the SplitMix64 Rademacher probe
+ * of `seed`, T' = L' L'^T and the root S = Q' L' (m x ks'), exactly the
+ * sampler run that love_precompute makes with LOVE_WANT_SAMPLER, but on the Rt
+ * the cache holds -- one made by love_precompute, love_cache_import or
+ * love_cache_load -- with the cache's own grid and kernel (K_UU's plans are
+ * built for the call and released).  For a BF16 cache Rt is read as stored
+ * (BF16-rounded); love_precompute's sampler uses Rt before that rounding.  A
+ * root the cache held before is replaced; afterwards the cache has
+ * LOVE_WANT_SAMPLER, love_cache_info reports sampler_k, sampler_fallback and
+ * phase_ms[3].  Work space and the root come from the cache's allocator.
+ * Synchronises `stream`.  Errors: LOVE_ERR_ARG (NULL cache, ks < 0 or > 200),
+ * LOVE_ERR_NAN (no Lanczos step survived), LOVE_ERR_OOM. */
+LOVE_API love_status love_sampler_precompute(love_cache_t cache, int ks, uint64_t seed, love_stream_t stream);
+
 /* love_var_backward -- vector-Jacobian product of L = sum_i g_i var_i (not in
  * the paper; derived from eq. pred_covar_ski_cache with K^^{-1} ~ Q T^{-1} Q^T,
  * Q held fixed):

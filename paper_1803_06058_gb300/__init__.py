@@ -402,6 +402,15 @@ def love_sample(cache: Cache, x_test: torch.Tensor, s: int, z: Optional[torch.Te
     return out
 
 
+def love_sampler_precompute(cache: Cache, k: int = 0, seed: int = 0, stream=None) -> Cache:
+    """Sampler root S (Sec. 3.3) for an existing cache (pre-computed, imported or
+    loaded): k Lanczos steps on K_UU - Rt Rt^T (0 -> the cache's k_eff).
+    Replaces any root the cache held; returns the same cache."""
+    check("love_sampler_precompute", lib().love_sampler_precompute(cache.handle, int(k), int(seed),
+                                                                   _stream(stream)))
+    return cache
+
+
 def love_var_backward(cache: Cache, x_test: torch.Tensor, grad_var: torch.Tensor,
                       want_x: bool = True, want_hyper: bool = True, stream=None):
     dt = _TORCH[cache.dtype]

@@ -76,6 +76,7 @@ SIGNATURES = {
     "love_sample": (C.c_int, [VP, C.c_int64, VP, C.c_int, VP, C.c_uint64, VP, VP]),
     "love_predict_var_root": (C.c_int, [VP, C.c_int64, VP, VP, VP]),
     "love_predict_covariance": (C.c_int, [VP, C.c_int64, VP, C.c_int64, VP, VP, VP]),
+    "love_sampler_precompute": (C.c_int, [VP, C.c_int, C.c_uint64, VP]),
     "love_var_backward": (C.c_int, [VP, C.c_int64, VP, VP, VP, DP, DP, VP]),
     "love_cache_info": (C.c_int, [VP, C.POINTER(love_cache_info_t)]),
     "love_cache_import": (C.c_int, [C.POINTER(love_ski_desc), C.c_int, C.c_int, C.c_uint, DP, DP,

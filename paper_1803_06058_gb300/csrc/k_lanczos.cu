@@ -2501,13 +2501,6 @@ __global__ void k_normalize_col(QT* __restrict__ q, int64_t n_pad, const double*
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x)
     q[i] *= sc;
 }
-// q (stored Lanczos vector) as FP64 for the operator product
-template <typename QT>
-__global__ void k_to_double(const QT* __restrict__ q, int64_t m, double* __restrict__ qd, const LanczosState* st) {
-  if (st->done) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-    qd[i] = (double)q[i];
-}
 // Partial products of the sampler operator's low-rank term (R = Rt, m x k,
 // column-major): tp[c * RS + rs] = sum over rows of slice rs of R[r, c] q[r],
 // a block per (column, slice of GEMV_SLICE rows), each thread 4 rows.
@@ -2565,62 +2558,54 @@ __global__ void k_gemv_n_sub(const T* __restrict__ R, int64_t ldr, int64_t m, in
 
 }  // namespace
 
-// The Lanczos vectors Q' are stored in T (FP32 for an FP32 ski): the operator
-// product M q is formed in FP64 (K_UU q and Rt (Rt^T q) cancel to ~1e-7 of
-// their size) and rounded once to T, and the reorthogonalisation sweeps run on
-// T with double-float (FP32) or FP64 sums -- on this part FP64 arithmetic runs
-// at ~1/64 of the FP32 rate, and FP32 storage keeps Q' orthonormal to the
-// accuracy of an FP32 root.
+// The Lanczos vectors Q' are FP64 whatever the data dtype T of Rt: the run is
+// m-sized, and M q (K_UU q and Rt (Rt^T q) cancel to ~1e-7 of their size on the
+// 1-D n = 1e6 workload) is formed and kept in FP64, so the root is that of the
+// operator the cache defines to FP64 accuracy before it is rounded to T.
 template <typename T>
 love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
-                            int k, int ks, uint64_t seed, double tau, T* Q, int64_t ldq, double* alpha_h,
+                            int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
                             double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s) {
   const int64_t m = gh.m, m_pad = ldq;
   if (ks < 1 || ks > LOVE_MAX_K || m_pad % TILE_R) return LOVE_ERR_ARG;
-  const int bc = box_cols(sizeof(T));
+  const int bc = box_cols(sizeof(double));
   const int max_grid = std::max(TILE_CTAS_PER_SM * num_sms(), 1024);
-  constexpr bool conv = sizeof(T) != sizeof(double);
-  DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s), qdb(al, s);
+  DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s);
   size_t fwb = fft_work_bytes(gh, fft, 1, true);
   if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)max_grid * (ks + 1)) ||
-      !kq.get(sizeof(double) * m) || !y.get(sizeof(T) * m_pad) ||
+      !kq.get(sizeof(double) * m) || !y.get(sizeof(double) * m_pad) ||
       !tv.get(sizeof(double) * (size_t)(k + 1) * (size_t)ceil_div(m, GEMV_SLICE)) ||
-      !fw.get(std::max<size_t>(fwb, 16)) || (conv && !qdb.get(sizeof(double) * m)))
+      !fw.get(std::max<size_t>(fwb, 16)))
     return LOVE_ERR_OOM;
   LanczosState* st = stb.as<LanczosState>();
   LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, ks, tau);
-  LOVE_COUNT_LAUNCH(); k_rademacher<T><<<ceil_div(m_pad, 256), 256, 0, s>>>(m, m_pad, seed, Q, st);
+  LOVE_COUNT_LAUNCH(); k_rademacher<double><<<ceil_div(m_pad, 256), 256, 0, s>>>(m, m_pad, seed, Q, st);
   LOVE_LAUNCH_CHECK();
-  TileArgs<T> ta{};
+  TileArgs<double> ta{};
   ta.n_pad = m_pad;
   ta.kcols = ks;
   ta.bc = bc;
   ta.Q = Q;
   ta.ldq = ldq;
-  ta.y = y.as<T>();
+  ta.y = y.as<double>();
   ta.partial = part.as<double2>();
   ta.st = st;
   ta.status = status;
   const int nb = std::min(4 * num_sms(), ceil_div(m_pad, 256));
   const int RS = ceil_div(m, GEMV_SLICE);
   const size_t nsub_smem = sizeof(double) * ((size_t)k + 8 * 32);
-  LOVE_TRY(allow_smem(k_gemv_n_sub<T, T>, nsub_smem));
+  LOVE_TRY(allow_smem(k_gemv_n_sub<T, double>, nsub_smem));
   for (int j = 0; j < ks; ++j) {
-    T* qj = Q + (int64_t)j * ldq;
-    LOVE_COUNT_LAUNCH(); k_normalize_col<T><<<nb, 256, 0, s>>>(qj, m_pad, st->scal + j, st);
-    const double* qd = reinterpret_cast<const double*>(qj);
-    if (conv) {
-      LOVE_COUNT_LAUNCH(); k_to_double<T><<<nb, 256, 0, s>>>(qj, m, qdb.as<double>(), st);
-      qd = qdb.as<double>();
-    }
-    LOVE_TRY(kuu_apply<double>(gh, fft, qd, kq.as<double>(), 1, m, fw.p, -1, s));
-    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<dim3(k, RS), 256, 0, s>>>(Rt, ldr, m, qd, tv.as<double>(), st);
-    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T, T><<<ceil_div(m_pad, 32), 256, nsub_smem, s>>>(Rt, ldr, m, m_pad, k, RS, tv.as<double>(), kq.as<double>(), y.as<T>(), st);
+    double* qj = Q + (int64_t)j * ldq;
+    LOVE_COUNT_LAUNCH(); k_normalize_col<double><<<nb, 256, 0, s>>>(qj, m_pad, st->scal + j, st);
+    LOVE_TRY(kuu_apply<double>(gh, fft, qj, kq.as<double>(), 1, m, fw.p, -1, s));
+    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<dim3(k, RS), 256, 0, s>>>(Rt, ldr, m, qj, tv.as<double>(), st);
+    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T, double><<<ceil_div(m_pad, 32), 256, nsub_smem, s>>>(Rt, ldr, m, m_pad, k, RS, tv.as<double>(), kq.as<double>(), y.as<double>(), st);
     LOVE_LAUNCH_CHECK();
     ta.j = j;
-    LOVE_TRY(tile_run<T, MODE_DOT>(ta, s));
-    LOVE_TRY(tile_run<T, MODE_UPDATE_DOT>(ta, s));
-    LOVE_TRY(tile_run<T, MODE_UPDATE_NORM>(ta, s));
+    LOVE_TRY(tile_run<double, MODE_DOT>(ta, s));
+    LOVE_TRY(tile_run<double, MODE_UPDATE_DOT>(ta, s));
+    LOVE_TRY(tile_run<double, MODE_UPDATE_NORM>(ta, s));
   }
   int keff = 0;
   LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -2632,7 +2617,7 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
 }
 
 template love_status sampler_lanczos<float>(const GridHost&, const FftPlan*, const Allocator&, const float*, int64_t,
-                                            int, int, uint64_t, double, float*, int64_t, double*, double*, int*,
+                                            int, int, uint64_t, double, double*, int64_t, double*, double*, int*,
                                             DevStatus*, cudaStream_t);
 template love_status sampler_lanczos<double>(const GridHost&, const FftPlan*, const Allocator&, const double*,
                                              int64_t, int, int, uint64_t, double, double*, int64_t, double*, double*,

@@ -2,13 +2,16 @@
 //
 // Pre-compute (eqs. lancapprox, sampling_pre_cholesky, pred_covar_ski_interp_form):
 // k' Lanczos steps on M = K_UU - R^T R' (k_lanczos.cu: sampler_lanczos) give
-// Q', T'; with T' = L' L'^T the root is S = Q' L' (m x k').  When T' is not
-// positive definite (M is a difference of two nearly equal PSD matrices, so
-// rounding can push small eigenvalues below zero) the root is the Cholesky
-// factor of T' + delta I, delta = -lambda_min(T') plus rounding (Sturm-count
-// multisection); should that fail too, it is taken from the eigendecomposition
-// T' = V diag(lam) V^T: S = Q' V diag(sqrt(max(lam, 0))), with the eigenpairs
-// from cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5).
+// Q', T' (FP64 vectors); with T' = L' L'^T the root is S = Q' L' (m x k'),
+// rounded once to the data dtype.  When T' is not positive definite (M is a
+// difference of two nearly equal PSD matrices, so rounding can push small
+// eigenvalues below zero) the root is that of T''s positive part, from the
+// eigendecomposition T' = V diag(lam) V^T: S = Q' V diag(sqrt(max(lam, 0))),
+// with the eigenpairs from cyclic Jacobi rotations (Golub & Van Loan, Sec. 8.5).
+// For an FP64 root, whose T' is indefinite only at the rounding level, the
+// Cholesky factor of T' + delta I (delta = -lambda_min(T') plus rounding, from
+// Sturm-count multisection) is taken first: it differs from the positive part by
+// that rounding; the eigen route remains its last resort.
 //
 // Test phase (eq. sample): F = mu 1^T + (W*^T S Z)^T, F sample-major (s x t):
 //   gather   G = W*^T S (t x k') and mu = W*^T a     (4^d rows of S per point)
@@ -109,9 +112,10 @@ __global__ void k_tri_shift(const double* alpha, const double* beta, int k, doub
   for (int j = t; j < k; j += nt) alpha_s[j] = alpha[j] + delta;
 }
 
-// S[r, c] = d_c Q'[r, c] + e_c Q'[r, c+1]   (S = Q' L', L' lower bidiagonal), row-major ld_s
+// S[r, c] = d_c Q'[r, c] + e_c Q'[r, c+1]   (S = Q' L', L' lower bidiagonal), row-major ld_s;
+// Q' in FP64, S rounded once to T
 template <typename T>
-__global__ void k_root_from_chol(const T* __restrict__ Q, int64_t ldq, int64_t m, int k, const double* d,
+__global__ void k_root_from_chol(const double* __restrict__ Q, int64_t ldq, int64_t m, int k, const double* d,
                                  const double* e, T* __restrict__ S, int ld_s) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * ld_s) return;
@@ -142,11 +146,14 @@ __global__ void k_tri_dense(const double* alpha, const double* beta, int n, doub
 // round-robin ordering, so each step applies n/2 rotations on disjoint index
 // pairs at once).  Each rotation (c, s at (p, q)) uses tan(phi) = t, the smaller
 // root of t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq), which
-// annihilates a_pq: A <- J^T A J, V <- V J.  Sweeps stop when the off-diagonal
-// mass is below 1e-13 of the total.  FP32 is enough here: eigenvalues below
-// ~1e-7 of the largest are clamped to zero anyway, and FP64 on this part runs
-// at a small fraction of FP32.  Writes lam (n) and V (n x n, eigenvectors in
-// columns) as doubles.  Shared memory: 2 np^2 + 2 np floats, np = n rounded up to even.
+// annihilates a_pq: A <- J^T A J, V <- V J.  The off-diagonal mass falls
+// quadratically once it is small, so the sweep after the one that starts with
+// off <= 1e-11 tot (squared Frobenius norms; the FP32 rounding floor is ~n^2
+// 2^-48 tot, ~4e-13 for n = 100) is the last.  FP32 is enough here: the root
+// it serves is stored in FP32 (an FP64 root whose T' is not PD takes the
+// shifted Cholesky first), and FP64 on this part runs at a small fraction of
+// FP32.  Writes lam (n) and V (n x n, eigenvectors in columns) as doubles.
+// Shared memory: 2 np^2 + 2 np floats, np = n rounded up to even.
 __global__ void k_jacobi_par(const double* __restrict__ Ain, int n, int max_sweeps, double* __restrict__ lam,
                              double* __restrict__ Vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -158,6 +165,7 @@ __global__ void k_jacobi_par(const double* __restrict__ Ain, int n, int max_swee
   __shared__ float red[2][32];
   __shared__ int stop;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) stop = 0;
   for (int i = tid; i < np * np; i += nt) {
     int r = i / np, c = i % np;
     A[i] = (r < n && c < n) ? (float)Ain[(int64_t)r * n + c] : 0.f;
@@ -187,10 +195,11 @@ __global__ void k_jacobi_par(const double* __restrict__ Ain, int n, int max_swee
         a += red[0][w];
         b += red[1][w];
       }
-      stop = (a <= 1e-13f * b) ? 1 : 0;
+      // 2: converged; 1: this sweep is the last
+      stop = (a <= 4e-13f * b || stop == 1) ? 2 : (a <= 1e-11f * b ? 1 : 0);
     }
     __syncthreads();
-    if (stop) break;
+    if (stop == 2) break;
     for (int step = 0; step < np - 1; ++step) {
       // round robin: position 0 holds index 0, positions 1..np-1 rotate by `step`
       for (int i = tid; i < half; i += nt) {
@@ -250,9 +259,9 @@ __global__ void k_scale_eig(const double* lam, const double* V, int n, double* B
   B[idx] = V[idx] * sqrt(l > 0.0 ? l : 0.0);
 }
 
-// S[r, c] = sum_j Q'[r, j] B[j, c]  (arithmetic in T; S row-major ld_s)
+// S[r, c] = sum_j Q'[r, j] B[j, c]  (Q' in FP64, B held in T: arithmetic in T; S row-major ld_s)
 template <typename T>
-__global__ void k_root_from_eig(const T* __restrict__ Q, int64_t ldq, int64_t m, int k,
+__global__ void k_root_from_eig(const double* __restrict__ Q, int64_t ldq, int64_t m, int k,
                                 const double* __restrict__ B, T* __restrict__ S, int ld_s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Bs = reinterpret_cast<T*>(smem_raw);  // k x k
@@ -618,18 +627,16 @@ struct Buf {
 }  // namespace
 
 template <typename T>
-love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uint64_t seed, double tau,
-                          cudaStream_t s) {
-  const GridHost& g = ski->grid;
-  const Allocator& al = ski->alloc;
+love_status sampler_build(const GridHost& g, const FftPlan* fft, const Allocator& al, love_cache* c, const T* Rt,
+                          int ks, uint64_t seed, double tau, cudaStream_t s) {
   const int64_t m = g.m;
   const int64_t m_pad = (m + 255) / 256 * 256;
   Buf Qb(al, s), ab(al, s), okb(al, s);
-  if (!Qb.get(sizeof(T) * m_pad * ks) || !ab.get(sizeof(double) * 5 * (ks + 1)) || !okb.get(sizeof(int)))
+  if (!Qb.get(sizeof(double) * m_pad * ks) || !ab.get(sizeof(double) * 5 * (ks + 1)) || !okb.get(sizeof(int)))
     return LOVE_ERR_OOM;
   std::vector<double> alpha(ks + 1), beta(ks + 1);
   int keff = 0;
-  LOVE_TRY(sampler_lanczos<T>(g, ski->fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<T>(), m_pad, alpha.data(),
+  LOVE_TRY(sampler_lanczos<T>(g, fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<double>(), m_pad, alpha.data(),
                               beta.data(), &keff, c->status, s));
   if (keff < 1) return LOVE_ERR_NAN;
   double* ad = ab.as<double>();
@@ -644,7 +651,14 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
   LOVE_CUDA(cudaMemcpyAsync(&ok, okb.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, s));
   LOVE_CUDA(cudaStreamSynchronize(s));
   int shifted = 0;
-  if (!ok) {
+  // An FP64 root whose T' is not PD is indefinite at the rounding level of K_UU -
+  // Rt Rt^T: the shifted Cholesky below differs from the positive part of T' by
+  // the size of that rounding.  An FP32 cache's Rt carries FP32 rounding, and
+  // K_UU - Rt Rt^T can then be indefinite by a sizeable fraction of |T'| (on the
+  // 1-D n = 1e6 workload: 32 negative eigenvalues, the lowest -0.12 |T'|), where a
+  // shift would add that much to every direction: the root is the positive part
+  // of T' instead (eigen fallback below), as the paper's covariance requires.
+  if (!ok && sizeof(T) == 8) {
     // T' not numerically PD (K_UU - Rt Rt^T has eigenvalues at the rounding
     // level): Cholesky of T' + delta I, delta = -lambda_min(T') + rounding
     double* as = ed + (ks + 1);
@@ -657,12 +671,17 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
     shifted = ok;
   }
   const int vec = 16 / (int)sizeof(T);
-  c->ks = keff;
+  // the root belongs to the cache: taken from (and later freed by) its allocator;
+  // a root computed earlier is replaced
+  if (c->S) c->alloc.free(c->S, sizeof(T) * (size_t)m * c->ld_s, s);
+  c->S = nullptr;
+  c->ks = 0;
   c->ld_s = (keff + vec - 1) / vec * vec;
-  c->S = al.alloc(sizeof(T) * (size_t)m * c->ld_s, s);
+  c->S = c->alloc.alloc(sizeof(T) * (size_t)m * c->ld_s, s);
   if (!c->S) return LOVE_ERR_OOM;
+  c->ks = keff;
   if (ok) {
-    LOVE_COUNT_LAUNCH(); k_root_from_chol<T><<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(Qb.as<T>(), m_pad, m, keff, dd, ed, (T*)c->S, c->ld_s);
+    LOVE_COUNT_LAUNCH(); k_root_from_chol<T><<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(Qb.as<double>(), m_pad, m, keff, dd, ed, (T*)c->S, c->ld_s);
     c->sampler_fallback = shifted;
   } else {
     Buf A(al, s), V(al, s), B(al, s);
@@ -681,7 +700,7 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
     (void)lam;
     size_t smb = sizeof(T) * nn;
     LOVE_TRY(allow_smem(k_root_from_eig<T>, smb));
-    LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<T>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);
+    LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<double>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);
     LOVE_LAUNCH_CHECK();
     LOVE_CUDA(cudaStreamSynchronize(s));
     c->sampler_fallback = 1;
@@ -690,9 +709,10 @@ love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uin
   return cuda_check(cudaStreamSynchronize(s));
 }
 
-template love_status sampler_build<float>(love_ski*, love_cache*, const float*, int, uint64_t, double, cudaStream_t);
-template love_status sampler_build<double>(love_ski*, love_cache*, const double*, int, uint64_t, double,
-                                           cudaStream_t);
+template love_status sampler_build<float>(const GridHost&, const FftPlan*, const Allocator&, love_cache*,
+                                          const float*, int, uint64_t, double, cudaStream_t);
+template love_status sampler_build<double>(const GridHost&, const FftPlan*, const Allocator&, love_cache*,
+                                           const double*, int, uint64_t, double, cudaStream_t);
 
 static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 template <typename T>

@@ -249,6 +249,56 @@ __global__ void k_import_rows(const double* __restrict__ src, int k, int64_t m, 
   else ((float*)out)[idx] = (float)v;
 }
 
+// columns [0, k) of the predict cache (m x ld rows of the cache dtype) as a
+// column-major m x k array of the data dtype T: the sampler's Rt operand
+template <typename T>
+__global__ void k_rc_to_cols(const void* __restrict__ Rc, int cdt, int64_t m, int ld, int k, T* __restrict__ out) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * k) return;
+  const int c = (int)(idx / m);
+  const int64_t r = idx - (int64_t)c * m;
+  const int64_t src = r * ld + c;
+  double v;
+  if (cdt == LOVE_BF16) v = (double)__bfloat162float(((const __nv_bfloat16*)Rc)[src]);
+  else if (cdt == LOVE_F64) v = ((const double*)Rc)[src];
+  else v = (double)((const float*)Rc)[src];
+  out[idx] = (T)v;
+}
+
+template <typename T>
+love_status sampler_for_cache(love_cache* c, int ks, uint64_t seed, cudaStream_t s) {
+  const GridHost& g = c->grid;
+  const Allocator& al = c->alloc;
+  const int64_t m = g.m;
+  const int k = c->k_eff;
+  ks = std::min<int64_t>(ks, m);
+  FftPlan plans[LOVE_MAX_DIM];
+  love_status rc = LOVE_OK;
+  for (int e = 0; e < g.dim && rc == LOVE_OK; ++e)
+    rc = fft_plan_create(plans[e], g, e, al, s, c->dtype == LOVE_F32);
+  const size_t rb = sizeof(T) * (size_t)m * k;
+  T* rt = rc == LOVE_OK ? (T*)al.alloc(rb, s) : nullptr;
+  if (rc == LOVE_OK && !rt) rc = LOVE_ERR_OOM;
+  PhaseEvents ev;
+  ev.record(3, s);
+  if (rc == LOVE_OK) {
+    LOVE_COUNT_LAUNCH(); k_rc_to_cols<T><<<ceil_div(m * k, 256), 256, 0, s>>>(c->Rc, (int)c->cache_dtype, m, c->ld, k, rt);
+    rc = cuda_check(cudaGetLastError());
+  }
+  // the same breakdown tolerance as the sampler run of love_precompute (FP64 vectors)
+  if (rc == LOVE_OK) rc = sampler_build<T>(g, plans, al, c, rt, ks, seed, 1e-12, s);
+  ev.record(4, s);
+  if (rt) al.free(rt, rb, s);
+  for (int e = 0; e < g.dim; ++e) fft_plan_destroy(plans[e], al, s);
+  if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
+  if (rc == LOVE_OK) {
+    c->flags |= LOVE_WANT_SAMPLER;
+    float ms = 0.f;
+    if (ev.ok && cudaEventElapsedTime(&ms, ev.e[3], ev.e[4]) == cudaSuccess) c->phase_ms[3] = ms;
+  }
+  return rc;
+}
+
 double bf16_to_double(uint16_t h) {
   uint32_t u = (uint32_t)h << 16;
   float f;
@@ -564,8 +614,8 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   if (rc == LOVE_OK && (flags & LOVE_WANT_SAMPLER)) {
     int ks = o->sampler_k > 0 ? o->sampler_k : o->k;
     ks = std::min<int64_t>(ks, g.m);
-    // breakdown tolerance of the sampler's Lanczos run: its vectors are stored in T
-    rc = sampler_build<T>(ski, c, rt_keep, ks, o->sampler_seed, sizeof(T) == 8 ? 1e-12 : 1e-8, s);
+    // breakdown tolerance of the sampler's Lanczos run: its vectors are FP64
+    rc = sampler_build<T>(ski->grid, ski->fft, ski->alloc, c, rt_keep, ks, o->sampler_seed, 1e-12, s);
   }
   if (rt_keep) al.free(rt_keep, rtb, s);
   ev.record(4, s);
@@ -703,6 +753,14 @@ love_status love_sample(love_cache_t c, int64_t t, const void* x_test, int s_cou
     if (!c->sws) return LOVE_ERR_OOM;
   }
   return sample_launch_z_ws(c, t, x_test, s_count, z, seed, out, c->sws, cs(stream));
+}
+LOVE_ENTRY_CATCH
+
+love_status love_sampler_precompute(love_cache_t c, int ks, uint64_t seed, love_stream_t stream) try {
+  if (!c || ks < 0 || ks > LOVE_MAX_K) return LOVE_ERR_ARG;
+  if (ks == 0) ks = c->k_eff;
+  if (c->dtype == LOVE_F64) return sampler_for_cache<double>(c, ks, seed, cs(stream));
+  return sampler_for_cache<float>(c, ks, seed, cs(stream));
 }
 LOVE_ENTRY_CATCH
 

@@ -413,15 +413,17 @@ love_status cache_set_mean(love_cache* c, const double* a, cudaStream_t s);
 template <typename T>
 love_status build_cache(love_ski* ski, love_cache* c, const T* Q, int64_t ldq, const double* zmean,
                         cudaStream_t s, T* keep_rt, const double* amean = nullptr);
-// sampler Lanczos on M = K_UU - Rt Rt^T (FP64); Rt: m x k column-major (ldr)
+// sampler Lanczos on M = K_UU - Rt Rt^T, FP64 vectors Q (m_pad x ks, column-major);
+// Rt: m x k column-major (ldr) of the data dtype
 template <typename T>
 love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
-                            int k, int ks, uint64_t seed, double tau, T* Q, int64_t ldq, double* alpha_h,
+                            int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
                             double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s);
 // k_sample.cu: S = Q' L' (or the eigen fallback), stored in the cache
+// (g, fft: the grid and K_UU plans of the cache's kernel; al: work space)
 template <typename T>
-love_status sampler_build(love_ski* ski, love_cache* c, const T* Rt, int ks, uint64_t seed, double tau,
-                          cudaStream_t s);
+love_status sampler_build(const GridHost& g, const FftPlan* fft, const Allocator& al, love_cache* c, const T* Rt,
+                          int ks, uint64_t seed, double tau, cudaStream_t s);
 
 template <typename T>
 love_status permute_in(const T* v, const int32_t* perm, int64_t n, int64_t n_pad, T* out, cudaStream_t s);
