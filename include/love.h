@@ -331,9 +331,11 @@ LOVE_API love_status love_get_device_status(love_cache_t cache, int reset, love_
 
 /* ski_mvm_kuu_noalloc -- out = K_UU v, like ski_mvm_kuu, for callers that may
  * not allocate device memory.  The paper has no counterpart; it exists for
- * callers such as code being captured into a CUDA graph whose replays must
- * not allocate, real-time loops that forbid allocator calls, or host
- * frameworks that have already reserved all device memory.  ski_mvm_kuu takes
+ * callers such as real-time loops that forbid allocator calls (an allocation
+ * can block on the allocator's lock or synchronise the device), host
+ * frameworks that own and have already reserved all device memory (a
+ * cudaMalloc would fail or compete with their pool), and code running inside
+ * the caching allocator's own callbacks, which cannot re-enter it.  ski_mvm_kuu takes
  * its FFT work area from the handle's allocator; this entry point instead uses
  * a fixed file-scope device array of 4 MiB, present on every GPU that loads the
  * library until the process exits, and calls no allocator (no cudaMalloc,
@@ -400,7 +402,9 @@ LOVE_API love_status love_sample_batched(love_batch_t batch, const void* x, int 
  * on one stream.  With use_graph != 0 the launches are captured into a CUDA
  * graph the first time a given (x, mean, var, s, seed, samples) is seen (after
  * one eager call that sets up the work space) and the graph is replayed on
- * later calls with the same arguments. */
+ * later calls with the same arguments.  A love_sample_batched call that has to
+ * grow the batch's work space waits for a replay in flight and drops the graph,
+ * so the next serve call captures again. */
 LOVE_API love_status love_batch_serve(love_batch_t batch, const void* x, void* mean, void* var, int s,
                                       uint64_t seed, void* samples, int use_graph, love_stream_t stream);
 
@@ -411,6 +415,9 @@ typedef struct {
   int n_candidates;
   float candidate_ms[16];   /* in the order lanes {small..large} x ctas {4, 8, 16} */
   int64_t chunks;
+  int64_t graph_captures;          /* CUDA graphs captured by love_batch_serve so far */
+  int64_t graph_captures_dropped;  /* of them, dropped because love_sample_batched needed a larger
+                                      work space (the next serve call captures again) */
 } love_batch_info_t;
 LOVE_API love_status love_batch_info(love_batch_t batch, love_batch_info_t* info);
 

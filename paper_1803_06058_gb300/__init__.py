@@ -258,7 +258,8 @@ class Batch:
         inf = _lib.love_batch_info_t()
         check("love_batch_info", lib().love_batch_info(self.handle, C.byref(inf)))
         return {"lanes_per_point": inf.lanes_per_point, "ctas_per_sm": inf.ctas_per_sm,
-                "candidate_ms": list(inf.candidate_ms)[:inf.n_candidates], "chunks": inf.chunks}
+                "candidate_ms": list(inf.candidate_ms)[:inf.n_candidates], "chunks": inf.chunks,
+                "graph_captures": inf.graph_captures, "graph_captures_dropped": inf.graph_captures_dropped}
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib._lib is not None:

@@ -55,7 +55,8 @@ class love_device_status_t(C.Structure):
 
 class love_batch_info_t(C.Structure):
     _fields_ = [("lanes_per_point", C.c_int), ("ctas_per_sm", C.c_int), ("n_candidates", C.c_int),
-                ("candidate_ms", C.c_float * 16), ("chunks", C.c_int64)]
+                ("candidate_ms", C.c_float * 16), ("chunks", C.c_int64), ("graph_captures", C.c_int64),
+                ("graph_captures_dropped", C.c_int64)]
 
 
 VP = C.c_void_p

@@ -46,6 +46,8 @@ struct love_batch {
   // the legacy default stream, which cannot be captured; the graph stream is
   // joined to the caller's by events) and the arguments it was captured with
   cudaGraphExec_t gexec = nullptr;
+  int64_t gcaptures = 0;          // graphs captured by love_batch_serve
+  int64_t gcaptures_dropped = 0;  // of them, dropped because the work space moved
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   const void* gx = nullptr;
@@ -100,6 +102,15 @@ love_status ensure_ws(love_batch* b, int s_count, cudaStream_t s) {
   for (int i = 0; i < b->B; ++i)
     need = std::max(need, sample_ws_bytes(b->caches[i], b->t_off[i + 1] - b->t_off[i], s_count));
   if (need > b->ws_bytes) {
+    // love_batch_serve's graph has the old buffer's address baked into its
+    // sample launches: let a replay in flight finish, then drop the graph so
+    // the next serve call captures again with the new buffer
+    if (b->gexec) {
+      if (b->gstream) LOVE_CUDA(cudaStreamSynchronize(b->gstream));
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+      ++b->gcaptures_dropped;
+    }
     if (b->ws) b->alloc.free(b->ws, b->ws_bytes, s);
     b->ws = b->alloc.alloc(need, s);
     b->ws_bytes = b->ws ? need : 0;
@@ -402,6 +413,7 @@ love_status love_batch_serve(love_batch_t b, const void* x, void* mean, void* va
     if (rc != LOVE_OK) return rc;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = ex;
+    ++b->gcaptures;
     b->gx = x;
     b->gmean = mean;
     b->gvar = var;
@@ -427,6 +439,8 @@ love_status love_batch_info(love_batch_t b, love_batch_info_t* info) try {
   info->n_candidates = b->n_cand;
   for (int i = 0; i < b->n_cand && i < 16; ++i) info->candidate_ms[i] = b->cand_ms[i];
   info->chunks = b->nchunks;
+  info->graph_captures = b->gcaptures;
+  info->graph_captures_dropped = b->gcaptures_dropped;
   return LOVE_OK;
 }
 LOVE_ENTRY_CATCH

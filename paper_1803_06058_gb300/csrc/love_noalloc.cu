@@ -3,10 +3,11 @@
 // ski_mvm_kuu needs a work area for the FFT of grid modes longer than 2048
 // points (a four-step transform that goes through global memory) and takes it
 // from the handle's allocator.  Some callers cannot allocate at that point: a
-// stream being captured into a CUDA graph whose replays must not allocate, a
-// real-time loop that forbids allocator calls, or a host framework that owns
-// and has already reserved all device memory.  ski_mvm_kuu_noalloc gives them
-// the same product with its scratch in a fixed, file-scope device array.
+// real-time loop that forbids allocator calls (an allocation can block on a
+// lock or synchronise the device), a host framework that owns and has already
+// reserved all device memory, or code running inside the caching allocator's
+// own callbacks, which cannot re-enter it.  ski_mvm_kuu_noalloc gives them the
+// same product with its scratch in a fixed, file-scope device array.
 //
 // Scratch: LOVE_NOALLOC_SCRATCH_BYTES (4 MiB) of device memory, present on every
 // GPU that loads this library, for the life of the process.  It holds

@@ -120,6 +120,43 @@ def test_batch_serve_graph_replay(love, batch_setup):
         assert torch.equal(mean, m_ref) and torch.equal(var, v_ref) and torch.equal(smp, s_ref)
 
 
+def test_batch_serve_recaptures_after_work_space_grows(love, batch_setup):
+    """A graph captured by love_batch_serve holds the work space's address; a
+    love_sample_batched call with more samples grows (moves) that work space, so
+    the graph must be dropped and the next serve call capture again: its
+    results stay bitwise those of the eager calls."""
+    members, t_sizes, skis, caches, keff, xs, x_all = batch_setup
+    batch = love.love_batch_create(caches, t_sizes)
+    T = x_all.shape[0]
+    s = 8
+    mean = torch.empty(T, device="cuda")
+    var = torch.empty(T, device="cuda")
+    smp = torch.empty(s * T, device="cuda")
+    m_ref, v_ref = love.love_predict_batched(batch, x_all)
+    s_ref = love.love_sample_batched(batch, x_all, s, seed=5)
+
+    def serve_and_check():
+        mean.fill_(0)
+        var.fill_(0)
+        smp.fill_(0)
+        love.love_batch_serve(batch, x_all, mean, var, s=s, seed=5, samples=smp, use_graph=True)
+        torch.cuda.synchronize()
+        assert torch.equal(mean, m_ref) and torch.equal(var, v_ref) and torch.equal(smp, s_ref)
+
+    serve_and_check()                       # eager call + capture
+    serve_and_check()                       # replay
+    inf = batch.info()
+    assert inf["graph_captures"] == 1 and inf["graph_captures_dropped"] == 0
+    big = love.love_sample_batched(batch, x_all, 64, seed=9)   # grows the work space
+    torch.cuda.synchronize()
+    assert batch.info()["graph_captures_dropped"] == 1
+    serve_and_check()                       # captures again with the new work space
+    serve_and_check()                       # and replays it
+    assert batch.info()["graph_captures"] == 2
+    ref_big = love.love_sample(caches[0], torch.tensor(xs[0], dtype=torch.float32, device="cuda"), 64, seed=9)
+    assert torch.equal(love.batch_split(batch, big, 64)[0], ref_big)
+
+
 def test_batch_of_one_and_errors(love, batch_setup):
     members, t_sizes, skis, caches, keff, xs, x_all = batch_setup
     b1 = love.love_batch_create([caches[0]], [t_sizes[0]])

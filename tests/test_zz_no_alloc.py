@@ -1,9 +1,10 @@
 """ski_mvm_kuu_noalloc: the K_UU product for callers that cannot allocate.
 
-Callers inside a CUDA-graph capture whose replays must not allocate, real-time
-loops that forbid allocator calls, or frameworks that have reserved all device
-memory use this entry point; its FFT scratch is a fixed file-scope device array
-(4 MiB) instead of memory from the handle's allocator.  This file is collected
+Real-time loops that forbid allocator calls (an allocation can block or
+synchronise the device), frameworks that have reserved all device memory, and
+code inside the caching allocator's own callbacks use this entry point; its FFT
+scratch is a fixed file-scope device array (4 MiB) instead of memory from the
+handle's allocator.  This file is collected
 last, so a failure here leaves every other test already run.  The test passes
 alone in a fresh process and after the other tests: the first call on a device
 looks up the array's address, every later call reuses it.
