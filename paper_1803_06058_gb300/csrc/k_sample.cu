@@ -56,11 +56,10 @@ __global__ void k_chol_tri(const double* alpha, const double* beta, int k, doubl
 // rounding of |T'|, lo the lower end of the final bracket of lambda_min (so
 // delta >= -lambda_min: the Cholesky factorisation of the shifted matrix
 // succeeds, and delta exceeds -lambda_min by at most the bracket's width);
-// alpha_s = alpha + delta.  One CTA: each round its threads count at as many
-// interior points of the bracket, and the bracket shrinks to the cell holding
-// lambda_min until its width is rel_res |T'| (FP64 resolution for an FP64
-// root; rel_res = 2^-30 for an FP32 root: the extra shift, at most 2^-30 |T'|,
-// is far below the FP32 rounding of S).  The counts are FP64 divisions, which
+// alpha_s = alpha + delta.  Used for an FP64 root only (T' indefinite at the
+// rounding level).  One CTA: each round its threads count at as many interior
+// points of the bracket, and the bracket shrinks to the cell holding
+// lambda_min until its width is rel_res |T'| (FP64 resolution).  The counts are FP64 divisions, which
 // this part runs at a small fraction of its FP32 rate, so a round costs in
 // proportion to the warps per SM sub-partition: it is launched with four warps
 // (128 points, 7 bits of the bracket per round).
@@ -129,125 +128,215 @@ __global__ void k_root_from_chol(const double* __restrict__ Q, int64_t ldq, int6
   S[idx] = (T)v;
 }
 
-// dense tridiagonal T' into A (n x n)
-__global__ void k_tri_dense(const double* alpha, const double* beta, int n, double* A) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * n) return;
-  int i = (int)(idx / n), j = (int)(idx % n);
-  double v = 0.0;
-  if (i == j) v = alpha[i];
-  else if (i == j + 1) v = beta[j];
-  else if (j == i + 1) v = beta[i];
-  A[idx] = v;
+// Eigenpairs of the symmetric tridiagonal T' (n <= 200) for the positive-part
+// root, one warp per eigenvalue (ascending index i):
+//   1  lam_i to ~2^-24 |T'| by multisection on FP32 Sturm counts (the number of
+//      negative pivots of the LDL^T factorisation of T' - x I is the number of
+//      eigenvalues below x): each round the 32 lanes count at 32 interior points
+//      of the bracket, which shrinks to the cell holding lam_i;
+//   2  inverse iteration in FP64 with that shift: LU of T' - lam I with partial
+//      pivoting (row swaps give U a second superdiagonal), INVIT solves,
+//      normalised each time (Golub & Van Loan, Sec. 8.2.2); the shift's error e
+//      shrinks the neighbours' components by e / gap per solve.  The start
+//      vector differs per index (1 + a SplitMix64 draw in [-1/2, 1/2) per entry),
+//      so eigenvalues too close for FP32 to separate, which share a shift, still
+//      give independent vectors of their common invariant subspace;
+//   3  lam_i = x^T T' x (FP64 Rayleigh quotient).
+// V[r * n + i] = x_r (eigenvectors in columns), lam[i].
+constexpr int INVIT = 4;
+__device__ int sturm_count_f(const float* a, const float* b2, int n, float x) {
+  int neg = 0;
+  float d = a[0] - x;
+  for (int j = 0;;) {
+    if (fabsf(d) < 1e-37f) d = -1e-37f;
+    if (d < 0.f) ++neg;
+    if (++j == n) break;
+    d = (a[j] - x) - b2[j - 1] / d;
+  }
+  return neg;
 }
 
-// Parallel Jacobi eigenvalue iteration on a symmetric n x n matrix, one CTA,
-// in FP32 shared memory (Golub & Van Loan, Sec. 8.5: cyclic Jacobi with the
-// round-robin ordering, so each step applies n/2 rotations on disjoint index
-// pairs at once).  Each rotation (c, s at (p, q)) uses tan(phi) = t, the smaller
-// root of t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq), which
-// annihilates a_pq: A <- J^T A J, V <- V J.  The off-diagonal mass falls
-// quadratically once it is small, so the sweep after the one that starts with
-// off <= 1e-11 tot (squared Frobenius norms; the FP32 rounding floor is ~n^2
-// 2^-48 tot, ~4e-13 for n = 100) is the last.  FP32 is enough here: the root
-// it serves is stored in FP32 (an FP64 root whose T' is not PD takes the
-// shifted Cholesky first), and FP64 on this part runs at a small fraction of
-// FP32.  Writes lam (n) and V (n x n, eigenvectors in columns) as doubles.
-// Shared memory: 2 np^2 + 2 np floats, np = n rounded up to even.
-__global__ void k_jacobi_par(const double* __restrict__ Ain, int n, int max_sweeps, double* __restrict__ lam,
-                             double* __restrict__ Vout) {
+__global__ void __launch_bounds__(32) k_tri_eigpairs(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                                     int n, double* __restrict__ lam, double* __restrict__ V) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int np = n + (n & 1);
-  float* A = reinterpret_cast<float*>(smem_raw);
-  float* V = A + (size_t)np * np;
-  float* cs = V + (size_t)np * np;   // [np/2][2]
-  int* pr = reinterpret_cast<int*>(cs + np);  // [np/2][2]
-  __shared__ float red[2][32];
-  __shared__ int stop;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) stop = 0;
-  for (int i = tid; i < np * np; i += nt) {
-    int r = i / np, c = i % np;
-    A[i] = (r < n && c < n) ? (float)Ain[(int64_t)r * n + c] : 0.f;
-    V[i] = (r == c) ? 1.f : 0.f;
+  double* u0 = reinterpret_cast<double*>(smem_raw);   // pivots
+  double* u1 = u0 + n;                                 // first superdiagonal of U
+  double* u2 = u1 + n;                                 // second superdiagonal (after swaps)
+  double* ml = u2 + n;                                 // multipliers
+  double* xv = ml + n;                                 // iterate
+  float* af = reinterpret_cast<float*>(xv + n);        // T' diagonal (FP32)
+  float* b2f = af + n;                                 // squared off-diagonal (FP32)
+  int* swp = reinterpret_cast<int*>(b2f + n);          // row swap at elimination step j
+  const int i = blockIdx.x, lane = threadIdx.x;
+  for (int j = lane; j < n; j += 32) {
+    af[j] = (float)alpha[j];
+    if (j + 1 < n) b2f[j] = (float)(beta[j] * beta[j]);
   }
-  __syncthreads();
-  const int half = np / 2;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    float off = 0.f, tot = 0.f;
-    for (int i = tid; i < np * np; i += nt) {
-      float v = A[i];
-      tot += v * v;
-      if (i / np != i % np) off += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = off;
-      red[1][tid >> 5] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float a = 0.f, b = 0.f;
-      for (int w = 0; w < (nt + 31) / 32; ++w) {
-        a += red[0][w];
-        b += red[1][w];
+  __syncwarp();
+  // Gershgorin interval (every lane the same)
+  double lo = 0.0, hi = 0.0, tn = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double r = (j > 0 ? fabs(beta[j - 1]) : 0.0) + (j + 1 < n ? fabs(beta[j]) : 0.0);
+    lo = j == 0 ? alpha[j] - r : fmin(lo, alpha[j] - r);
+    hi = j == 0 ? alpha[j] + r : fmax(hi, alpha[j] + r);
+  }
+  tn = fmax(fabs(lo), fabs(hi));
+  float flo = (float)lo - 1e-6f * (float)tn, fhi = (float)hi + 1e-6f * (float)tn;
+  for (int round = 0; round < 8; ++round) {
+    const float w = fhi - flo;
+    if (!(w > 2.4e-7f * (float)tn)) break;
+    const float x = flo + w * (float)(lane + 1) / 33.f;
+    const bool above = sturm_count_f(af, b2f, n, x) >= i + 1;
+    const unsigned bal = __ballot_sync(0xffffffffu, above);
+    const int f = bal ? __ffs(bal) - 1 : 32;   // first point with >= i + 1 eigenvalues below it
+    const float nlo = f == 0 ? flo : flo + w * (float)f / 33.f;
+    const float nhi = f == 32 ? fhi : flo + w * (float)(f + 1) / 33.f;
+    flo = nlo;
+    fhi = nhi;
+  }
+  const double shift = 0.5 * ((double)flo + (double)fhi);
+  // LU with partial pivoting of T' - shift I (lane 0; tridiagonal, so O(n))
+  if (lane == 0) {
+    const double tiny = 2.2204460492503131e-16 * fmax(tn, 1e-300);
+    double d = alpha[0] - shift, e = n > 1 ? beta[0] : 0.0, g = 0.0;   // current row: (d, e, g) at cols j, j+1, j+2
+    for (int j = 0; j < n - 1; ++j) {
+      const double bl = beta[j];                  // T'[j+1, j]
+      const double an = alpha[j + 1] - shift;     // T'[j+1, j+1]
+      const double cn = j + 2 < n ? beta[j + 1] : 0.0;
+      if (fabs(bl) > fabs(d)) {                   // swap rows j and j+1
+        const double mlt = d / bl;
+        u0[j] = bl;
+        u1[j] = an;
+        u2[j] = cn;
+        ml[j] = mlt;
+        swp[j] = 1;
+        d = e - mlt * an;
+        e = g - mlt * cn;
+        g = 0.0;
+      } else {
+        const double piv = d == 0.0 ? tiny : d;
+        const double mlt = bl / piv;
+        u0[j] = piv;
+        u1[j] = e;
+        u2[j] = g;
+        ml[j] = mlt;
+        swp[j] = 0;
+        d = an - mlt * e;
+        e = cn - mlt * g;
+        g = 0.0;
       }
-      // 2: converged; 1: this sweep is the last
-      stop = (a <= 4e-13f * b || stop == 1) ? 2 : (a <= 1e-11f * b ? 1 : 0);
     }
-    __syncthreads();
-    if (stop == 2) break;
-    for (int step = 0; step < np - 1; ++step) {
-      // round robin: position 0 holds index 0, positions 1..np-1 rotate by `step`
-      for (int i = tid; i < half; i += nt) {
-        int ja = i, jb = np - 1 - i;
-        int a = ja == 0 ? 0 : 1 + (ja - 1 + step) % (np - 1);
-        int b = 1 + (jb - 1 + step) % (np - 1);
-        int p = a < b ? a : b, q = a < b ? b : a;
-        float apq = A[p * np + q], app = A[p * np + p], aqq = A[q * np + q];
-        float c = 1.f, sn = 0.f;
-        if (fabsf(apq) > 1e-30f && fabsf(apq) > 1e-8f * sqrtf(fabsf(app * aqq))) {
-          float theta = (aqq - app) / (2.f * apq);
-          float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-          c = rsqrtf(t * t + 1.f);
-          sn = t * c;
+    u0[n - 1] = d == 0.0 ? tiny : d;
+    u1[n - 1] = 0.0;
+    u2[n - 1] = 0.0;
+    if (n > 1) u2[n - 2] = 0.0;
+  }
+  for (int j = lane; j < n; j += 32) {
+    uint64_t z = (uint64_t)(i * n + j + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    xv[j] = 1.0 + ((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+  }
+  __syncwarp();
+  for (int it = 0; it < INVIT; ++it) {
+    if (lane == 0) {
+      for (int j = 0; j < n - 1; ++j) {           // L^{-1} with the swaps
+        if (swp[j]) {
+          const double t = xv[j];
+          xv[j] = xv[j + 1];
+          xv[j + 1] = t;
         }
-        pr[2 * i] = p;
-        pr[2 * i + 1] = q;
-        cs[2 * i] = c;
-        cs[2 * i + 1] = sn;
+        xv[j + 1] -= ml[j] * xv[j];
       }
-      __syncthreads();
-      for (int w = tid; w < half * np; w += nt) {  // columns p, q of A and V
-        int i = w / np, r = w % np;
-        int p = pr[2 * i], q = pr[2 * i + 1];
-        float c = cs[2 * i], sn = cs[2 * i + 1];
-        if (sn == 0.f) continue;
-        float arp = A[r * np + p], arq = A[r * np + q];
-        A[r * np + p] = c * arp - sn * arq;
-        A[r * np + q] = sn * arp + c * arq;
-        float vrp = V[r * np + p], vrq = V[r * np + q];
-        V[r * np + p] = c * vrp - sn * vrq;
-        V[r * np + q] = sn * vrp + c * vrq;
+      for (int j = n - 1; j >= 0; --j) {          // U^{-1}
+        double r = xv[j];
+        if (j + 1 < n) r -= u1[j] * xv[j + 1];
+        if (j + 2 < n) r -= u2[j] * xv[j + 2];
+        xv[j] = r / u0[j];
       }
-      __syncthreads();
-      for (int w = tid; w < half * np; w += nt) {  // rows p, q of A
-        int i = w / np, cidx = w % np;
-        int p = pr[2 * i], q = pr[2 * i + 1];
-        float c = cs[2 * i], sn = cs[2 * i + 1];
-        if (sn == 0.f) continue;
-        float apc = A[p * np + cidx], aqc = A[q * np + cidx];
-        A[p * np + cidx] = c * apc - sn * aqc;
-        A[q * np + cidx] = sn * apc + c * aqc;
-      }
-      __syncthreads();
+    }
+    __syncwarp();
+    double ss = 0.0;
+    for (int j = lane; j < n; j += 32) ss = fma(xv[j], xv[j], ss);
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double sc = 1.0 / sqrt(ss);
+    for (int j = lane; j < n; j += 32) xv[j] *= sc;
+    __syncwarp();
+  }
+  // Rayleigh quotient and the sign (largest-magnitude entry positive)
+  double rq = 0.0, best = -1.0;
+  int bi = 0;
+  for (int j = lane; j < n; j += 32) {
+    double tx = alpha[j] * xv[j];
+    if (j > 0) tx += beta[j - 1] * xv[j - 1];
+    if (j + 1 < n) tx += beta[j] * xv[j + 1];
+    rq = fma(xv[j], tx, rq);
+    if (fabs(xv[j]) > best) {
+      best = fabs(xv[j]);
+      bi = j;
     }
   }
-  for (int i = tid; i < n; i += nt) lam[i] = (double)A[i * np + i];
-  for (int i = tid; i < n * n; i += nt) Vout[i] = (double)V[(i / n) * np + (i % n)];
+  for (int o = 16; o > 0; o >>= 1) {
+    rq += __shfl_xor_sync(0xffffffffu, rq, o);
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  const double sgn = xv[bi] < 0.0 ? -1.0 : 1.0;
+  for (int j = lane; j < n; j += 32) V[(size_t)j * n + i] = sgn * xv[j];
+  if (lane == 0) lam[i] = rq;
+}
+
+// Vectors whose eigenvalues lie within 1e-3 |T'| of their neighbour (a cluster)
+// are made orthonormal by modified Gram-Schmidt in index order, applied twice
+// (LAPACK's stein criterion for the clusters); inverse iteration leaves the
+// others orthogonal to ~eps |T'| / gap.  A vector that the projections leave
+// (numerically) empty lay in the span of its predecessors: a unit vector takes
+// its place before the passes are repeated.  One warp per cluster; lam is only
+// read (its Rayleigh quotients already hold to the vectors' accuracy squared).
+__global__ void __launch_bounds__(256) k_tri_cluster_mgs(int n, const double* __restrict__ lam,
+                                                          double* __restrict__ V) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double tn = 0.0;
+  for (int j = 0; j < n; ++j) tn = fmax(tn, fabs(lam[j]));
+  const double tol = 1e-3 * tn;
+  // clusters: maximal runs [c0, c1) of consecutive eigenvalues with gaps < tol
+  int cid = 0;
+  for (int c0 = 0; c0 < n;) {
+    int c1 = c0 + 1;
+    while (c1 < n && lam[c1] - lam[c1 - 1] < tol) ++c1;
+    if (c1 - c0 > 1 && (cid++ % nw) == w) {
+      for (int q = c0 + 1; q < c1; ++q) {
+        for (int attempt = 0; attempt < 2; ++attempt) {
+          for (int pass = 0; pass < 2; ++pass)
+            for (int p = c0; p < q; ++p) {
+              double d = 0.0;
+              for (int j = lane; j < n; j += 32) d = fma(V[(size_t)j * n + p], V[(size_t)j * n + q], d);
+              for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+              for (int j = lane; j < n; j += 32) V[(size_t)j * n + q] -= d * V[(size_t)j * n + p];
+              __syncwarp();
+            }
+          double ss = 0.0;
+          for (int j = lane; j < n; j += 32) ss = fma(V[(size_t)j * n + q], V[(size_t)j * n + q], ss);
+          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          if (ss > 1e-20) {   // the vector had unit norm before the projections
+            const double sc = 1.0 / sqrt(ss);
+            for (int j = lane; j < n; j += 32) V[(size_t)j * n + q] *= sc;
+            __syncwarp();
+            break;
+          }
+          // empty: restart from the unit vector e_(q - c0 + attempt) mod n
+          for (int j = lane; j < n; j += 32) V[(size_t)j * n + q] = j == (q - c0 + attempt) % n ? 1.0 : 0.0;
+          __syncwarp();
+        }
+      }
+    }
+    c0 = c1;
+  }
 }
 
 // B[j, c] = V[j, c] sqrt(max(lam_c, 0))
@@ -259,20 +348,38 @@ __global__ void k_scale_eig(const double* lam, const double* V, int n, double* B
   B[idx] = V[idx] * sqrt(l > 0.0 ? l : 0.0);
 }
 
-// S[r, c] = sum_j Q'[r, j] B[j, c]  (Q' in FP64, B held in T: arithmetic in T; S row-major ld_s)
+// S[r, c] = sum_j Q'[r, j] B[j, c]  (Q' and B in FP64, arithmetic in T; S row-major
+// ld_s).  A CTA takes ROOT_ROWS rows, their Q' entries staged in shared memory,
+// and B too when it fits (stage_b); thread (rr, cg) forms the columns cg, cg + 4,
+// ... of row rr (the 32 lanes of a warp share c: B's entries are broadcasts).
+constexpr int ROOT_ROWS = 64;
 template <typename T>
-__global__ void k_root_from_eig(const double* __restrict__ Q, int64_t ldq, int64_t m, int k,
-                                const double* __restrict__ B, T* __restrict__ S, int ld_s) {
+__global__ void __launch_bounds__(256) k_root_from_eig(const double* __restrict__ Q, int64_t ldq, int64_t m, int k,
+                                                       const double* __restrict__ B, T* __restrict__ S, int ld_s,
+                                                       int stage_b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Bs = reinterpret_cast<T*>(smem_raw);  // k x k
-  for (int i = threadIdx.x; i < k * k; i += blockDim.x) Bs[i] = (T)B[i];
+  T* Qs = reinterpret_cast<T*>(smem_raw);     // k x ROOT_ROWS
+  T* Bs = Qs + (size_t)k * ROOT_ROWS;         // k x k when staged
+  const int64_t r0 = (int64_t)blockIdx.x * ROOT_ROWS;
+  if (stage_b)
+    for (int i = threadIdx.x; i < k * k; i += blockDim.x) Bs[i] = (T)B[i];
+  for (int i = threadIdx.x; i < k * ROOT_ROWS; i += blockDim.x) {
+    const int j = i / ROOT_ROWS, rr = i - j * ROOT_ROWS;
+    const int64_t r = r0 + rr;
+    Qs[i] = r < m ? (T)Q[(int64_t)j * ldq + r] : T(0);
+  }
   __syncthreads();
-  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rr = threadIdx.x % ROOT_ROWS, cg = threadIdx.x / ROOT_ROWS;   // 4 column groups
+  const int64_t r = r0 + rr;
   if (r >= m) return;
-  for (int c = 0; c < ld_s; ++c) {
+  for (int c = cg; c < ld_s; c += 4) {
     T acc = T(0);
-    if (c < k)
-      for (int j = 0; j < k; ++j) acc += (T)Q[(int64_t)j * ldq + r] * Bs[j * k + c];
+    if (c < k) {
+      if (stage_b)
+        for (int j = 0; j < k; ++j) acc += Qs[j * ROOT_ROWS + rr] * Bs[j * k + c];
+      else
+        for (int j = 0; j < k; ++j) acc += Qs[j * ROOT_ROWS + rr] * (T)__ldg(B + (size_t)j * k + c);
+    }
     S[r * ld_s + c] = acc;
   }
 }
@@ -636,8 +743,13 @@ love_status sampler_build(const GridHost& g, const FftPlan* fft, const Allocator
     return LOVE_ERR_OOM;
   std::vector<double> alpha(ks + 1), beta(ks + 1);
   int keff = 0;
-  LOVE_TRY(sampler_lanczos<T>(g, fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<double>(), m_pad, alpha.data(),
-                              beta.data(), &keff, c->status, s));
+  // one persistent launch where the grid allows it (1-D), else the multi-launch run
+  love_status lrc = sampler_lanczos_fused<T>(g, fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<double>(), m_pad,
+                                             alpha.data(), beta.data(), &keff, c->status, s);
+  if (lrc == LOVE_ERR_UNSUPPORTED)
+    lrc = sampler_lanczos<T>(g, fft, al, Rt, m, c->k_eff, ks, seed, tau, Qb.as<double>(), m_pad, alpha.data(),
+                             beta.data(), &keff, c->status, s);
+  LOVE_TRY(lrc);
   if (keff < 1) return LOVE_ERR_NAN;
   double* ad = ab.as<double>();
   double* bd = ad + (ks + 1);
@@ -662,7 +774,7 @@ love_status sampler_build(const GridHost& g, const FftPlan* fft, const Allocator
     // T' not numerically PD (K_UU - Rt Rt^T has eigenvalues at the rounding
     // level): Cholesky of T' + delta I, delta = -lambda_min(T') + rounding
     double* as = ed + (ks + 1);
-    const double rel_res = sizeof(T) == 8 ? 2.0 * 2.2204460492503131e-16 : 0x1p-30;
+    const double rel_res = 2.0 * 2.2204460492503131e-16;
     LOVE_COUNT_LAUNCH(); k_tri_shift<<<1, 128, 0, s>>>(ad, bd, keff, as, rel_res);
     LOVE_COUNT_LAUNCH(); k_chol_tri<<<1, 32, 0, s>>>(as, bd, keff, dd, ed, okb.as<int>());
     LOVE_LAUNCH_CHECK();
@@ -684,23 +796,19 @@ love_status sampler_build(const GridHost& g, const FftPlan* fft, const Allocator
     LOVE_COUNT_LAUNCH(); k_root_from_chol<T><<<ceil_div(m * c->ld_s, 256), 256, 0, s>>>(Qb.as<double>(), m_pad, m, keff, dd, ed, (T*)c->S, c->ld_s);
     c->sampler_fallback = shifted;
   } else {
-    Buf A(al, s), V(al, s), B(al, s);
+    Buf V(al, s), B(al, s), L(al, s);
     const int64_t nn = (int64_t)keff * keff;
-    if (!A.get(sizeof(double) * nn) || !V.get(sizeof(double) * nn) || !B.get(sizeof(double) * nn)) return LOVE_ERR_OOM;
-    LOVE_COUNT_LAUNCH(); k_tri_dense<<<ceil_div(nn, 256), 256, 0, s>>>(ad, bd, keff, A.as<double>());
-    const int np = keff + (keff & 1);
-    size_t sm = sizeof(float) * (2 * (size_t)np * np + 2 * np);
-    if (sm > 220 * 1024) return LOVE_ERR_UNSUPPORTED;   // k' > ~165
-    LOVE_TRY(allow_smem(k_jacobi_par, sm));
-    double* lam = B.as<double>();                        // first n entries of B as scratch
-    Buf L(al, s);
-    if (!L.get(sizeof(double) * keff)) return LOVE_ERR_OOM;
-    LOVE_COUNT_LAUNCH(); k_jacobi_par<<<1, 1024, sm, s>>>(A.as<double>(), keff, 40, L.as<double>(), V.as<double>());
+    if (!V.get(sizeof(double) * nn) || !B.get(sizeof(double) * nn) || !L.get(sizeof(double) * keff))
+      return LOVE_ERR_OOM;
+    const size_t sme = sizeof(double) * 5 * (size_t)keff + sizeof(float) * 2 * (size_t)keff + sizeof(int) * keff;
+    LOVE_COUNT_LAUNCH(); k_tri_eigpairs<<<keff, 32, sme, s>>>(ad, bd, keff, L.as<double>(), V.as<double>());
+    LOVE_COUNT_LAUNCH(); k_tri_cluster_mgs<<<1, 256, 0, s>>>(keff, L.as<double>(), V.as<double>());
     LOVE_COUNT_LAUNCH(); k_scale_eig<<<ceil_div(nn, 256), 256, 0, s>>>(L.as<double>(), V.as<double>(), keff, B.as<double>());
-    (void)lam;
-    size_t smb = sizeof(T) * nn;
+    const size_t smq = sizeof(T) * (size_t)keff * ROOT_ROWS, smbb = sizeof(T) * (size_t)nn;
+    const int stage_b = smq + smbb <= 100 * 1024;
+    const size_t smb = smq + (stage_b ? smbb : 0);
     LOVE_TRY(allow_smem(k_root_from_eig<T>, smb));
-    LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, 256), 256, smb, s>>>(Qb.as<double>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s);
+    LOVE_COUNT_LAUNCH(); k_root_from_eig<T><<<ceil_div(m, ROOT_ROWS), 256, smb, s>>>(Qb.as<double>(), m_pad, m, keff, B.as<double>(), (T*)c->S, c->ld_s, stage_b);
     LOVE_LAUNCH_CHECK();
     LOVE_CUDA(cudaStreamSynchronize(s));
     c->sampler_fallback = 1;

@@ -252,6 +252,70 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---------------------------------------------------------------------------
+// grid-wide barrier of a cooperative launch (all CTAs co-resident), bounded
+// like every other wait: after ~1 s a CTA flags LOVE_ERR_TIMEOUT, raises the
+// abort word (so the others stop waiting too) and the call returns false; the
+// kernel must then return without entering another barrier.  The counters live
+// in global memory, zeroed before the launch.  Thread 0 of each CTA arrives
+// with a release add after the CTA's bar.sync and waits with acquire loads, so
+// every global write made before the barrier by any CTA is visible after it
+// (data that other CTAs wrote must still be read past L1: ld.global.cg).
+struct GridSync {
+  unsigned int count;   // CTAs arrived at the current barrier
+  unsigned int gen;     // barriers completed
+  unsigned int abort;   // a CTA gave up waiting
+  unsigned int pad;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// `gen` is the caller's count of barriers passed (the same in every CTA)
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned int& gen, DevStatus* status) {
+  __shared__ int gb_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = gen;
+    __threadfence();
+    if (atom_add_acq_rel_gpu(&gs->count, 1u) == gridDim.x - 1) {
+      gs->count = 0u;                  // ordered before the release below
+      st_release_gpu(&gs->gen, g + 1u);
+    } else {
+      const uint64_t t0 = global_timer_ns();
+      while (ld_acquire_gpu(&gs->gen) == g) {
+        if (ld_acquire_gpu(&gs->abort)) {
+          ok = 0;
+          break;
+        }
+        if (global_timer_ns() - t0 > 1000000000ull) {
+          atomicExch(&gs->abort, 1u);
+          dev_flag(status, LOVE_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    gb_ok = ok;
+  }
+  __syncthreads();
+  gen += 1u;
+  return gb_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
 // host-side handle definitions
 struct FftPlan {
   int64_t g = 0;       // Toeplitz size along this mode
@@ -419,6 +483,12 @@ template <typename T>
 love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
                             int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
                             double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s);
+// k_sampler.cu: the same run as one persistent cooperative kernel (1-D grids
+// whose per-CTA share fits in shared memory); LOVE_ERR_UNSUPPORTED otherwise
+template <typename T>
+love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt,
+                                  int64_t ldr, int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq,
+                                  double* alpha_h, double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s);
 // k_sample.cu: S = Q' L' (or the eigen fallback), stored in the cache
 // (g, fft: the grid and K_UU plans of the cache's kernel; al: work space)
 template <typename T>
