@@ -56,6 +56,20 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _profile_value(name, key):
+    """A number from a committed ncu summary (a line 'key: N')."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    for ln in open(p):
+        if ln.strip().startswith(key + ":"):
+            try:
+                return float(ln.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
 def _profile_traffic(name):
     """dram bytes per launch from a committed ncu summary (line 'traffic_bytes_per_launch: N')."""
     p = os.path.join(ROOT, "profiles", name)
@@ -150,6 +164,106 @@ def cpu_oracle(wl, n_sample=200_000, t_sample=None, reps=1):
     # its time unchanged, so one core is what it uses
     return {"vars_per_s": xs.shape[0] / min(times), "precompute_s": pre_s, "t": xs.shape[0],
             "n_sample": n_sample, "times": times, "cores": 1, "cores_available": os.cpu_count(), "np": np}
+
+
+def oracle_accuracy(wl, xs, xq, var_g, mean_g, var_root_g, samples_g, sampler_seed, k, n_var=10_000,
+                    n_exact=2_000, n_cov=1_000):
+    """Errors of the GPU outputs of one bench step against the FP64 oracle
+    (part of the cpu_baseline leg: the oracle runs on the host, after the timed
+    region).  xs: the predict points (t x 1), xq: the sample points; var_g,
+    mean_g: GPU outputs at xs; var_root_g: love_predict_var_root at the first
+    n_exact of the sampled predict points; samples_g: s x t_sample.
+
+      * LOVE at the same k: oracle pre-compute on the full training set, variance
+        at n_var sampled predict points (|dvar| / p and relative);
+      * the exact SKI posterior, by the push-through identity with one dense
+        m x m LU (A = K_UU G + s^2 I, G = W W^T): variance and mean at n_exact
+        points -- the error LOVE makes there, and the error of the variance from
+        the posterior root (Sec. 3.3) -- and the posterior covariance at n_cov
+        sample points, against which the samples' empirical covariance is
+        measured by element-wise mean absolute error (the paper's Sec. 4
+        sampling table);
+      * the oracle's own sampler root at the same k' and seed."""
+    import numpy as np
+    import scipy.linalg
+    from oracle import grid as og
+    from oracle import love as ol
+    from oracle import ski as os_
+    t0 = time.perf_counter()
+    x = wl.x_train()
+    y = wl.y_train(x)
+    grid = og.grid_from_workload(wl)
+    ski = os_.SKI(grid, x, wl.noise, y)
+    c_o = ol.precompute(ski, k=k, want_mean=False)
+    rng = np.random.default_rng(2024)
+    idx = rng.choice(xs.shape[0], n_var, replace=False)
+    xv = xs[idx]
+    p = ol.prior(grid, xv)
+    _, v_o = ol.predict(c_o, xv)
+    vg = var_g[idx]
+    dv = np.abs(vg - v_o)
+    out = {"variance_vs_oracle_same_k": {
+        "points": int(n_var), "max_abs_dvar_over_p": float(np.max(dv / p)),
+        "median_abs_dvar_over_p": float(np.median(dv / p)),
+        "median_rel": float(np.median(dv / v_o)), "p99_rel": float(np.quantile(dv / v_o, 0.99)),
+        "median_var_over_p": float(np.median(v_o / p)),
+        "tolerance_abs_dvar_over_p": 1e-6}}
+    # exact SKI posterior by the push-through identity
+    K = grid.dense_kuu()
+    G = (ski.W @ ski.W.T).tocsr()
+    A = np.asarray((G.T @ K.T).T) + wl.noise * np.eye(grid.m)      # K G + s^2 I
+    del K
+    lu = scipy.linalg.lu_factor(A, overwrite_a=True, check_finite=False)
+    del A
+    ie = idx[:n_exact]
+    iq = rng.choice(xq.shape[0], n_cov, replace=False)
+    Wv = grid.W(xs[ie])
+    Wq = grid.W(xq[iq])
+    B = grid.kuu_matmul(np.hstack([Wv.toarray(), Wq.toarray()]))   # K W*
+    Y = scipy.linalg.lu_solve(lu, B, check_finite=False)           # (K G + s^2 I)^{-1} K W*
+    GY = G @ Y
+    Bv, GYv = B[:, :n_exact], GY[:, :n_exact]
+    pe = ol.prior(grid, xs[ie])
+    var_ex = pe - np.einsum("mt,mt->t", Bv, GYv)
+    Bq, GYq = B[:, n_exact:], GY[:, n_exact:]
+    cov_ex = Wq.T @ Bq - Bq.T @ GYq
+    cov_ex = 0.5 * (cov_ex + cov_ex.T)
+    z = scipy.linalg.lu_solve(lu, ski.W @ ski.y, trans=1, check_finite=False)   # (G K + s^2 I)^{-1} W y
+    a_ex = grid.kuu_matmul(z)
+    mu_ex = Wv.T @ a_ex
+    sd_y = float(np.std(y))
+    rel_love = np.abs(var_g[ie] - var_ex) / var_ex
+    rel_oracle = np.abs(v_o[:n_exact] - var_ex) / var_ex
+    rel_root = np.abs(var_root_g - var_ex) / var_ex
+    dmu = np.abs(mean_g[ie] - mu_ex) / sd_y
+    out["vs_exact_ski_posterior"] = {
+        "points": int(n_exact),
+        "love_variance_rel_median": float(np.median(rel_love)), "love_variance_rel_p99": float(np.quantile(rel_love, 0.99)),
+        "oracle_love_fp64_rel_median": float(np.median(rel_oracle)),
+        "root_variance_rel_median": float(np.median(rel_root)), "root_variance_rel_p99": float(np.quantile(rel_root, 0.99)),
+        "mean_abs_err_over_std_y_max": float(np.max(dmu)), "mean_abs_err_over_std_y_median": float(np.median(dmu)),
+        "note": "exact = the SKI posterior (push-through, dense m x m LU, FP64); love = love_predict_mean_var "
+                "(k steps, FP32 cache); root = love_predict_var_root (|S^T w|^2, sampler root)"}
+    # samples: the paper's sample-covariance error, and the root against the oracle's
+    S_o, _ = ol.sampler_precompute(c_o, k=k, seed=sampler_seed)
+    Go = Wq.T @ S_o
+    cov_root_o = Go @ Go.T
+    F = samples_g[:, iq]
+    emp = np.cov(F.T)
+    s_count = samples_g.shape[0]
+    d = np.diag(cov_ex)
+    noise = np.mean(np.sqrt(2 / np.pi) * np.sqrt((np.outer(d, d) + cov_ex ** 2) / (s_count - 1)))
+    out["samples"] = {
+        "samples": int(s_count), "points": int(n_cov),
+        "sample_cov_mae_vs_exact": float(np.mean(np.abs(emp - cov_ex))),
+        "sample_cov_mae_vs_oracle_root": float(np.mean(np.abs(emp - cov_root_o))),
+        "sampling_noise_mae_expected": float(noise),
+        "mean_abs_exact_cov": float(np.mean(np.abs(cov_ex))), "mean_exact_var": float(np.mean(d)),
+        "note": "element-wise MAE of the s-sample covariance at n_cov of the sample points (the paper's "
+                "Sec. 4 sampling table measure) against the exact SKI posterior covariance and against "
+                "the oracle's rank-k' root W*^T S S^T W* (same k', seed)"}
+    out["oracle_s"] = time.perf_counter() - t0
+    return out
 
 
 def run_reference(args):
@@ -261,6 +375,7 @@ def run_gpu(args):
     w0 = time.perf_counter()
     records = []
     phases = []
+    last_seed = 1000 + args.steps - 1
     for i in range(args.steps):
         flush.zero_()
         ev, cache, smp = step(1000 + i)
@@ -346,12 +461,49 @@ def run_gpu(args):
     out = None
     if rank == 0:
         cpu = None
+        accuracy = None
         if world == 1 and not args.no_cpu:
             c = cpu_oracle(wl, n_sample=200_000)
             cpu = {"value": c["vars_per_s"], "unit": UNIT, "cores": c["cores"], "kind": "oracle",
                    "sample": (f"FP64 numpy oracle: LOVE predict on all {c['t']} test points, cache from an "
                               f"oracle pre-compute (k={wl.k}) on the first {c['n_sample']} training points "
                               f"({c['precompute_s']:.1f} s); one host thread of {c['cores_available']}")}
+            # the last step's outputs against the oracle (after timing; not part of any timed number)
+            m_acc = torch.empty(t, dtype=torch.float32, device=dev)
+            v_acc = torch.empty(t, dtype=torch.float32, device=dev)
+            love.love_predict_mean_var(cache, xs_d, out_mean=m_acc, out_var=v_acc)
+            xs_np = xs_h.double().numpy()
+            import numpy as _np
+            idx_e = _np.random.default_rng(2024).choice(t, 10_000, replace=False)[:2_000]
+            vr = love.love_predict_var_root(cache, xs_d[torch.as_tensor(idx_e, device=dev)]) if sampler[0] else None
+            torch.cuda.synchronize()
+            if sampler[0]:
+                accuracy = oracle_accuracy(wl, xs_np, xq_h.double().numpy(), v_acc.double().cpu().numpy(),
+                                           m_acc.double().cpu().numpy(), vr.double().cpu().numpy(),
+                                           smp.double().cpu().numpy(), last_seed, wl.k)
+                accuracy["dtype"] = "f32 (FP32 data and cache; the oracle FP64)"
+        # the predict kernel: algorithmic bytes per launch (d*4 + 8 + 4^d (k+1) 4 per point) over its
+        # CUDA-event time, against the measured HBM copy peak.  Its 4 MB cache stays in the 129 MB
+        # L2, so the level that binds is L1TEX/L2 (ncu percentages from the committed profile); the
+        # compulsory HBM traffic is x in, mean and var out, and one read of the cache.
+        prof = "predict_c2_ncu.md"
+        traffic = _profile_traffic(prof)
+        alg_bytes = bytes_per_pt * t
+        cache_bytes = cache.info()["m"] * cache.info()["ld"] * 4
+        comp = t * (4 * dim + 8) + cache_bytes
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_point": bytes_per_pt,
+                    "traffic": traffic,
+                    "binding_level": "l1tex/l2",
+                    "level_pct_of_peak": {"l1tex": _profile_value(prof, "l1tex_throughput_pct"),
+                                          "lts": _profile_value(prof, "lts_throughput_pct"),
+                                          "dram": _profile_value(prof, "dram_throughput_pct")},
+                    "dram_over_algorithmic": (traffic / alg_bytes) if traffic else None,
+                    "compulsory_hbm": {"bytes": comp, "time_us_at_peak": comp / (peak * 1e9) * 1e6,
+                                       "kernel_time_us": pred_ms * 1e3},
+                    "note": ("the 4 MB cache is L2-resident: achieved counts algorithmic bytes, so frac "
+                             "can exceed 1; L1TEX/L2 bind (level_pct_of_peak), HBM carries ~0.5% of "
+                             "the algorithmic bytes")}
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -372,16 +524,13 @@ def run_gpu(args):
                           "cache_dtype": "f32", "reorth": REORTH,
                           "l2": "flushed before every step and every predict timing (256 MB write)",
                           "parallelism": f"replicas x{world} (each rank: full step on its own copy)"},
-               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "peak_kind": peak_kind,
-                            "bytes_per_point": bytes_per_pt,
-                            "traffic": _profile_traffic("predict_c2_ncu.md"),
-                            "note": "cache (4 MB) is L2-resident; achieved counts algorithmic bytes"},
+               "roofline": roofline,
                "e2e": {"value": world * t / (e2e_ms * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": int(t * 4), "d2h_bytes_per_step": int(t * 8)},
                "gpu_launches": int(launches),
                "clocks": clocks, "wall_s": wall,
-               "cpu_baseline": cpu}
+               "cpu_baseline": cpu,
+               "accuracy": accuracy}
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
