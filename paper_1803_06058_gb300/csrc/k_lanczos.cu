@@ -1810,12 +1810,30 @@ love_status lanczos_run(love_ski* ski, int k, double tau, double eta, T* Q, int6
     rev.resize(2 * (size_t)k, nullptr);
     for (auto& e : rev) LOVE_CUDA(cudaEventCreate(&e));
   }
+  // 1-D grids with FP32 data: the whole product in one cooperative kernel (k_mvm.cu)
+  DevBuf fz(ski->alloc, s);
+  bool fused = sizeof(T) == 4 && dim == 1 && !gh.additive && fz.get(ski_mvm_fused_work_bytes(ski));
+  if (fused) {
+    const love_status fr = ski_mvm_fused_reset(ski, fz.p, s);
+    if (fr == LOVE_ERR_UNSUPPORTED) fused = false;
+    else LOVE_TRY(fr);
+  }
+  unsigned int fgen = 0;
   for (int j = 0; j < k; ++j) {
-    // u = W q_j (q_j stored unnormalised, scaled by scal[j])
-    LOVE_TRY(scatter_any<T>(ski, Q + (int64_t)j * ldq, st->scal + j, T(1), u1, s));
-    LOVE_TRY(kuu_apply<T>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
-    // y = W^T u + s^2 q_j (q_j normalised in place)
-    LOVE_TRY(lanczos_gather_any<T>(ski, u2, Q + (int64_t)j * ldq, y.as<T>(), st, j, s));
+    if (fused) {
+      const love_status fr = ski_mvm_fused(ski, reinterpret_cast<float*>(Q + (int64_t)j * ldq), st->scal + j,
+                                           &st->done, reinterpret_cast<float*>(y.as<T>()), fz.p, fgen, s);
+      if (fr == LOVE_ERR_UNSUPPORTED && j == 0) fused = false;
+      else LOVE_TRY(fr);
+      fgen += 4;
+    }
+    if (!fused) {
+      // u = W q_j (q_j stored unnormalised, scaled by scal[j])
+      LOVE_TRY(scatter_any<T>(ski, Q + (int64_t)j * ldq, st->scal + j, T(1), u1, s));
+      LOVE_TRY(kuu_apply<T>(gh, ski->fft, u1, u2, 1, gh.m, fw.p, -1, s));
+      // y = W^T u + s^2 q_j (q_j normalised in place)
+      LOVE_TRY(lanczos_gather_any<T>(ski, u2, Q + (int64_t)j * ldq, y.as<T>(), st, j, s));
+    }
     ta.j = j;
     ta.y = y.as<T>();
     if (reorth_ms) LOVE_CUDA(cudaEventRecord(rev[2 * (size_t)j], s));

@@ -255,14 +255,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // grid-wide barrier of a cooperative launch (all CTAs co-resident), bounded
 // like every other wait: after ~1 s a CTA flags LOVE_ERR_TIMEOUT, raises the
 // abort word (so the others stop waiting too) and the call returns false; the
-// kernel must then return without entering another barrier.  The counters live
-// in global memory, zeroed before the launch.  Thread 0 of each CTA arrives
-// with a release add after the CTA's bar.sync and waits with acquire loads, so
-// every global write made before the barrier by any CTA is visible after it
-// (data that other CTAs wrote must still be read past L1: ld.global.cg).
+// kernel must then return without entering another barrier.  The arrival
+// counter lives in global memory, zeroed before the first barrier of a run, and
+// only grows: barrier number `gen` (counted from 0 over the run) is passed when
+// it reaches (gen + 1) x gridDim.x.  After the CTA's bar.sync, thread 0 arrives
+// with a release add (red.release: cumulative over the CTA's writes) and polls
+// with acquire loads, which read the last add of a release sequence holding
+// every arrival: every global write made before the barrier by any CTA is
+// visible after it (data other CTAs wrote must still be read past L1,
+// ld.global.cg).
 struct GridSync {
-  unsigned int count;   // CTAs arrived at the current barrier
-  unsigned int gen;     // barriers completed
+  unsigned int count;   // arrivals since the run's first barrier
+  unsigned int gen;     // unused (layout kept)
   unsigned int abort;   // a CTA gave up waiting
   unsigned int pad;
 };
@@ -272,13 +276,8 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
-  unsigned int old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // `gen` is the caller's count of barriers passed (the same in every CTA)
@@ -287,14 +286,11 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned int& gen, De
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int g = gen;
-    __threadfence();
-    if (atom_add_acq_rel_gpu(&gs->count, 1u) == gridDim.x - 1) {
-      gs->count = 0u;                  // ordered before the release below
-      st_release_gpu(&gs->gen, g + 1u);
-    } else {
+    const unsigned int target = (gen + 1u) * gridDim.x;
+    red_release_add_gpu(&gs->count, 1u);
+    if ((int)(ld_acquire_gpu(&gs->count) - target) < 0) {
       const uint64_t t0 = global_timer_ns();
-      while (ld_acquire_gpu(&gs->gen) == g) {
+      while ((int)(ld_acquire_gpu(&gs->count) - target) < 0) {
         if (ld_acquire_gpu(&gs->abort)) {
           ok = 0;
           break;
@@ -307,7 +303,6 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, unsigned int& gen, De
         }
       }
     }
-    __threadfence();
     gb_ok = ok;
   }
   __syncthreads();
@@ -483,6 +478,17 @@ template <typename T>
 love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
                             int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
                             double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s);
+// k_mvm.cu: the SKI product of one Lanczos step (1-D grid, FP32 data) as one
+// cooperative kernel: y = W^T K_UU W q_j + s^2 q_j, q_j scaled by *scal in place;
+// a no-op once *done.  work: ski_mvm_fused_work_bytes(ski) bytes, set up once per
+// run by ski_mvm_fused_reset (df twiddle and spectrum tables, zeroed barrier
+// counters); gen0: the barriers the run's
+// earlier products completed (4 per product).  LOVE_ERR_UNSUPPORTED where the
+// grid or the device does not allow it.
+size_t ski_mvm_fused_work_bytes(const love_ski* ski);
+love_status ski_mvm_fused_reset(const love_ski* ski, void* work, cudaStream_t s);
+love_status ski_mvm_fused(love_ski* ski, float* qj, const double* scal, const int* done, float* y, void* work,
+                          unsigned int gen0, cudaStream_t s);
 // k_sampler.cu: the same run as one persistent cooperative kernel (1-D grids
 // whose per-CTA share fits in shared memory); LOVE_ERR_UNSUPPORTED otherwise
 template <typename T>
