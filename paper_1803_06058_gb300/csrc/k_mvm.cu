@@ -368,16 +368,20 @@ love_status ski_mvm_fused(love_ski* ski, float* qj, const double* scal, const in
                                                 dim3(MVM_THREADS), args, smem, s));
 }
 
-// the barrier counters of a run's fused products (zeroed once per run)
-love_status ski_mvm_fused_reset(const love_ski* ski, void* work, cudaStream_t s) {
-  const FftPlan& p = ski->fft[0];
+love_status fft_df_tables(const FftPlan& p, float4* twdf, float2* lamdf, cudaStream_t s) {
   const int N = (int)p.N;
   if (!p.tw_d || !p.lam_d) return LOVE_ERR_UNSUPPORTED;
   LOVE_COUNT_LAUNCH();
-  k_mvm_tables<<<ceil_div(N, 256), 256, 0, s>>>((const double2*)p.tw_d, (const double*)p.lam_d, N,
-                                                 (float4*)((char*)work + sizeof(dfc) * (size_t)N),
-                                                 (float2*)((char*)work + sizeof(dfc) * 2 * (size_t)N));
+  k_mvm_tables<<<ceil_div(N, 256), 256, 0, s>>>((const double2*)p.tw_d, (const double*)p.lam_d, N, twdf, lamdf);
   LOVE_LAUNCH_CHECK();
+  return LOVE_OK;
+}
+
+// the df tables and the barrier counters of a run's fused products (once per run)
+love_status ski_mvm_fused_reset(const love_ski* ski, void* work, cudaStream_t s) {
+  const FftPlan& p = ski->fft[0];
+  const size_t N = (size_t)p.N;
+  LOVE_TRY(fft_df_tables(p, (float4*)((char*)work + sizeof(dfc) * N), (float2*)((char*)work + sizeof(dfc) * 2 * N), s));
   return cuda_check(cudaMemsetAsync((char*)work + mvm_gs_offset(ski), 0, sizeof(GridSync), s));
 }
 

@@ -4,9 +4,11 @@
 // k' steps of Lanczos with full reorthogonalisation (classical Gram-Schmidt
 // twice, as the main run and the oracle) on the m x m operator
 //     M = K_UU - Rt Rt^T        (K_UU Toeplitz, Rt m x k)
-// from the SplitMix64 Rademacher probe.  All arithmetic is FP64: the work is
-// m-sized, and M's two terms cancel to ~1e-7 of their size on the 1-D n = 1e6
-// workload.  The multi-launch form of the same run (k_lanczos.cu) spends ~8
+// from the SplitMix64 Rademacher probe.  The arithmetic is double-float
+// (~2^-48 relative, on the FP32 pipes), with the per-step scalars in FP64: M's
+// two terms cancel to ~1e-7 of their size on the 1-D n = 1e6 workload, so FP32
+// alone would leave nothing of M.  The multi-launch form of the same run (k_lanczos.cu,
+// FP64) spends ~8
 // short launches per step, each latency-bound on m = 1e4 vectors; here one
 // launch runs every step, with bounded grid barriers between its phases.
 //
@@ -62,14 +64,14 @@ struct SamplerArgs {
   int64_t ldq;
   int N, N1, N2, logN1, logN2, logNB;
   int NB, FB, R2;        // n1 per CTA, k2 rows per CTA in pass B, rows per n1
-  const double2* tw;     // W_N^j
-  const double* lam;     // circulant spectrum / N
-  double2* work;         // N complex
+  const float4* twdf;    // W_N^j, df complex
+  const float2* lamdf;   // circulant spectrum / N, df
+  float4* work;          // N df complex
   float2* part_t;        // G x KP df pairs: partial sums of Rt^T q
   float2* part_c1;       // G x KP df pairs
   float2* part_c2;       // G x KP df pairs
-  double* part_nn;       // G
-  double* tvec;          // k
+  float2* part_nn;       // G df pairs
+  float2* tvec;          // k df pairs
   double* alpha;         // ks
   double* beta;          // ks
   int* k_eff;
@@ -86,53 +88,94 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// GB300 runs FP64 at a small fraction of its FP32 rate, so the run keeps its
+// vectors, products and transforms in double-float (a value as an unevaluated
+// float pair hi + lo, ~2^-48 relative; error-free transformations on the FP32
+// pipes): FP64 is left to the per-step scalars (alpha_j, beta_j, the stop rule)
+// and to the rows of Q' written out.
+
+// sum of exact products of double-float factors (Dot2 with the cross terms)
+struct DotDF {
+  float s, c;
+  __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+  __device__ __forceinline__ void add(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float pe = fmaf(a.x, b.x, -p);
+    pe = fmaf(a.x, b.y, pe);
+    pe = fmaf(a.y, b.x, pe);
+    const float t = s + p;
+    const float z = t - s;
+    c += pe + ((s - (t - z)) + (p - z));
+    s = t;
+  }
+  __device__ __forceinline__ df get() const { return fast_two_sum(s, c); }
+};
+__device__ __forceinline__ df ld_df(const float2 v) { return df{v.x, v.y}; }
+__device__ __forceinline__ float2 st_df(const df v) { return make_float2(v.hi, v.lo); }
+__device__ __forceinline__ df warp_sum_df(df v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.hi, o), l = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, df{h, l});
+  }
   return v;
 }
+__device__ __forceinline__ dfc ld_dfc(const float4* p) {
+  const float4 v = __ldcg(p);
+  return dfc{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ void st_dfc(float4* p, const dfc& v) { __stcg(p, make_float4(v.rh, v.rl, v.ih, v.il)); }
+// a complex double-float times a real one
+__device__ __forceinline__ dfc dfc_scale(const dfc& a, float2 l) {
+  const df re = df_mul(df{a.rh, a.rl}, ld_df(l)), im = df_mul(df{a.ih, a.il}, ld_df(l));
+  return dfc{re.hi, re.lo, im.hi, im.lo};
+}
+// the twiddles W_L^j (j < L/2) of one transform length from the df table of W_N
+__device__ __forceinline__ void load_twiddles_tab(dfc* w, int L, const float4* __restrict__ twdf, int N) {
+  const int step = N / L;
+  for (int j = threadIdx.x; j < (L >> 1); j += blockDim.x) {
+    const float4 v = twdf[(int64_t)j * step];
+    w[j] = dfc{v.x, v.y, v.z, v.w};
+  }
+}
 
-// This part runs FP64 at a small fraction of its FP32 rate, and the run is
-// bound by the FP64 pipe: the dots below keep their FP64 work to one FMA per
-// row and column (plus two adds per column), and the per-CTA partials that
-// every CTA must add up go out as double-float pairs, summed on the FP32 pipes
-// (error-free transformations, ~2^-48 relative).
-
-// part[i] = sum over own rows of Ms[i][lr] v[lr] for i < ncols, as a df pair:
-// 4 threads per column take every 4th row, then two shuffles add them
-__device__ __forceinline__ void cols_dot(const double* Ms, int RL, int ncols, const double* v, float2* part) {
+// part[i] = sum over own rows of Ms[i][lr] v[lr] for i < ncols: 4 threads per
+// column take every 4th row, then two shuffles add them
+__device__ __forceinline__ void cols_dot(const float2* Ms, int RL, int ncols, const float2* v, float2* part) {
   const int sub = threadIdx.x & 3;
   for (int i = threadIdx.x >> 2; i < ((ncols + 7) & ~7); i += SAMP_THREADS / 4) {
-    double s = 0.0;
+    DotDF acc;
+    acc.zero();
     if (i < ncols) {
-      const double* col = Ms + (size_t)i * RL;
-      for (int lr = sub; lr < RL; lr += 4) s = fma(col[lr], v[lr], s);
+      const float2* col = Ms + (size_t)i * RL;
+      for (int lr = sub; lr < RL; lr += 4) acc.add(col[lr], v[lr]);
     }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (sub == 0 && i < ncols) {
-      const float hi = (float)s;
-      __stcg(part + i, make_float2(hi, (float)(s - (double)hi)));
+    df r = acc.get();
+    for (int o = 1; o <= 2; o <<= 1) {
+      const float h = __shfl_xor_sync(0xffffffffu, r.hi, o), l = __shfl_xor_sync(0xffffffffu, r.lo, o);
+      r = df_add(r, df{h, l});
     }
+    if (sub == 0 && i < ncols) __stcg(part + i, st_df(r));
   }
 }
 
 // out[lr] = base[lr] - sum_{i < ncols} Ms[i][lr] c[i] for own rows: NG groups of
 // RL threads split the columns, the group partials are added in group order
-__device__ __forceinline__ void rows_sub(const double* Ms, int RL, int ncols, const double* c, const double* base,
-                                         double* out, double* scratch) {
+__device__ __forceinline__ void rows_sub(const float2* Ms, int RL, int ncols, const float2* c, const float2* base,
+                                         float2* out, float2* scratch) {
   const int NG = SAMP_THREADS / RL;   // RL <= SAMP_THREADS is enforced on the host
   const int g = threadIdx.x / RL, lr = threadIdx.x - g * RL;
   if (g < NG) {
-    double s = 0.0;
-    for (int i = g; i < ncols; i += NG) s = fma(Ms[(size_t)i * RL + lr], c[i], s);
-    scratch[g * RL + lr] = s;
+    DotDF acc;
+    acc.zero();
+    for (int i = g; i < ncols; i += NG) acc.add(Ms[(size_t)i * RL + lr], c[i]);
+    scratch[g * RL + lr] = st_df(acc.get());
   }
   __syncthreads();
   for (int r = threadIdx.x; r < RL; r += SAMP_THREADS) {
-    double s = 0.0;
-    for (int q = 0; q < NG; ++q) s += scratch[q * RL + r];
-    out[r] = base[r] - s;
+    df s = ld_df(scratch[r]);
+    for (int q = 1; q < NG; ++q) s = df_add(s, ld_df(scratch[q * RL + r]));
+    out[r] = st_df(df_add(ld_df(base[r]), df_neg(s)));
   }
   __syncthreads();
 }
@@ -140,8 +183,7 @@ __device__ __forceinline__ void rows_sub(const double* Ms, int RL, int ncols, co
 // out[i] = sum_b part[b][i] for i < n (df pairs from every CTA), the same in
 // every CTA: thread (q, i) adds the partials of CTAs q, q + 4, ... in order
 // (all its loads issued first), then thread i adds the four quarter sums
-
-__device__ __forceinline__ void reduce_parts(const float2* part, int G, int n, double* out, float2* scratch) {
+__device__ __forceinline__ void reduce_parts(const float2* part, int G, int n, float2* out, float2* scratch) {
   for (int t = threadIdx.x; t < RQ * n; t += SAMP_THREADS) {
     const int q = t / n, i = t - q * n;
     df acc{0.f, 0.f};
@@ -149,25 +191,25 @@ __device__ __forceinline__ void reduce_parts(const float2* part, int G, int n, d
     for (; bb + 3 * RQ < G; bb += 4 * RQ) {
       float2 p0 = __ldcg(part + (size_t)bb * KP + i), p1 = __ldcg(part + (size_t)(bb + RQ) * KP + i);
       float2 p2 = __ldcg(part + (size_t)(bb + 2 * RQ) * KP + i), p3 = __ldcg(part + (size_t)(bb + 3 * RQ) * KP + i);
-      acc = df_add(acc, df{p0.x, p0.y});
-      acc = df_add(acc, df{p1.x, p1.y});
-      acc = df_add(acc, df{p2.x, p2.y});
-      acc = df_add(acc, df{p3.x, p3.y});
+      acc = df_add(acc, ld_df(p0));
+      acc = df_add(acc, ld_df(p1));
+      acc = df_add(acc, ld_df(p2));
+      acc = df_add(acc, ld_df(p3));
     }
-    for (; bb < G; bb += RQ) {
-      const float2 p = __ldcg(part + (size_t)bb * KP + i);
-      acc = df_add(acc, df{p.x, p.y});
-    }
-    scratch[t] = make_float2(acc.hi, acc.lo);
+    for (; bb < G; bb += RQ) acc = df_add(acc, ld_df(__ldcg(part + (size_t)bb * KP + i)));
+    scratch[t] = st_df(acc);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += SAMP_THREADS) {
-    df acc{scratch[i].x, scratch[i].y};
-    for (int q = 1; q < RQ; ++q) acc = df_add(acc, df{scratch[q * n + i].x, scratch[q * n + i].y});
-    out[i] = (double)acc.hi + (double)acc.lo;
+    df acc = ld_df(scratch[i]);
+    for (int q = 1; q < RQ; ++q) acc = df_add(acc, ld_df(scratch[q * n + i]));
+    out[i] = st_df(acc);
   }
   __syncthreads();
 }
+
+template <typename RT> __device__ __forceinline__ float2 to_df(RT v);
+template <> __device__ __forceinline__ float2 to_df<float>(float v) { return make_float2(v, 0.f); }
 
 template <typename RT>
 __global__ void __launch_bounds__(SAMP_THREADS, 1) k_sampler_lanczos(const __grid_constant__ SamplerArgs<RT> a) {
@@ -176,34 +218,34 @@ __global__ void __launch_bounds__(SAMP_THREADS, 1) k_sampler_lanczos(const __gri
   const int NB = a.NB, R2 = a.R2, RL = NB * R2;
   const int n1_0 = b * NB;
   // shared memory: x [N / G] complex, wA [N2 / 2], wB [N1 / 2] (complex first: 16-byte
-  // aligned), scratch [SAMP_THREADS], cvec [KP], tv [KP], v [RL], kq [RL], Qs [ks][RL],
-  // then Rs [k][RL] (RT)
-  double2* x = reinterpret_cast<double2*>(smem_raw);
-  double2* wA = x + a.N / G;
-  double2* wB = wA + a.N2 / 2;
-  double* scratch = reinterpret_cast<double*>(wB + a.N1 / 2);   // SCRATCH doubles
-  double* cvec = scratch + SCRATCH;
-  double* tv = cvec + KP;
-  double* v = tv + KP;
-  double* kq = v + RL;
-  double* Qs = kq + RL;
-  double* Rs = Qs + (size_t)a.ks * RL;   // Rt's own rows, in FP64
+  // aligned), scratch [SCRATCH], cvec [KP], tv [KP], v [RL], kq [RL], Qs [ks][RL],
+  // then Rs [k][RL]; every real entry a df pair
+  dfc* x = reinterpret_cast<dfc*>(smem_raw);
+  dfc* wA = x + a.N / G;
+  dfc* wB = wA + a.N2 / 2;
+  float2* scratch = reinterpret_cast<float2*>(wB + a.N1 / 2);
+  float2* cvec = scratch + SCRATCH;
+  float2* tv = cvec + KP;
+  float2* v = tv + KP;
+  float2* kq = v + RL;
+  float2* Qs = kq + RL;
+  float2* Rs = Qs + (size_t)a.ks * RL;   // Rt's own rows
   __shared__ double s_beta, s_amax;
   __shared__ int s_stop;
 
-  load_twiddles(wA, a.N2, a.tw, a.N);
-  load_twiddles(wB, a.N1, a.tw, a.N);
+  load_twiddles_tab(wA, a.N2, a.twdf, a.N);
+  load_twiddles_tab(wB, a.N1, a.twdf, a.N);
   // own rows of Rt (zero past m) and of the probe v_0 (Rademacher, 1 / sqrt(m) after scaling)
   for (int i = tid; i < a.k * RL; i += SAMP_THREADS) {
     const int c = i / RL, lr = i - c * RL;
     const int f = lr / R2, n2 = lr - f * R2;
     const int r = n1_0 + f + a.N1 * n2;
-    Rs[i] = r < a.m ? (double)a.Rt[(int64_t)c * a.ldr + r] : 0.0;
+    Rs[i] = r < a.m ? to_df<RT>(a.Rt[(int64_t)c * a.ldr + r]) : make_float2(0.f, 0.f);
   }
   for (int lr = tid; lr < RL; lr += SAMP_THREADS) {
     const int f = lr / R2, n2 = lr - f * R2;
     const int r = n1_0 + f + a.N1 * n2;
-    v[lr] = r < a.m ? ((splitmix64_at(a.seed, (uint64_t)r) & 1ull) ? 1.0 : -1.0) : 0.0;
+    v[lr] = make_float2(r < a.m ? ((splitmix64_at(a.seed, (uint64_t)r) & 1ull) ? 1.f : -1.f) : 0.f, 0.f);
   }
   if (tid == 0) {
     s_beta = sqrt((double)a.m);
@@ -215,29 +257,28 @@ __global__ void __launch_bounds__(SAMP_THREADS, 1) k_sampler_lanczos(const __gri
   int keff = a.ks;
   for (int j = 0; j < a.ks; ++j) {
     // ---- 1: q_j, pass A, partials of Rt^T q_j
-    const double inv = 1.0 / s_beta;
-    double* qj = Qs + (size_t)j * RL;
+    const df inv = df_from_double(1.0 / s_beta);
+    float2* qj = Qs + (size_t)j * RL;
     for (int lr = tid; lr < RL; lr += SAMP_THREADS) {
-      const double q = v[lr] * inv;
-      qj[lr] = q;
+      const df q = df_mul(ld_df(v[lr]), inv);
+      qj[lr] = st_df(q);
       const int f = lr / R2, n2 = lr - f * R2;
       const int r = n1_0 + f + a.N1 * n2;
-      if (r < a.m) a.Q[(int64_t)j * a.ldq + r] = q;
+      if (r < a.m) a.Q[(int64_t)j * a.ldq + r] = df_to_double(q);
     }
     __syncthreads();
     for (int t = tid; t < (a.N2 << a.logNB); t += SAMP_THREADS) {
       const int f = t & (NB - 1), n2 = t >> a.logNB;
-      double2 c;
-      c.x = n2 < R2 ? qj[f * R2 + n2] : 0.0;
-      c.y = 0.0;
-      x[(bitrev(n2, a.logN2) << a.logNB) + f] = c;
+      const float2 q = n2 < R2 ? qj[f * R2 + n2] : make_float2(0.f, 0.f);
+      x[(bitrev(n2, a.logN2) << a.logNB) + f] = dfc{q.x, q.y, 0.f, 0.f};
     }
     __syncthreads();
-    fft_dit(x, a.N2, a.logNB, wA, false);
+    fft_dit_df(x, a.N2, a.logNB, wA, false);
     for (int t = tid; t < (a.N2 << a.logNB); t += SAMP_THREADS) {
       const int f = t & (NB - 1), k2 = t >> a.logNB;
       const int n1 = n1_0 + f;
-      __stcg(a.work + (int64_t)k2 * a.N1 + n1, cmul(x[t], a.tw[((int64_t)n1 * k2) & (a.N - 1)]));
+      const float4 w = a.twdf[((int64_t)n1 * k2) & (a.N - 1)];
+      st_dfc(a.work + (int64_t)k2 * a.N1 + n1, dfc_mul(x[t], dfc{w.x, w.y, w.z, w.w}, false));
     }
     cols_dot(Rs, RL, a.k, qj, a.part_t + (size_t)b * KP);
     if (!grid_barrier(a.gs, gen, a.status)) return;
@@ -247,21 +288,19 @@ __global__ void __launch_bounds__(SAMP_THREADS, 1) k_sampler_lanczos(const __gri
       const int k2_0 = b * FB;
       for (int t = tid; t < (a.N1 << logFB); t += SAMP_THREADS) {
         const int n1 = t & (a.N1 - 1), f = t >> a.logN1;
-        x[(bitrev(n1, a.logN1) << logFB) + f] = __ldcg(a.work + (int64_t)(k2_0 + f) * a.N1 + n1);
+        x[(bitrev(n1, a.logN1) << logFB) + f] = ld_dfc(a.work + (int64_t)(k2_0 + f) * a.N1 + n1);
       }
       __syncthreads();
-      fft_dit(x, a.N1, logFB, wB, false);
+      fft_dit_df(x, a.N1, logFB, wB, false);
       for (int t = tid; t < (a.N1 << logFB); t += SAMP_THREADS) {
         const int f = t & (FB - 1), k1 = t >> logFB;
-        const double l = a.lam[(k2_0 + f) + a.N2 * k1];
-        x[t].x *= l;
-        x[t].y *= l;
+        x[t] = dfc_scale(x[t], a.lamdf[(k2_0 + f) + a.N2 * k1]);
       }
       __syncthreads();
-      fft_dif(x, a.N1, logFB, wB, true);
+      fft_dif_df(x, a.N1, logFB, wB, true);
       for (int t = tid; t < (a.N1 << logFB); t += SAMP_THREADS) {
         const int n1 = t & (a.N1 - 1), f = t >> a.logN1;
-        __stcg(a.work + (int64_t)(k2_0 + f) * a.N1 + n1, x[(bitrev(n1, a.logN1) << logFB) + f]);
+        st_dfc(a.work + (int64_t)(k2_0 + f) * a.N1 + n1, x[(bitrev(n1, a.logN1) << logFB) + f]);
       }
     }
     for (int c = b + G * (tid >> 5); c < a.k && (tid >> 5) < SAMP_WARPS; c += G * SAMP_WARPS) {
@@ -269,16 +308,9 @@ __global__ void __launch_bounds__(SAMP_THREADS, 1) k_sampler_lanczos(const __gri
       // CTAs l, l + 32, ..., then a fixed df butterfly across the lanes
       const int lane = tid & 31;
       df acc{0.f, 0.f};
-      for (int bb = lane; bb < G; bb += 32) {
-        const float2 p = __ldcg(a.part_t + (size_t)bb * KP + c);
-        acc = df_add(acc, df{p.x, p.y});
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float h = __shfl_xor_sync(0xffffffffu, acc.hi, o), l = __shfl_xor_sync(0xffffffffu, acc.lo, o);
-        acc = df_add(acc, df{h, l});
-      }
-      if (lane == 0) __stcg(a.tvec + c, (double)acc.hi + (double)acc.lo);
+      for (int bb = lane; bb < G; bb += 32) acc = df_add(acc, ld_df(__ldcg(a.part_t + (size_t)bb * KP + c)));
+      acc = warp_sum_df(acc);
+      if (lane == 0) __stcg(a.tvec + c, st_df(acc));
     }
     if (!grid_barrier(a.gs, gen, a.status)) return;
     // ---- 3: pass C -> K_UU q_j on own rows; v = K_UU q_j - Rt t; partials of c1
@@ -286,54 +318,55 @@ __global__ void __launch_bounds__(SAMP_THREADS, 1) k_sampler_lanczos(const __gri
     for (int t = tid; t < (a.N2 << a.logNB); t += SAMP_THREADS) {
       const int f = t & (NB - 1), k2 = t >> a.logNB;
       const int n1 = n1_0 + f;
-      double2 w = a.tw[((int64_t)n1 * k2) & (a.N - 1)];
-      w.y = -w.y;
-      x[t] = cmul(__ldcg(a.work + (int64_t)k2 * a.N1 + n1), w);
+      const float4 w = a.twdf[((int64_t)n1 * k2) & (a.N - 1)];
+      x[t] = dfc_mul(ld_dfc(a.work + (int64_t)k2 * a.N1 + n1), dfc{w.x, w.y, w.z, w.w}, true);
     }
     __syncthreads();
-    fft_dif(x, a.N2, a.logNB, wA, true);
+    fft_dif_df(x, a.N2, a.logNB, wA, true);
     for (int lr = tid; lr < RL; lr += SAMP_THREADS) {
       const int f = lr / R2, n2 = lr - f * R2;
       const int r = n1_0 + f + a.N1 * n2;
-      kq[lr] = r < a.m ? x[(bitrev(n2, a.logN2) << a.logNB) + f].x : 0.0;
+      const dfc& o = x[(bitrev(n2, a.logN2) << a.logNB) + f];
+      kq[lr] = r < a.m ? make_float2(o.rh, o.rl) : make_float2(0.f, 0.f);
     }
     __syncthreads();
     rows_sub(Rs, RL, a.k, tv, kq, v, scratch);
     cols_dot(Qs, RL, j + 1, v, a.part_c1 + (size_t)b * KP);
     if (!grid_barrier(a.gs, gen, a.status)) return;
     // ---- 4: c1; alpha_j; v -= Q_j c1; partials of c2
-    reduce_parts(a.part_c1, G, j + 1, cvec, reinterpret_cast<float2*>(scratch));
-    const double alpha_j = cvec[j];
+    reduce_parts(a.part_c1, G, j + 1, cvec, scratch);
+    const double alpha_j = df_to_double(ld_df(cvec[j]));
     rows_sub(Qs, RL, j + 1, cvec, v, v, scratch);
     cols_dot(Qs, RL, j + 1, v, a.part_c2 + (size_t)b * KP);
     if (!grid_barrier(a.gs, gen, a.status)) return;
     // ---- 5: c2; v -= Q_j c2; partial of |v|^2
-    reduce_parts(a.part_c2, G, j + 1, cvec, reinterpret_cast<float2*>(scratch));
+    reduce_parts(a.part_c2, G, j + 1, cvec, scratch);
     rows_sub(Qs, RL, j + 1, cvec, v, v, scratch);
     {
       const int lane = tid & 31, w = tid >> 5;
-      double s = 0.0;
-      for (int lr = tid; lr < RL; lr += SAMP_THREADS) s = fma(v[lr], v[lr], s);
-      s = warp_sum(s);
-      if (lane == 0) scratch[w] = s;
+      DotDF acc;
+      acc.zero();
+      for (int lr = tid; lr < RL; lr += SAMP_THREADS) acc.add(v[lr], v[lr]);
+      const df s = warp_sum_df(acc.get());
+      if (lane == 0) scratch[w] = st_df(s);
       __syncthreads();
       if (tid == 0) {
-        double t = 0.0;
-        for (int q = 0; q < SAMP_WARPS; ++q) t += scratch[q];
-        __stcg(a.part_nn + b, t);
+        df t = ld_df(scratch[0]);
+        for (int q = 1; q < SAMP_WARPS; ++q) t = df_add(t, ld_df(scratch[q]));
+        __stcg(a.part_nn + b, st_df(t));
       }
     }
     if (!grid_barrier(a.gs, gen, a.status)) return;
     // ---- beta_j and the stop rule (identical in every CTA)
     if (tid < 32) {
-      double nn = 0.0;
-      for (int bb = tid; bb < G; bb += 32) nn += __ldcg(a.part_nn + bb);
-      nn = warp_sum(nn);
-      if (tid == 0) scratch[0] = nn;
+      df nn{0.f, 0.f};
+      for (int bb = tid; bb < G; bb += 32) nn = df_add(nn, ld_df(__ldcg(a.part_nn + bb)));
+      nn = warp_sum_df(nn);
+      if (tid == 0) scratch[0] = st_df(nn);
     }
     __syncthreads();
     if (tid == 0) {
-      const double beta_j = sqrt(scratch[0]);
+      const double beta_j = sqrt(df_to_double(ld_df(scratch[0])));
       s_amax = fmax(s_amax, fabs(alpha_j));
       if (b == 0) {
         a.alpha[j] = alpha_j;
@@ -368,8 +401,8 @@ int ilog2i(int v) {
 }
 
 size_t sampler_smem_bytes(int ks, int k, int RL, int N, int G, int N1, int N2) {
-  return sizeof(double2) * ((size_t)N / G + N2 / 2 + N1 / 2) +
-         sizeof(double) * (SCRATCH + 2 * (size_t)KP + 2 * (size_t)RL + (size_t)(ks + k) * RL);
+  return sizeof(dfc) * ((size_t)N / G + N2 / 2 + N1 / 2) +
+         sizeof(float2) * (SCRATCH + 2 * (size_t)KP + 2 * (size_t)RL + (size_t)(ks + k) * RL);
 }
 
 }  // namespace
@@ -378,7 +411,9 @@ template <typename T>
 love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt,
                                   int64_t ldr, int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq,
                                   double* alpha_h, double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s) {
-  if (gh.dim != 1 || gh.additive) return LOVE_ERR_UNSUPPORTED;
+  // FP64 caches keep FP64 Lanczos vectors (the multi-launch run): double-float
+  // moves their late sampler columns by ~1e-7 relative
+  if (gh.dim != 1 || gh.additive || sizeof(T) != sizeof(float)) return LOVE_ERR_UNSUPPORTED;
   if (ks < 1 || ks > LOVE_MAX_K || k < 1 || k > LOVE_MAX_K) return LOVE_ERR_ARG;
   const FftPlan& p = fft[0];
   const int m = (int)gh.m;
@@ -406,8 +441,10 @@ love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const 
   LOVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sampler_lanczos<T>, SAMP_THREADS, smem));
   if (per_sm < 1 || (int64_t)per_sm * num_sms() < G) return LOVE_ERR_UNSUPPORTED;
 
-  // work: N complex | 3 G KP partials | G | k | ks alpha | ks beta | k_eff | GridSync
-  const size_t off_part = sizeof(double2) * (size_t)N;
+  // work: N df complex | N df twiddles | N df spectrum | 3 G KP partials | G | k |
+  // ks alpha | ks beta | k_eff | GridSync
+  const size_t off_tab = sizeof(float4) * (size_t)N;
+  const size_t off_part = off_tab + (sizeof(float4) + sizeof(float2)) * (size_t)N;
   const size_t n_dbl = 3 * (size_t)G * KP + G + KP + 2 * (size_t)KP;
   const size_t off_int = off_part + sizeof(double) * n_dbl;
   const size_t bytes = off_int + 64 + sizeof(GridSync);
@@ -430,16 +467,16 @@ love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const 
   a.NB = NB;
   a.FB = FB;
   a.R2 = R2;
-  a.tw = (const double2*)p.tw_d;
-  a.lam = (const double*)p.lam_d;
-  a.work = (double2*)w;
+  a.work = (float4*)w;
+  a.twdf = (const float4*)(w + off_tab);
+  a.lamdf = (const float2*)(w + off_tab + sizeof(float4) * (size_t)N);
   double* d = (double*)(w + off_part);
   a.part_t = reinterpret_cast<float2*>(d);   // a float2 is one double's bytes
   a.part_c1 = a.part_t + (size_t)G * KP;
   a.part_c2 = a.part_c1 + (size_t)G * KP;
-  a.part_nn = d + 3 * (size_t)G * KP;
+  a.part_nn = a.part_c2 + (size_t)G * KP;
   a.tvec = a.part_nn + G;
-  a.alpha = a.tvec + KP;
+  a.alpha = d + 3 * (size_t)G * KP + G + KP;
   a.beta = a.alpha + KP;
   a.k_eff = (int*)(w + off_int);
   a.gs = (GridSync*)(w + off_int + 64);
@@ -447,7 +484,8 @@ love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const 
   a.tau = tau;
   a.status = status;
   // rows m .. ldq of Q' are not written: the root kernels read rows below m only
-  love_status rc = cuda_check(cudaMemsetAsync(w + off_int, 0, 64 + sizeof(GridSync), s));
+  love_status rc = fft_df_tables(p, (float4*)(w + off_tab), (float2*)(w + off_tab + sizeof(float4) * (size_t)N), s);
+  if (rc == LOVE_OK) rc = cuda_check(cudaMemsetAsync(w + off_int, 0, 64 + sizeof(GridSync), s));
   if (rc == LOVE_OK) rc = cuda_check(cudaMemsetAsync(a.alpha, 0, sizeof(double) * 2 * KP, s));
   if (rc == LOVE_OK) {
     void* args[] = {(void*)&a};
@@ -472,8 +510,11 @@ love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const 
 template love_status sampler_lanczos_fused<float>(const GridHost&, const FftPlan*, const Allocator&, const float*,
                                                   int64_t, int, int, uint64_t, double, double*, int64_t, double*,
                                                   double*, int*, DevStatus*, cudaStream_t);
-template love_status sampler_lanczos_fused<double>(const GridHost&, const FftPlan*, const Allocator&, const double*,
-                                                   int64_t, int, int, uint64_t, double, double*, int64_t, double*,
-                                                   double*, int*, DevStatus*, cudaStream_t);
+template <>
+love_status sampler_lanczos_fused<double>(const GridHost&, const FftPlan*, const Allocator&, const double*, int64_t,
+                                          int, int, uint64_t, double, double*, int64_t, double*, double*, int*,
+                                          DevStatus*, cudaStream_t) {
+  return LOVE_ERR_UNSUPPORTED;
+}
 
 }  // namespace love

@@ -485,6 +485,9 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
 // counters); gen0: the barriers the run's
 // earlier products completed (4 per product).  LOVE_ERR_UNSUPPORTED where the
 // grid or the device does not allow it.
+// the circulant's twiddles W_N^j and spectrum lambda_j / N as double-float
+// tables (twdf: {re.hi, re.lo, im.hi, im.lo}; lamdf: {hi, lo}), N entries each
+love_status fft_df_tables(const FftPlan& p, float4* twdf, float2* lamdf, cudaStream_t s);
 size_t ski_mvm_fused_work_bytes(const love_ski* ski);
 love_status ski_mvm_fused_reset(const love_ski* ski, void* work, cudaStream_t s);
 love_status ski_mvm_fused(love_ski* ski, float* qj, const double* scal, const int* done, float* y, void* work,
