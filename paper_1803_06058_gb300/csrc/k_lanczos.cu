@@ -681,6 +681,7 @@ struct TileArgs {
   int detect;         // skip the second pass when |Q_j^T y'| <= eta |y'|
   double eta2;        // eta^2
   double* gram;       // low-synchronisation mode: Q^T Q (kcols x kcols, FP64), else nullptr
+  int reverse;        // walk the row tiles from the last one (tiled sweeps)
 };
 
 // 4 consecutive rows of one column in shared memory (one 16-byte access for
@@ -907,7 +908,11 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
   // thread 0 fills a stage: 2-D TMA boxes of Q (bc columns x 128 rows; per
   // column 1-D bulk copies issued from a whole warp measured 1.4-1.5x slower)
   // and a 1-D bulk copy of y, completing on the stage's mbarrier
-  auto issue = [&](int64_t tile, int s) {
+  // consecutive sweeps walk the tiles in opposite orders, so each one starts
+  // on the tiles the previous one left in L2
+  auto phys = [&](int64_t t) { return a.reverse ? ntiles - 1 - t : t; };
+  auto issue = [&](int64_t t, int s) {
+    const int64_t tile = phys(t);
     mbar_arrive_expect_tx(&bar[s], tx);
     T* dst = ring + (size_t)s * stage_elems;
     for (int b = 0; b < nbox; ++b)
@@ -929,7 +934,8 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
   const int r0 = 4 * lane;   // this lane's rows r0 .. r0 + 3
 
   int it = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int64_t tile = phys(t);
     const int s = it % a.stages;
     const uint32_t parity = (uint32_t)((it / a.stages) & 1);
     bool ok = mbar_wait_bounded(&bar[s], parity);
@@ -1004,7 +1010,7 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
     }
     __syncthreads();
     if (tid == 0) {
-      int64_t nt = tile + (int64_t)a.stages * gridDim.x;
+      int64_t nt = t + (int64_t)a.stages * gridDim.x;
       if (nt < ntiles) {
         fence_proxy_async();
         issue(nt, s);
@@ -1636,6 +1642,7 @@ love_status tile_run(TileArgs<T> a, cudaStream_t s) {
     return LOVE_ERR_UNSUPPORTED;
   }
   a.kpad = (ncols + a.bc - 1) / a.bc * a.bc;
+  a.reverse = MODE == MODE_UPDATE_DOT;   // dot forward, update + dot back, update + norm forward
   const TileGeom tg = tile_geom(a.kpad, a.kcols, sizeof(T));
   if (tg.stages == 0) return LOVE_ERR_UNSUPPORTED;
   a.stages = tg.stages;
