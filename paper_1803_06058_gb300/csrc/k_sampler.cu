@@ -42,7 +42,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "love_internal.cuh"
+#include "lanczos_common.cuh"
 #include "fft_core.cuh"
 
 namespace love {
@@ -516,5 +516,144 @@ love_status sampler_lanczos_fused<double>(const GridHost&, const FftPlan*, const
                                           DevStatus*, cudaStream_t) {
   return LOVE_ERR_UNSUPPORTED;
 }
+
+// ---------------------------------------------------------------------------
+// The same sampler run as a sequence of launches, for the cases the persistent
+// kernel above does not take (FP64 caches, 2-D and 3-D grids, additive
+// compositions): k' steps on M = K_UU - Rt Rt^T, an m x m operator, in FP64
+// with the n-space run's CGS2 reorthogonalisation sweeps.
+// M's entries are differences of nearly equal numbers (K_UU ~ 1, posterior
+// ~ 1e-7 on the 1-D n = 1e6 workload), so FP32 would lose them entirely.
+// The probe (not given by the paper) is the Rademacher vector
+// r_i = +1 if the low bit of SplitMix64 output i (seeded with `seed`) is 1, else -1.
+namespace {
+
+template <typename QT>
+__global__ void k_rademacher(int64_t m, int64_t m_pad, uint64_t seed, QT* __restrict__ q0, LanczosState* st) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m_pad) q0[i] = i < m ? ((splitmix64_at(seed, (uint64_t)i) & 1ull) ? QT(1) : QT(-1)) : QT(0);
+  if (i == 0) st->scal[0] = 1.0 / sqrt((double)m);
+}
+// Partial products of the sampler operator's low-rank term (R = Rt, m x k,
+// column-major): tp[c * RS + rs] = sum over rows of slice rs of R[r, c] q[r],
+// a block per (column, slice of GEMV_SLICE rows), each thread 4 rows.
+constexpr int GEMV_SLICE = 1024;
+template <typename T>
+__global__ void k_gemv_t(const T* __restrict__ R, int64_t ldr, int64_t m, const double* __restrict__ q,
+                         double* __restrict__ tp, const LanczosState* st) {
+  __shared__ DotAccD red[32];
+  if (st->done) return;
+  const int c = blockIdx.x, rs = blockIdx.y;
+  const int64_t r0 = (int64_t)rs * GEMV_SLICE;
+  DotAccD a;
+  a.zero();
+#pragma unroll
+  for (int u = 0; u < GEMV_SLICE / 256; ++u) {
+    const int64_t r = r0 + u * 256 + threadIdx.x;
+    if (r < m) a.add_prod((double)R[(int64_t)c * ldr + r], q[r]);
+  }
+  block_merge(a, red);
+  if (threadIdx.x == 0) tp[(int64_t)c * gridDim.y + rs] = a.value();
+}
+// y[r] = Kq[r] - sum_c R[r, c] t[c]  (0 on padding rows); t[c] = the sum of
+// the RS slice partials (fixed order).  A block covers 32 rows: warp w takes
+// the columns w, w + 8, ..., lane l row l, then the 8 warp sums are added.
+// (y in the storage type of the Lanczos vectors: the FP64 difference rounded once)
+template <typename T, typename YT>
+__global__ void k_gemv_n_sub(const T* __restrict__ R, int64_t ldr, int64_t m, int64_t m_pad, int k, int RS,
+                             const double* __restrict__ tp, const double* __restrict__ Kq, YT* __restrict__ y,
+                             const LanczosState* st) {
+  extern __shared__ double t_s[];   // [k] then [8][32]
+  if (st->done) return;
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double v = 0.0;
+    for (int rs = 0; rs < RS; ++rs) v += tp[(int64_t)c * RS + rs];
+    t_s[c] = v;
+  }
+  __syncthreads();
+  double* ws = t_s + k;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+  double acc = 0.0;
+  if (r < m) {
+#pragma unroll 4
+    for (int c = w; c < k; c += 8) acc = fma((double)R[(int64_t)c * ldr + r], t_s[c], acc);
+  }
+  ws[w * 32 + lane] = acc;
+  __syncthreads();
+  if (w == 0 && r < m_pad) {
+    double sum = 0.0;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) sum += ws[v * 32 + lane];
+    y[r] = r < m ? (YT)(Kq[r] - sum) : YT(0);
+  }
+}
+
+}  // namespace
+
+// The Lanczos vectors Q' are FP64 whatever the data dtype T of Rt: the run is
+// m-sized, and M q (K_UU q and Rt (Rt^T q) cancel to ~1e-7 of their size on the
+// 1-D n = 1e6 workload) is formed and kept in FP64, so the root is that of the
+// operator the cache defines to FP64 accuracy before it is rounded to T.
+template <typename T>
+love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Allocator& al, const T* Rt, int64_t ldr,
+                            int k, int ks, uint64_t seed, double tau, double* Q, int64_t ldq, double* alpha_h,
+                            double* beta_h, int* ks_eff, DevStatus* status, cudaStream_t s) {
+  const int64_t m = gh.m, m_pad = ldq;
+  if (ks < 1 || ks > LOVE_MAX_K || m_pad % TILE_R) return LOVE_ERR_ARG;
+  const int bc = box_cols(sizeof(double));
+  const int max_grid = std::max(TILE_CTAS_PER_SM * num_sms(), 1024);
+  DevBuf stb(al, s), part(al, s), kq(al, s), y(al, s), tv(al, s), fw(al, s);
+  size_t fwb = fft_work_bytes(gh, fft, 1, true);
+  if (!stb.get(sizeof(LanczosState)) || !part.get(sizeof(double2) * (size_t)max_grid * (ks + 1)) ||
+      !kq.get(sizeof(double) * m) || !y.get(sizeof(double) * m_pad) ||
+      !tv.get(sizeof(double) * (size_t)(k + 1) * (size_t)ceil_div(m, GEMV_SLICE)) ||
+      !fw.get(std::max<size_t>(fwb, 16)))
+    return LOVE_ERR_OOM;
+  LanczosState* st = stb.as<LanczosState>();
+  LOVE_COUNT_LAUNCH(); k_state_init<<<1, 1, 0, s>>>(st, ks, tau);
+  LOVE_COUNT_LAUNCH(); k_rademacher<double><<<ceil_div(m_pad, 256), 256, 0, s>>>(m, m_pad, seed, Q, st);
+  LOVE_LAUNCH_CHECK();
+  TileArgs<double> ta{};
+  ta.n_pad = m_pad;
+  ta.kcols = ks;
+  ta.bc = bc;
+  ta.Q = Q;
+  ta.ldq = ldq;
+  ta.y = y.as<double>();
+  ta.partial = part.as<double2>();
+  ta.st = st;
+  ta.status = status;
+  const int nb = std::min(4 * num_sms(), ceil_div(m_pad, 256));
+  const int RS = ceil_div(m, GEMV_SLICE);
+  const size_t nsub_smem = sizeof(double) * ((size_t)k + 8 * 32);
+  LOVE_TRY(allow_smem(k_gemv_n_sub<T, double>, nsub_smem));
+  for (int j = 0; j < ks; ++j) {
+    double* qj = Q + (int64_t)j * ldq;
+    LOVE_COUNT_LAUNCH(); k_normalize_col<double><<<nb, 256, 0, s>>>(qj, m_pad, st->scal + j, st);
+    LOVE_TRY(kuu_apply<double>(gh, fft, qj, kq.as<double>(), 1, m, fw.p, -1, s));
+    LOVE_COUNT_LAUNCH(); k_gemv_t<T><<<dim3(k, RS), 256, 0, s>>>(Rt, ldr, m, qj, tv.as<double>(), st);
+    LOVE_COUNT_LAUNCH(); k_gemv_n_sub<T, double><<<ceil_div(m_pad, 32), 256, nsub_smem, s>>>(Rt, ldr, m, m_pad, k, RS, tv.as<double>(), kq.as<double>(), y.as<double>(), st);
+    LOVE_LAUNCH_CHECK();
+    ta.j = j;
+    LOVE_TRY(reorth_sweep<double, MODE_DOT>(ta, s));
+    LOVE_TRY(reorth_sweep<double, MODE_UPDATE_DOT>(ta, s));
+    LOVE_TRY(reorth_sweep<double, MODE_UPDATE_NORM>(ta, s));
+  }
+  int keff = 0;
+  LOVE_CUDA(cudaMemcpyAsync(&keff, &st->k_eff, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaMemcpyAsync(alpha_h, st->alpha, sizeof(double) * ks, cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaMemcpyAsync(beta_h, st->beta, sizeof(double) * ks, cudaMemcpyDeviceToHost, s));
+  LOVE_CUDA(cudaStreamSynchronize(s));
+  *ks_eff = keff;
+  return LOVE_OK;
+}
+
+template love_status sampler_lanczos<float>(const GridHost&, const FftPlan*, const Allocator&, const float*, int64_t,
+                                            int, int, uint64_t, double, double*, int64_t, double*, double*, int*,
+                                            DevStatus*, cudaStream_t);
+template love_status sampler_lanczos<double>(const GridHost&, const FftPlan*, const Allocator&, const double*,
+                                             int64_t, int, int, uint64_t, double, double*, int64_t, double*, double*,
+                                             int*, DevStatus*, cudaStream_t);
 
 }  // namespace love
