@@ -659,10 +659,26 @@ def run_secondary(args):
         seq_pre = a.elapsed_time(b)
         a, b = _ev(), _ev()
         a.record()
+        str_caches, _ = love.love_precompute_batched(skis, streams=True, **kw)
+        b.record()
+        torch.cuda.synchronize()
+        str_pre = a.elapsed_time(b)
+        del str_caches
+        a, b = _ev(), _ev()
+        a.record()
         caches, keff = love.love_precompute_batched(skis, **kw)
         b.record()
         torch.cuda.synchronize()
         bat_pre = a.elapsed_time(b)
+        # each GP's batched-run variances against its own single-GP run (outputscale 1: the
+        # prior variance p is ~1 at every point, so |d var| reads as |d var| / p)
+        dmax = 0.0
+        for i in range(0, len(members), 16):
+            xi = torch.tensor(members[i].x_test()[:2000], dtype=torch.float32, device=dev)
+            _, v1 = love.love_predict_mean_var(seq_caches[i], xi)
+            _, v2 = love.love_predict_mean_var(caches[i], xi)
+            dmax = max(dmax, float((v1 - v2).abs().max()))
+        rows_used = caches[0].info()["batched_rows"]
         del seq_caches
         batch = love.love_batch_create(caches, t_sizes)
         mean = torch.empty(T, device=dev)
@@ -699,7 +715,13 @@ def run_secondary(args):
                     config={"workload": bw.name, "gps": len(members), "sum_n": int(sum(m.n for m in members)),
                             "sum_m": int(sum(m.m for m in members)), "k": bw.k, "t_per_gp": bw.t, "s": bw.s,
                             "cache_dtype": "bf16", "l2": "flushed before every timed call (256 MB write)"},
-                    precompute_ms={"sequential": seq_pre, "batched": bat_pre, "speedup": seq_pre / bat_pre},
+                    precompute_ms={"sequential": seq_pre, "batched": bat_pre, "speedup": seq_pre / bat_pre,
+                                   "per_gp_streams": str_pre, "batched_sweep_rows": rows_used,
+                                   "batched_vs_sequential_max_abs_dvar": dmax,
+                                   "note": "batched: the 256 Lanczos runs as one batched run (one launch per "
+                                           "phase per step, CUDA graph), then mean/cache/sampler per GP on "
+                                           "8 pool streams; per_gp_streams: each GP's love_precompute on the "
+                                           "pool streams"},
                     predict_ms={"sequential": t_seq_pred, "batched_one_launch": t_bat_pred,
                                 "speedup": t_seq_pred / t_bat_pred},
                     predict_sample_ms={"sequential": t_seq, "batched_eager": t_eager, "batched_graph": t_graph,

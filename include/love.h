@@ -130,6 +130,8 @@ LOVE_API love_status ski_mvm_kuu(love_ski_t ski, const void* v, void* out, love_
 #define LOVE_WANT_GRAD 0x4u     /* keep P = W Q L^{-T} for love_var_backward  */
 #define LOVE_PRIOR_EXACT 0x8u   /* prior k(x*,x*) = s_f instead of w^T K_UU w */
 #define LOVE_TIME_REORTH 0x10u  /* time the reorthogonalisation sweeps (love_cache_info.reorth_ms) */
+#define LOVE_BATCH_STREAMS 0x20u /* love_precompute_batched: one love_precompute per GP on a pool
+                                    stream instead of the batched Lanczos kernels */
 
 typedef struct {
   int k;                   /* Lanczos steps (1..200)                           */
@@ -281,6 +283,9 @@ typedef struct {
   int reorth_skipped;      /* Lanczos steps that skipped the second pass (DETECT) */
   float reorth_ms;         /* device time of the reorthogonalisation sweeps within phase_ms[0]
                               (CUDA events around each step's sweeps; LOVE_TIME_REORTH, else 0) */
+  int batched_rows;        /* made by love_precompute_batched's batched Lanczos run: the rows of
+                              its sweep chunks (phase_ms[0] is then the device time of the whole
+                              batch's run, reorth_ms 0); else 0 */
 } love_cache_info_t;
 
 LOVE_API love_status love_cache_info(love_cache_t cache, love_cache_info_t* info);
@@ -356,10 +361,18 @@ LOVE_API love_status ski_mvm_kuu_noalloc(love_ski_t ski, const void* v, void* ou
  * the single-GP calls on its own handles (up to summation order). */
 
 /* love_precompute_batched -- love_precompute for skis[0..B) with shared opts.
- * Up to `workers` pre-computes run at the same time (0 -> 8; at most 32), each
- * on a stream of a pool the library owns, ordered after the work already
- * queued on `stream`; the call returns when all are done (like
- * love_precompute, it synchronises).  caches[b] receives GP b's handle and
+ * When every ski is 1-D, FP32 and not additive (and LOVE_BATCH_STREAMS is not
+ * set), the B Lanczos runs are ONE batched run: each step is one launch per
+ * phase (scatter, K_UU, gather, three reorthogonalisation sweeps) over a ragged
+ * list of chunks of all GPs, the k steps captured into one CUDA graph, and the
+ * sweep chunk size picked by timing the batch's own dot sweep.  Its
+ * reorthogonalisation is the detection form (LOVE_REORTH_DETECT; LOWSYNC is
+ * read as DETECT), so each GP's cache equals the single-GP cache to the FP32
+ * tolerance, not bitwise.  The remaining phases (mean, cache, sampler) and
+ * every other batch run as love_precompute per GP: up to `workers` at the
+ * same time (0 -> 8; at most 32), each on a stream of a pool the library
+ * owns, ordered after the work already queued on `stream`; the call returns
+ * when all are done (like love_precompute, it synchronises).  caches[b] receives GP b's handle and
  * k_eff[b] (may be NULL) its Lanczos steps.  On failure every cache this call
  * created is destroyed, caches[] is all NULL and the status of the lowest
  * failing b is returned. */

@@ -229,13 +229,19 @@ def love_precompute_batched(skis: Sequence[Ski], k: int, cache_dtype: str = None
                             want_sampler: bool = False, want_grad: bool = False, prior_exact: bool = False,
                             breakdown_tol: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
                             sampler_k: int = 0, sampler_seed: int = 0, workers: int = 0, reorth: str = "always",
-                            reorth_eta: float = 0.0, cg_plain: bool = False, stream=None):
-    """love_precompute for every ski (shared options), run concurrently; returns (caches, k_eff)."""
+                            reorth_eta: float = 0.0, cg_plain: bool = False, streams: bool = False, stream=None):
+    """love_precompute for every ski (shared options), run concurrently; returns (caches, k_eff).
+    1-D FP32 batches run their Lanczos steps as one batched run (one launch per phase
+    per step for all GPs, captured into a CUDA graph; caches[b].info()["batched_rows"]
+    is the sweep chunk size it picked); streams=True runs each GP's own
+    love_precompute on a pool stream instead."""
     B = len(skis)
     if B == 0:
         return [], []
     o = _opts(skis[0].dtype, k, cache_dtype, want_mean, want_sampler, want_grad, prior_exact, breakdown_tol,
               cg_tol, cg_max_iter, sampler_k, sampler_seed, reorth, reorth_eta, cg_plain)
+    if streams:
+        o.flags |= _lib.BATCH_STREAMS
     hs = (C.c_void_p * B)(*[s.handle for s in skis])
     out = (C.c_void_p * B)()
     keff = (C.c_int * B)()

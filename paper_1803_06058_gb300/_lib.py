@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "LOVE_OK", 1: "LOVE_ERR_ARG", 2: "LOVE_ERR_DOMAIN", 3: "LOVE_
                 8: "LOVE_ERR_STATE", 9: "LOVE_ERR_UNSUPPORTED"}
 F32, F64, BF16 = 0, 1, 2
 WANT_MEAN, WANT_SAMPLER, WANT_GRAD, PRIOR_EXACT, TIME_REORTH = 0x1, 0x2, 0x4, 0x8, 0x10
+BATCH_STREAMS = 0x20
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -46,7 +47,8 @@ class love_cache_info_t(C.Structure):
                 ("k_eff", C.c_int), ("ld", C.c_int), ("sampler_k", C.c_int),
                 ("cg_iters", C.c_int), ("sampler_fallback", C.c_int), ("dtype", C.c_int),
                 ("cache_dtype", C.c_int), ("flags", C.c_uint), ("phase_ms", C.c_float * 4),
-                ("reorth_skipped", C.c_int), ("reorth_ms", C.c_float)]
+                ("reorth_skipped", C.c_int), ("reorth_ms", C.c_float),
+                ("batched_rows", C.c_int)]
 
 
 class love_device_status_t(C.Structure):

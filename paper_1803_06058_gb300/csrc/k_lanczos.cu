@@ -239,157 +239,6 @@ template <> struct Row4<double> {
   }
 };
 
-// end of step j: beta_j = sqrt(norm2); stop at kmax, on NaN or on breakdown
-// (beta_j <= tau max|alpha|), else the scale of the stored q_{j+1}
-__device__ void finish_step(LanczosState* st, DevStatus* status, int j) {
-  const double b = sqrt(st->norm2);
-  st->beta[j] = b;
-  if (!isfinite(b)) {
-    dev_flag(status, LOVE_ERR_NAN);
-    st->done = 1;
-    st->k_eff = j;
-  } else if (j + 1 >= st->kmax) {
-    st->k_eff = st->kmax;
-    st->done = 1;
-  } else if (b <= st->tau * st->maxabs) {
-    st->k_eff = j + 1;
-    st->done = 1;
-  } else {
-    st->scal[j + 1] = 1.0 / b;
-  }
-}
-
-// End of a sweep (both kernel shapes): per-CTA partials of the column dots
-// (or of |y|^2), the last CTA's fixed-order merge, and the step's scalar work
-// (alpha_j; the detection test; beta_j, breakdown and the next scale).
-template <typename T, int MODE, int KPW>
-__device__ __forceinline__ void sweep_epilogue(const TileArgs<T>& a, typename AccOf<T>::type (&acc)[KPW],
-                                               typename AccOf<T>::type& nacc, typename AccOf<T>::type* red,
-                                               double2* scratch) {
-  using Acc = typename AccOf<T>::type;
-  LanczosState* st = a.st;
-  const int j = a.j;
-  const int ncols = j + 1;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // ---- CTA partials
-  const int pstride = a.kcols + 1;
-  if (MODE == MODE_UPDATE_NORM) {
-    block_merge(nacc, red);
-    if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride, nacc);
-  } else {
-#pragma unroll
-    for (int s2 = 0; s2 < KPW; ++s2) {
-      const int i = warp + NWARP * s2;
-      warp_merge(acc[s2]);
-      if (lane == 0 && i < ncols) acc_store(a.partial + (int64_t)blockIdx.x * pstride + i, acc[s2]);
-    }
-    if (MODE == MODE_UPDATE_DOT && a.detect) {   // |y'|^2 in slot j + 1
-      block_merge(nacc, red);
-      if (tid == 0) acc_store(a.partial + (int64_t)blockIdx.x * pstride + ncols, nacc);
-    }
-  }
-  double* result = MODE == MODE_UPDATE_NORM ? &st->norm2 : (MODE == MODE_UPDATE_DOT ? st->coef2 : st->coef);
-  const int nres = MODE == MODE_UPDATE_NORM ? 1 : ncols + (MODE == MODE_UPDATE_DOT && a.detect ? 1 : 0);
-  // scratch (shared memory, at least j + 1 + blockDim.x doubles): the merged
-  // sums, then the pieces of the low-synchronisation product
-  double* cm = reinterpret_cast<double*>(scratch);
-  bool last = last_cta_reduce<Acc>(a.partial, pstride, nres, result, st->counter,
-                                   MODE == MODE_UPDATE_NORM ? nullptr : cm);
-  if (!last) return;
-  if (MODE == MODE_DOT && a.gram != nullptr) {
-    // low-synchronisation form: the second Gram-Schmidt pass folded into the
-    // first through the Gram matrix G = Q_j^T Q_j, c <- c + (c - G c) (the
-    // coefficients CGS2's second pass would find on y - Q_j c); alpha_j keeps
-    // the first-pass c_j.  G is stored symmetric, so row i of G is read as
-    // column i (coalesced across a warp); the threads split the l range of
-    // every row into `parts` pieces (16 loads in flight each), then add the
-    // pieces in a fixed order.
-    const double* G = a.gram;
-    double* pp = cm + ncols;   // [parts][ncols], parts * ncols <= blockDim.x
-    const int parts = max(1, (int)blockDim.x / ncols);
-    const int span = (ncols + parts - 1) / parts;
-    for (int t = tid; t < parts * ncols; t += blockDim.x) {
-      const int part = t / ncols, i = t - part * ncols;
-      const int lb = part * span, le = min(ncols, lb + span);
-      double v = 0.0;
-      for (int l0 = lb; l0 < le; l0 += 16) {
-        double gl[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-          gl[u] = l0 + u < le ? __ldcg(G + (int64_t)(l0 + u) * a.kcols + i) : 0.0;
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (l0 + u < le) v = fma(gl[u], cm[l0 + u], v);
-      }
-      pp[t] = v;
-    }
-    __syncthreads();
-    for (int i = tid; i < ncols; i += blockDim.x) {
-      double v = 0.0;
-      for (int p = 0; p < parts; ++p) v += pp[p * ncols + i];
-      st->coef[i] = 2.0 * cm[i] - v;
-    }
-    if (tid != 0) return;
-    const double c1j = cm[j];
-    st->alpha[j] = c1j;
-    if (!isfinite(c1j)) {
-      dev_flag(a.status, LOVE_ERR_NAN);
-      st->done = 1;
-      st->k_eff = j;
-    }
-    st->maxabs = fmax(st->maxabs, fabs(c1j));
-    return;
-  }
-  if (MODE == MODE_UPDATE_DOT && a.detect) {
-    // the detection test on the measured c' = Q_j^T y' (warp 0, fixed order)
-    __shared__ int skip_sh;
-    if (warp == 0) {
-      double c2 = 0.0;
-      for (int i = lane; i < ncols; i += 32) c2 = fma(cm[i], cm[i], c2);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-      if (lane == 0) skip_sh = c2 <= a.eta2 * cm[ncols];   // false for NaN: the second pass reports it
-    }
-    __syncthreads();
-    const bool skip = skip_sh != 0;
-    const double yn = cm[ncols];
-    if (a.gram != nullptr && j + 1 < a.kcols) {
-      // row and column j + 1 of G: the measured dots of q_{j+1} = y'/|y'| with
-      // Q_j (zero when the second pass runs and removes them)
-      double* G = a.gram;
-      const int64_t ld = a.kcols;
-      const double inv = skip && yn > 0.0 ? 1.0 / sqrt(yn) : 0.0;
-      for (int i = tid; i < ncols; i += blockDim.x) {
-        const double g = cm[i] * inv;
-        G[(int64_t)(j + 1) * ld + i] = g;
-        G[(int64_t)i * ld + (j + 1)] = g;
-      }
-      if (tid == 0) G[(int64_t)(j + 1) * ld + (j + 1)] = 1.0;
-    }
-    if (tid != 0) return;
-    st->skip = skip;
-    if (skip) {
-      st->n_skip += 1;
-      st->norm2 = yn;
-      finish_step(st, a.status, j);
-    }
-    return;
-  }
-  if (tid != 0) return;
-  if (MODE == MODE_DOT) {
-    double al = cm[j];
-    st->alpha[j] = al;
-    if (!isfinite(al)) {
-      dev_flag(a.status, LOVE_ERR_NAN);
-      st->done = 1;
-      st->k_eff = j;
-    }
-    st->maxabs = fmax(st->maxabs, fabs(al));
-  } else if (MODE == MODE_UPDATE_NORM) {
-    finish_step(st, a.status, j);
-  }
-}
-
 // One reorthogonalisation sweep over the row tiles of [Q_j | y].  Per tile,
 // TILE_R rows of columns 0..j of Q (2-D TMA boxes of bc columns) and of y (a
 // 1-D bulk copy) land in one stage of a shared-memory ring, so every step
@@ -551,7 +400,8 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
   }
 
   // every issued stage has been consumed: the ring is free for the merge
-  sweep_epilogue<T, MODE, KPW>(a, acc, nacc, red, reinterpret_cast<double2*>(smem_raw));
+  sweep_epilogue<T, MODE, KPW>(a, acc, nacc, red, reinterpret_cast<double2*>(smem_raw), (int)gridDim.x,
+                              (int)blockIdx.x);
 }
 
 // The same three sweeps for short vectors (fewer row tiles than two per SM:
@@ -665,7 +515,7 @@ __global__ void __launch_bounds__(TILE_T) k_lanczos_small(const __grid_constant_
       if (i < ncols) acc[s2].add(fma(q[s2][1], y1, q[s2][0] * y0));
     }
   }
-  sweep_epilogue<T, MODE, KPW>(a, acc, nacc, red, wsum);
+  sweep_epilogue<T, MODE, KPW>(a, acc, nacc, red, wsum, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // Lanczos product y = W^T u + s^2 q_j (u = K_UU W q_j), normalising q_j in

@@ -722,11 +722,11 @@ struct Buf {
   Buf(const Allocator& a, cudaStream_t st) : al(&a), s(st) {}
   bool get(size_t bytes) {
     b = bytes;
-    p = al->alloc(bytes, s);
+    p = scratch_alloc(*al, bytes, s);
     return p != nullptr;
   }
   ~Buf() {
-    if (p) al->free(p, b, s);
+    if (p) scratch_free(*al, p, b, s);
   }
   template <typename X> X* as() const { return (X*)p; }
 };

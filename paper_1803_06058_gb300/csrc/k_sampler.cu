@@ -448,7 +448,7 @@ love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const 
   const size_t n_dbl = 3 * (size_t)G * KP + G + KP + 2 * (size_t)KP;
   const size_t off_int = off_part + sizeof(double) * n_dbl;
   const size_t bytes = off_int + 64 + sizeof(GridSync);
-  char* w = (char*)al.alloc(bytes, s);
+  char* w = (char*)scratch_alloc(al, bytes, s);
   if (!w) return LOVE_ERR_OOM;
   SamplerArgs<T> a{};
   a.m = m;
@@ -500,7 +500,7 @@ love_status sampler_lanczos_fused(const GridHost& gh, const FftPlan* fft, const 
   if (rc == LOVE_OK) rc = cuda_check(cudaMemcpyAsync(alpha_h, a.alpha, sizeof(double) * ks, cudaMemcpyDeviceToHost, s));
   if (rc == LOVE_OK) rc = cuda_check(cudaMemcpyAsync(beta_h, a.beta, sizeof(double) * ks, cudaMemcpyDeviceToHost, s));
   if (rc == LOVE_OK) rc = cuda_check(cudaStreamSynchronize(s));
-  al.free(w, bytes, s);
+  scratch_free(al, w, bytes, s);
   if (rc != LOVE_OK) return rc;
   if (gsh.abort) return LOVE_ERR_TIMEOUT;   // a grid barrier gave up waiting
   *ks_eff = keff;

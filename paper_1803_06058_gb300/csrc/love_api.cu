@@ -49,6 +49,58 @@ void Allocator::free(void* p, size_t bytes, cudaStream_t s) const {
   cudaFreeAsync(p, s);
 }
 
+static bool same_allocator(const Allocator& a, const Allocator& b) {
+  return a.user == b.user && (!a.user || (a.a.alloc == b.a.alloc && a.a.free == b.a.free && a.a.ctx == b.a.ctx));
+}
+void* ScratchCache::take(const Allocator& al, size_t bytes, cudaStream_t s) {
+  size_t r = 256;
+  while (r < bytes) r <<= 1;
+  for (size_t i = 0; i < idle.size(); ++i) {
+    if (idle[i].s == s && idle[i].bytes == r && same_allocator(idle[i].al, al)) {
+      busy.push_back(idle[i]);
+      idle.erase(idle.begin() + (std::ptrdiff_t)i);
+      return busy.back().p;
+    }
+  }
+  void* p = al.alloc(r, s);
+  if (p) busy.push_back(Blk{al, s, p, r});
+  return p;
+}
+bool ScratchCache::give(void* p) {
+  for (size_t i = 0; i < busy.size(); ++i) {
+    if (busy[i].p == p) {
+      idle.push_back(busy[i]);
+      busy.erase(busy.begin() + (std::ptrdiff_t)i);
+      return true;
+    }
+  }
+  return false;
+}
+void ScratchCache::release() {
+  for (auto& b : idle) b.al.free(b.p, b.bytes, b.s);
+  for (auto& b : busy) b.al.free(b.p, b.bytes, b.s);
+  idle.clear();
+  busy.clear();
+}
+ScratchCache*& thread_scratch() {
+  static thread_local ScratchCache* t = nullptr;
+  return t;
+}
+ScratchCache*& thread_mean_scratch() {
+  static thread_local ScratchCache* t = nullptr;
+  return t;
+}
+void* scratch_alloc(const Allocator& al, size_t bytes, cudaStream_t s) {
+  ScratchCache* c = thread_scratch();
+  return c ? c->take(al, bytes, s) : al.alloc(bytes, s);
+}
+void scratch_free(const Allocator& al, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  ScratchCache* c = thread_scratch();
+  if (c && c->give(p)) return;
+  al.free(p, bytes, s);
+}
+
 GridDev GridHost::dev() const {
   GridDev d{};
   d.dim = dim;
@@ -471,9 +523,12 @@ struct MeanJob {
   }
 };
 
+// pre_Q / pre: the Lanczos run already made (by the batched run): Q (k columns,
+// from ski's allocator; owned from here on) and its scalars
 template <typename T>
 static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o, cudaStream_t s, love_cache** out,
-                                   int* k_eff_out) {
+                                   int* k_eff_out, T* pre_Q = nullptr, const BatchedLanczos::Gp* pre = nullptr,
+                                   int pre_rows = 0) {
   const GridHost& g = ski->grid;
   const Allocator& al = ski->alloc;
   int k = std::min<int64_t>(o->k, std::min<int64_t>(ski->n, g.m));
@@ -500,7 +555,7 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     am = (double*)al.alloc(amb, s);
     if (!am) return LOVE_ERR_OOM;
   }
-  T* Q = (T*)al.alloc(qb, s);
+  T* Q = pre_Q ? pre_Q : (T*)al.alloc(qb, s);
   if (!Q) {
     al.free(am, amb, s);
     return LOVE_ERR_OOM;
@@ -522,8 +577,10 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     cudaGetDevice(&dev);
     const bool precond = o->cg_plain == 0;
     try {
-      mj.th = std::thread([ski, cg_tol, cg_maxit, am, s2, dev, precond, &mj] {
+      ScratchCache* mean_cache = thread_mean_scratch();
+      mj.th = std::thread([ski, cg_tol, cg_maxit, am, s2, dev, precond, &mj, mean_cache] {
         cudaSetDevice(dev);
+        thread_scratch() = mean_cache;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -553,8 +610,16 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   PhaseEvents ev;
   ev.record(0, s);
   float reorth_ms = 0.f;
-  love_status rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, s,
-                                  (flags & LOVE_TIME_REORTH) ? &reorth_ms : nullptr, lowsync);
+  love_status rc = LOVE_OK;
+  if (pre) {
+    std::copy(pre->alpha.begin(), pre->alpha.begin() + std::min<size_t>(pre->alpha.size(), k), alpha.begin());
+    std::copy(pre->beta.begin(), pre->beta.begin() + std::min<size_t>(pre->beta.size(), k), beta.begin());
+    keff = pre->k_eff;
+    skipped = pre->skipped;
+  } else {
+    rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, s,
+                        (flags & LOVE_TIME_REORTH) ? &reorth_ms : nullptr, lowsync);
+  }
   ev.record(1, s);
   if (rc != LOVE_OK) {
     join_mean();
@@ -585,6 +650,7 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   }
   c->reorth_skipped = skipped;
   c->reorth_ms = reorth_ms;
+  c->batched_rows = pre_rows;
   std::copy(alpha.begin(), alpha.begin() + keff, c->alpha);
   std::copy(beta.begin(), beta.begin() + std::max(keff - 1, 0), c->beta);
   // n-space mean CG (3-D grids), on this stream
@@ -641,17 +707,50 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
   return LOVE_OK;
 }
 
+namespace love {
+
+love_status precompute_opts_check(const love_ski* ski, const love_precompute_opts* opts) {
+  if (opts->k < 1 || opts->k > LOVE_MAX_K) return LOVE_ERR_ARG;
+  if (ski->dtype == LOVE_F64 && opts->cache_dtype != LOVE_F64) return LOVE_ERR_ARG;
+  if (ski->dtype == LOVE_F32 && opts->cache_dtype == LOVE_F64) return LOVE_ERR_ARG;
+  if (opts->sampler_k > LOVE_MAX_K) return LOVE_ERR_ARG;
+  if (ski->grid.additive && (opts->flags & LOVE_WANT_GRAD)) return LOVE_ERR_UNSUPPORTED;
+  return LOVE_OK;
+}
+
+int precompute_k(const love_ski* ski, const love_precompute_opts* o) {
+  return (int)std::min<int64_t>(o->k, std::min<int64_t>(ski->n, ski->grid.m));
+}
+
+void precompute_lanczos_params(const love_ski* ski, const love_precompute_opts* o, double* tau, double* eta) {
+  const bool f64 = ski->dtype == LOVE_F64;
+  *tau = o->breakdown_tol > 0 ? o->breakdown_tol : (f64 ? 1e-12 : 1e-8);
+  *eta = o->reorth == LOVE_REORTH_ALWAYS ? 0.0 : (o->reorth_eta > 0 ? o->reorth_eta : (f64 ? 0x1p-51 : 0x1p-22));
+}
+
+love_status precompute_from_lanczos(love_ski* ski, const love_precompute_opts* opts, cudaStream_t s, float* Q,
+                                    const BatchedLanczos::Gp& r, int rows, float lanczos_ms, love_cache** out,
+                                    int* k_eff) {
+  *out = nullptr;
+  const love_status rc = precompute_opts_check(ski, opts);
+  if (rc != LOVE_OK || ski->dtype != LOVE_F32) {
+    ski->alloc.free(Q, sizeof(float) * (size_t)ski->n_pad * precompute_k(ski, opts), s);
+    return rc != LOVE_OK ? rc : LOVE_ERR_ARG;
+  }
+  const love_status prc = precompute_impl<float>(ski, opts, s, out, k_eff, Q, &r, rows);
+  if (prc == LOVE_OK) (*out)->phase_ms[0] = lanczos_ms;   // the whole batch's run
+  return prc;
+}
+
+}  // namespace love
+
 extern "C" {
 
 love_status love_precompute(love_ski_t ski, const love_precompute_opts* opts, love_stream_t stream,
                             love_cache_t* out, int* k_eff) try {
   if (!ski || !opts || !out) return LOVE_ERR_ARG;
   *out = nullptr;
-  if (opts->k < 1 || opts->k > LOVE_MAX_K) return LOVE_ERR_ARG;
-  if (ski->dtype == LOVE_F64 && opts->cache_dtype != LOVE_F64) return LOVE_ERR_ARG;
-  if (ski->dtype == LOVE_F32 && opts->cache_dtype == LOVE_F64) return LOVE_ERR_ARG;
-  if (opts->sampler_k > LOVE_MAX_K) return LOVE_ERR_ARG;
-  if (ski->grid.additive && (opts->flags & LOVE_WANT_GRAD)) return LOVE_ERR_UNSUPPORTED;
+  LOVE_TRY(precompute_opts_check(ski, opts));
   cudaStream_t s = cs(stream);
   if (ski->dtype == LOVE_F64) return precompute_impl<double>(ski, opts, s, out, k_eff);
   return precompute_impl<float>(ski, opts, s, out, k_eff);
@@ -790,6 +889,7 @@ love_status love_cache_info(love_cache_t c, love_cache_info_t* info) try {
   info->flags = c->flags;
   for (int i = 0; i < 4; ++i) info->phase_ms[i] = c->phase_ms[i];
   info->reorth_skipped = c->reorth_skipped;
+  info->batched_rows = c->batched_rows;
   info->reorth_ms = c->reorth_ms;
   return LOVE_OK;
 }

@@ -249,13 +249,66 @@ love_status love_precompute_batched(int B, const love_ski_t* skis, const love_pr
   for (int w = 0; w < nw; ++w) LOVE_CUDA(cudaStreamWaitEvent(st[w], fork, 0));
   std::vector<love_status> rc(B, LOVE_OK);
   std::vector<int> ke(B, 0);
+  // 1-D FP32 batches: the B Lanczos runs as one batched run on the first pool
+  // stream (capturable), then the remaining phases per GP on the workers
+  bool batched = !(opts->flags & LOVE_BATCH_STREAMS);
+  for (int b = 0; b < B && batched; ++b) {
+    const love_ski* k = skis[b];
+    batched = k->dtype == LOVE_F32 && k->grid.dim == 1 && !k->grid.additive &&
+              precompute_opts_check(k, opts) == LOVE_OK;
+  }
+  std::vector<float*> Qb(B, nullptr);
+  std::vector<int> kb(B, 0);
+  BatchedLanczos bl;
+  auto free_q = [&]() {
+    for (int b = 0; b < B; ++b)
+      if (Qb[b]) skis[b]->alloc.free(Qb[b], sizeof(float) * (size_t)skis[b]->n_pad * kb[b], st[0]);
+    for (int b = 0; b < B; ++b) Qb[b] = nullptr;
+  };
+  if (batched) {
+    double tau = 0.0, eta = 0.0;
+    precompute_lanczos_params(skis[0], opts, &tau, &eta);
+    love_status brc = LOVE_OK;
+    for (int b = 0; b < B && brc == LOVE_OK; ++b) {
+      kb[b] = precompute_k(skis[b], opts);
+      Qb[b] = (float*)skis[b]->alloc.alloc(sizeof(float) * (size_t)skis[b]->n_pad * kb[b], st[0]);
+      if (!Qb[b]) brc = LOVE_ERR_OOM;
+    }
+    if (brc == LOVE_OK) brc = lanczos_batched(B, skis, kb.data(), Qb.data(), tau, eta, 0, st[0], &bl);
+    if (brc == LOVE_OK) brc = cuda_check(cudaStreamSynchronize(st[0]));
+    if (brc != LOVE_OK) {
+      free_q();
+      cudaStreamSynchronize(st[0]);
+      if (brc != LOVE_ERR_UNSUPPORTED) {
+        cudaEventDestroy(fork);
+        return brc;
+      }
+      batched = false;   // a GP of a form the batched run does not take: per-GP runs
+    }
+  }
   std::atomic<int> next{0};
   auto work = [&](int w) {
     cudaSetDevice(dev);
+    // this worker's work buffers (and its mean-solve threads') are reused from GP to GP
+    ScratchCache own, mean;
+    thread_scratch() = &own;
+    thread_mean_scratch() = &mean;
+    struct Uninstall {
+      ~Uninstall() {
+        thread_scratch() = nullptr;
+        thread_mean_scratch() = nullptr;
+      }
+    } uninstall;
     for (;;) {
       const int b = next.fetch_add(1);
       if (b >= B) break;
-      rc[b] = love_precompute(skis[b], opts, (love_stream_t)st[w], &caches[b], &ke[b]);
+      if (batched) {
+        float* q = Qb[b];
+        Qb[b] = nullptr;   // owned by the call from here on
+        rc[b] = precompute_from_lanczos(skis[b], opts, st[w], q, bl.gp[b], bl.rows, bl.ms, &caches[b], &ke[b]);
+      } else {
+        rc[b] = love_precompute(skis[b], opts, (love_stream_t)st[w], &caches[b], &ke[b]);
+      }
     }
   };
   std::vector<std::thread> th;

@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/love.h"
 
 #define LOVE_MAX_DIM 3
@@ -340,6 +342,32 @@ struct Allocator {
   void free(void* p, size_t bytes, cudaStream_t s) const;
 };
 
+// Work buffers of one host thread kept for reuse: while a thread has one
+// installed (love_precompute_batched's workers and their mean-solve threads),
+// scratch_alloc / scratch_free hand a freed buffer back to the next request
+// of the same allocator and stream that fits it (sizes rounded up to powers of
+// two), so B pre-computes in a row call the allocator (for the torch binding,
+// a Python callback per call) about as often as one.  Reuse on the same stream
+// only, so the stream orders a buffer's earlier work before its next use.
+// release() returns every buffer to its allocator.
+struct ScratchCache {
+  struct Blk {
+    Allocator al;
+    cudaStream_t s;
+    void* p;
+    size_t bytes;
+  };
+  std::vector<Blk> idle, busy;
+  ~ScratchCache() { release(); }
+  void* take(const Allocator& al, size_t bytes, cudaStream_t s);
+  bool give(void* p);
+  void release();
+};
+ScratchCache*& thread_scratch();        // this thread's cache, or nullptr
+ScratchCache*& thread_mean_scratch();   // the cache a mean-solve thread started here adopts
+void* scratch_alloc(const Allocator& al, size_t bytes, cudaStream_t s);
+void scratch_free(const Allocator& al, void* p, size_t bytes, cudaStream_t s);
+
 struct GridHost {
   int dim = 1;
   bool additive = false;                 // block-diagonal K_UU of 1-D blocks
@@ -417,6 +445,7 @@ struct love_cache {
   int cg_iters = 0;
   int reorth_skipped = 0;
   float reorth_ms = 0.f;
+  int batched_rows = 0;        // sweep chunk rows of the batched Lanczos run that made it (0: single)
   int sampler_fallback = 0;
   float phase_ms[4] = {0, 0, 0, 0};
   DevStatus* status = nullptr;
@@ -485,6 +514,34 @@ love_status sampler_lanczos(const GridHost& gh, const FftPlan* fft, const Alloca
 // counters); gen0: the barriers the run's
 // earlier products completed (4 per product).  LOVE_ERR_UNSUPPORTED where the
 // grid or the device does not allow it.
+// k_lanczos_batched.cu: the n-space Lanczos runs of B independent GPs on 1-D
+// grids (FP32 data, kcols[b] steps each, the detection form of the
+// reorthogonalisation with eta), one launch per phase per step for all GPs,
+// the steps captured into one CUDA graph on s (a stream that can be captured:
+// not the legacy default stream).  Q[b]: n_pad x kcols[b] (ski b's allocator).
+// rows: rows per sweep chunk (a multiple of 64 >= 256), or 0 to pick it by
+// timing the dot sweep.  LOVE_ERR_UNSUPPORTED where a GP is not of that form.
+struct BatchedLanczos {
+  struct Gp {
+    std::vector<double> alpha, beta;
+    int k_eff = 0, skipped = 0;
+  };
+  std::vector<Gp> gp;
+  int rows = 0;                  // the sweep chunk rows used
+  float ms = 0.f;                // device time of the batch's probe and k steps (CUDA events)
+  std::vector<float> tune_ms;    // dot-sweep time per candidate (256, 512, 1024, 2048 rows)
+};
+love_status lanczos_batched(int B, love_ski* const* skis, const int* kcols, float* const* Q, double tau, double eta,
+                            int rows, cudaStream_t s, BatchedLanczos* out);
+// love_api.cu: the option checks and Lanczos parameters of love_precompute, and
+// its remaining phases (mean, cache, sampler) on a Lanczos run already made
+// (Q: n_pad x precompute_k columns from ski's allocator, owned by the call)
+love_status precompute_opts_check(const love_ski* ski, const love_precompute_opts* opts);
+int precompute_k(const love_ski* ski, const love_precompute_opts* o);
+void precompute_lanczos_params(const love_ski* ski, const love_precompute_opts* o, double* tau, double* eta);
+love_status precompute_from_lanczos(love_ski* ski, const love_precompute_opts* opts, cudaStream_t s, float* Q,
+                                    const BatchedLanczos::Gp& r, int rows, float lanczos_ms, love_cache** out,
+                                    int* k_eff);
 // the circulant's twiddles W_N^j and spectrum lambda_j / N as double-float
 // tables (twdf: {re.hi, re.lo, im.hi, im.lo}; lamdf: {hi, lo}), N entries each
 love_status fft_df_tables(const FftPlan& p, float4* twdf, float2* lamdf, cudaStream_t s);

@@ -1,8 +1,10 @@
 """GPU parity of the batched entry points (many independent 1-D GPs of uneven
 size, the 256-GP workload's members at reduced n and t):
 
-  * love_precompute_batched gives, per GP, the cache love_precompute gives
-    (same kernels on another stream: bitwise equal);
+  * love_precompute_batched with streams=True (each GP's own love_precompute
+    on a pool stream) gives, per GP, the cache love_precompute gives (same
+    kernels on another stream: bitwise equal); the batched Lanczos kernels of
+    the default form are checked in test_gpu_batched_lanczos.py;
   * love_predict_batched (one launch, autotuned shape) matches per-GP
     love_predict_mean_var to the FP32 variance tolerance |d var| / p <= 1e-6
     (only the lanes-per-point summation order can differ) and two GPs match
@@ -44,7 +46,8 @@ def batch_setup(love):
     t_sizes[3] = 0          # a GP with no test points
     t_sizes[5] = 777        # a ragged chunk tail
     skis = [_ski(love, wl) for wl in members]
-    caches, keff = love.love_precompute_batched(skis, k=32, want_mean=True, want_sampler=True, workers=4)
+    caches, keff = love.love_precompute_batched(skis, k=32, want_mean=True, want_sampler=True, workers=4,
+                                                streams=True)
     xs = [np.asarray(wl.x_test()[:t], np.float32).astype(np.float64) for wl, t in zip(members, t_sizes)]
     x_all = torch.tensor(np.concatenate(xs), dtype=torch.float32, device="cuda")
     return members, t_sizes, skis, caches, keff, xs, x_all
