@@ -158,7 +158,7 @@ __device__ int sturm_count_f(const float* a, const float* b2, int n, float x) {
 
 __global__ void __launch_bounds__(32) k_tri_eigpairs(const double* __restrict__ alpha, const double* __restrict__ beta,
                                                      int n, double* __restrict__ lam, double* __restrict__ V) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   double* u0 = reinterpret_cast<double*>(smem_raw);   // pivots
   double* u1 = u0 + n;                                 // first superdiagonal of U
   double* u2 = u1 + n;                                 // second superdiagonal (after swaps)
@@ -357,7 +357,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_root_from_eig(const double* __restrict__ Q, int64_t ldq, int64_t m, int k,
                                                        const double* __restrict__ B, T* __restrict__ S, int ld_s,
                                                        int stage_b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* Qs = reinterpret_cast<T*>(smem_raw);     // k x ROOT_ROWS
   T* Bs = Qs + (size_t)k * ROOT_ROWS;         // k x k when staged
   const int64_t r0 = (int64_t)blockIdx.x * ROOT_ROWS;
@@ -396,11 +396,28 @@ struct SampleGatherArgs {
   int ld_c;
   int kc;
   int cache_dtype;
-  void* G;           // t x ld_g
+  void* G;           // t x ld_g, or null when Gc is given
   int ld_g;
+  unsigned char* Gc; // FP32 data: G split into TF32 hi / lo, 128-point canonical tiles (canon_off)
+  int kpad;          // columns of a Gc tile (ks rounded up to 8)
   void* mu;          // t
   DevStatus* status;
 };
+
+// The FP32 operands of the tensor-core sample product, split and laid out once:
+// tile p holds rows 128 p .. 128 p + 127 (points of G, samples of Z^T) as its
+// TF32 hi part, then its lo part, each kpad x 128 in the canonical K-major
+// no-swizzle layout of umma_off (K slices of 16 bytes 2 KB apart), so a K
+// range of a part is one contiguous run of bytes.
+__host__ __device__ __forceinline__ size_t canon_tile_bytes(int kpad) { return (size_t)kpad * 1024; }
+__device__ __forceinline__ void canon_store(unsigned char* base, int kpad, int64_t row, int k, float v) {
+  uint32_t h, l;
+  split_tf32(v, h, l);
+  unsigned char* tb = base + (size_t)(row >> 7) * canon_tile_bytes(kpad);
+  const uint32_t o = umma_off((int)(row & 127), k);
+  *reinterpret_cast<uint32_t*>(tb + o) = h;
+  *reinterpret_cast<uint32_t*>(tb + (size_t)kpad * 512 + o) = l;
+}
 
 template <typename T>
 __device__ __forceinline__ T load_cache_elem(const void* Rc, int64_t idx, int cdt) {
@@ -427,7 +444,12 @@ __global__ void k_sample_gather(SampleGatherArgs a) {
 #pragma unroll
     for (int e = 0; e < D; ++e) ok &= keys_weights(grid_coord(x[pt * D + e], a.g, e), a.g.g[e], base[e], w[e]);
     if (!ok) {
-      for (int c = lane; c < a.ld_g; c += 32) G[pt * a.ld_g + c] = T(0);
+      if constexpr (std::is_same<T, float>::value) {
+        if (a.Gc)
+          for (int c = lane; c < a.kpad; c += 32) canon_store(a.Gc, a.kpad, pt, c, 0.f);
+      }
+      if (G)
+        for (int c = lane; c < a.ld_g; c += 32) G[pt * a.ld_g + c] = T(0);
       if (lane == 0) {
         mu[pt] = (T)NAN;
         atomicAdd(&a.status->domain_errors, 1ull);
@@ -461,13 +483,18 @@ __global__ void k_sample_gather(SampleGatherArgs a) {
       rows[q] = row;
       ww[q] = wq;
     }
-    for (int c = lane; c < a.ld_g; c += 32) {
+    const int cend = G ? a.ld_g : a.kpad;
+    for (int c = lane; c < cend; c += 32) {
       T acc = T(0);
       if (c < a.ks) {
 #pragma unroll
         for (int q = 0; q < NR; ++q) acc += ww[q] * S[rows[q] * a.ld_s + c];
       }
-      G[pt * a.ld_g + c] = acc;
+      if (G) {
+        G[pt * a.ld_g + c] = acc;
+      } else if constexpr (std::is_same<T, float>::value) {
+        canon_store(a.Gc, a.kpad, pt, c, acc);
+      }
     }
     if (lane == 0) {
       T m_ = T(0);
@@ -534,114 +561,96 @@ __global__ void __launch_bounds__(256) k_sample_gemm(const T* __restrict__ G, in
 }
 
 // ---------------------------------------------------------------------------
-// The product on the 5th-generation tensor cores (tcgen05, kind::tf32,
-// one CTA, accumulator in tensor memory).  A CTA computes a 128-point x
-// 128-sample tile D[i][j] = sum_c G[i][c] Z[c][j]:
-//   * G (A, M = points) and Z^T (B, N = samples) pass through shared memory in
-//     K chunks of UKC columns (two buffers: the next chunk is staged while the
-//     tensor core works on the previous one), each FP32 value split into two TF32 parts
-//     (hi = x rounded to TF32, lo = the rounded remainder); both operands are
-//     K-major in the no-swizzle canonical layout: 8-row x 16-byte core matrices,
-//     the 16 row blocks of one 16-byte K slice contiguous (stride 128 B), the
-//     K slices 2 KB apart;
-//   * one thread issues, per K step of 8, the MMAs hi*hi, hi*lo and lo*hi into
-//     the 128 x 128 FP32 accumulator (128 tensor-memory columns; lane = point),
-//     then commits them to the buffer's mbarrier, which every thread waits on
-//     (bounded) before that buffer is staged again;
-//   * the epilogue reads the accumulator with tcgen05.ld (warp w: lanes
-//     32 (w mod 4) .., columns 64 (w / 4) ..), adds mu and writes
-//     F[j][i] (sample-major, consecutive points per store).
-__global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __restrict__ G, int ld_g,
-                                                              const float* __restrict__ Z, int s, int ks,
+// The product on the 5th-generation tensor cores (tcgen05, kind::tf32, one
+// CTA, accumulator in tensor memory).  A CTA computes a 128-point x 128-sample
+// tile D[i][j] = sum_c G[i][c] Z[c][j] from the pre-split canonical tiles of G
+// (A, M = points) and Z^T (B, N = samples).  One thread drives a two-stage
+// ring of K chunks (SG_KC columns): it issues the four bulk copies of chunk
+// c + 1 (the hi and lo parts of both operands: contiguous runs of the
+// canonical tiles) before it waits for chunk c, then issues chunk c's MMAs
+// (per K step of 8: hi*hi, hi*lo and lo*hi; the lo*lo term, ~2^-22 relative,
+// is dropped) into the 128 x 128 FP32 accumulator in tensor memory and commits
+// them to the stage's "empty" mbarrier, which the next copy into that stage
+// waits on.  The other warps wait (bounded) for the last commit; then the
+// epilogue reads the accumulator with tcgen05.ld (warp w: lanes 32 (w mod 4)
+// .., columns 64 (w / 4) ..), adds mu and writes F[j][i] (sample-major, 32
+// consecutive points per store).  Two CTAs share an SM (96 KB of shared
+// memory each), so one CTA's epilogue overlaps the other's copies and MMAs.
+constexpr int SG_KC = 24;
+constexpr uint32_t SG_PART = SG_KC * 512;              // one operand part of one chunk
+constexpr uint32_t SG_STAGE = 4 * SG_PART;             // A hi, A lo, B hi, B lo
+constexpr size_t SG_SMEM = 2 * (size_t)SG_STAGE + 64;  // two stages + barriers
+__global__ void __launch_bounds__(256, 2) k_sample_gemm_tc05(const unsigned char* __restrict__ Gc,
+                                                              const unsigned char* __restrict__ Zc, int kpad, int s,
                                                               const float* __restrict__ mu, int64_t t,
                                                               float* __restrict__ F, DevStatus* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 8 * (size_t)U_TILE_BYTES);   // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // barriers: full[2] (copies landed), empty[2] (MMAs done with the stage), done
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * (size_t)SG_STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 5);
+  __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t i0 = (int64_t)blockIdx.x * UM;
   const int j0 = blockIdx.y * UN;
+  const unsigned char* ga = Gc + (size_t)blockIdx.x * canon_tile_bytes(kpad);
+  const unsigned char* zb = Zc + (size_t)blockIdx.y * canon_tile_bytes(kpad);
+  const size_t lo_off = (size_t)kpad * 512;
+  const int nch = (kpad + SG_KC - 1) / SG_KC;
   if (warp == 0) tmem_alloc_warp(tmem_slot, UN);
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int q = 0; q < 5; ++q) mbar_init(&bar[q], 1);
     fence_mbar_init();
+    s_ok = 1;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  bool ok = true;
-  uint32_t uses[2] = {0u, 0u};   // commits made to each buffer's barrier
-  // the operands of one chunk held in registers between their (early) global
-  // loads and their conversion into shared memory: G as a row-major tile;
-  // Z^T by sample column tid % 128 (coalesced along the samples) and 4-row
-  // groups (tid / 128) * 4 + 8 q (q < UKC / 8)
-  constexpr int QG = UKC / 8;
-  RowTileRegs greg;
-  float zreg[QG][4];
-  const int zn = tid & (UN - 1), zk = (tid >> 7) * 4;
-  const int zj = j0 + zn;
-  auto load_z = [&](int c0) {
-#pragma unroll
-    for (int q = 0; q < QG; ++q)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int kz = zk + 8 * q + u;
-        zreg[q][u] = (zj < s && c0 + kz < ks) ? Z[(int64_t)(c0 + kz) * s + zj] : 0.f;
+  if (tid == 0) {
+    auto load = [&](int c) {
+      const int st = c & 1, k0 = c * SG_KC;
+      const uint32_t pb = (uint32_t)min(SG_KC, kpad - k0) * 512u;
+      unsigned char* d = smem_raw + (size_t)st * SG_STAGE;
+      mbar_arrive_expect_tx(&bar[st], 4u * pb);
+      bulk_g2s(d, ga + (size_t)k0 * 512, pb, &bar[st]);
+      bulk_g2s(d + SG_PART, ga + lo_off + (size_t)k0 * 512, pb, &bar[st]);
+      bulk_g2s(d + 2 * SG_PART, zb + (size_t)k0 * 512, pb, &bar[st]);
+      bulk_g2s(d + 3 * SG_PART, zb + lo_off + (size_t)k0 * 512, pb, &bar[st]);
+    };
+    bool ok = true;
+    int issued = 0;   // chunks whose copies were issued
+    int c = 0;        // chunks whose MMAs were issued
+    load(0);
+    issued = 1;
+    for (; c < nch && ok; ++c) {
+      const int st = c & 1;
+      if (issued < nch) {
+        // stage of chunk c + 1: free once chunk c - 1's MMAs completed
+        if (c >= 1) ok = mbar_wait_bounded(&bar[2 + (issued & 1)], ((issued >> 1) - 1) & 1u);
+        if (!ok) break;
+        load(issued);
+        ++issued;
       }
-  };
-  greg.load(G, ld_g, i0, t, 0, ks, tid);
-  load_z(0);
-  int chunk = 0;
-  for (int c0 = 0; c0 < ks; c0 += UKC, ++chunk) {
-    const int b = chunk & 1;
-    unsigned char* Ahi = smem_raw + (size_t)b * 4 * U_TILE_BYTES;
-    unsigned char* Alo = Ahi + U_TILE_BYTES;
-    unsigned char* Bhi = Alo + U_TILE_BYTES;
-    unsigned char* Blo = Bhi + U_TILE_BYTES;
-    // the tensor core must be done with this buffer (chunk - 2) before it is rewritten
-    if (uses[b] > 0) {
-      ok = ok && mbar_wait_bounded(&bar[b], (uses[b] - 1u) & 1u);
-      if (__syncthreads_or(!ok)) break;
-    }
-    const int kc = min(UKC, (ks - c0 + 7) & ~7);   // columns of this chunk, padded to 8
-    // the held operands as TF32 hi / lo parts, one 16-byte core-matrix row
-    // (4 consecutive K) per store; zero outside the matrices
-    greg.store(Ahi, Alo, kc, tid);
-#pragma unroll
-    for (int q = 0; q < QG; ++q) {
-      if (8 * q + zk < kc) {
-        uint4 h, l;
-        split_tf32(zreg[q][0], h.x, l.x);
-        split_tf32(zreg[q][1], h.y, l.y);
-        split_tf32(zreg[q][2], h.z, l.z);
-        split_tf32(zreg[q][3], h.w, l.w);
-        const uint32_t o = umma_off(zn, zk + 8 * q);
-        *reinterpret_cast<uint4*>(Bhi + o) = h;
-        *reinterpret_cast<uint4*>(Blo + o) = l;
-      }
-    }
-    // the next chunk's global loads are in flight during the MMAs of this one
-    if (c0 + UKC < ks) {
-      greg.load(G, ld_g, i0, t, c0 + UKC, ks, tid);
-      load_z(c0 + UKC);
-    }
-    fence_proxy_async();   // the generic-proxy stores become visible to the tensor core
-    __syncthreads();
-    if (tid == 0) {
+      ok = mbar_wait_bounded(&bar[st], (c >> 1) & 1u);
+      if (!ok) break;
       tc_fence_after();
-      umma_chunk(tmem, Ahi, Alo, Bhi, Blo, kc, c0 == 0);
-      umma_commit(&bar[b]);
+      unsigned char* d = smem_raw + (size_t)st * SG_STAGE;
+      umma_chunk(tmem, d, d + SG_PART, d + 2 * SG_PART, d + 3 * SG_PART, min(SG_KC, kpad - c * SG_KC), c == 0);
+      umma_commit(&bar[2 + st]);
     }
-    uses[b] += 1u;
+    if (ok) umma_commit(&bar[4]);   // completes when every MMA issued before it has
+    if (!ok) {
+      s_ok = 0;
+      dev_flag(status, LOVE_ERR_TIMEOUT);
+      // copies or MMAs that never signalled may still be in flight: give them a
+      // bounded last chance before the shared and tensor memory are released
+      for (int x = c; x < issued; ++x) mbar_wait_bounded(&bar[x & 1], (x >> 1) & 1u);
+      for (int x = c > 2 ? c - 2 : 0; x < c; ++x) mbar_wait_bounded(&bar[2 + (x & 1)], (x >> 1) & 1u);
+    }
   }
-  // the last commit covers every MMA issued before it
-  if (ok && chunk > 0) {
-    const int b = (chunk - 1) & 1;
-    ok = mbar_wait_bounded(&bar[b], (uses[b] - 1u) & 1u);
-    ok = !__syncthreads_or(!ok);
-  }
+  __syncthreads();
+  bool ok = s_ok != 0;
+  if (ok) ok = mbar_wait_bounded(&bar[4], 0u);
   tc_fence_after();
   if (ok) {
     const int lb = 32 * (warp & 3);            // this warp's tensor-memory lanes (points)
@@ -660,7 +669,7 @@ __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __rest
         }
       }
     }
-  } else if (tid == 0) {
+  } else if (s_ok) {
     dev_flag(status, LOVE_ERR_TIMEOUT);
   }
   tc_fence_before();
@@ -671,6 +680,20 @@ __global__ void __launch_bounds__(256, 1) k_sample_gemm_tc05(const float* __rest
   }
 }
 
+// Z (ks x s, row-major) as the split canonical tiles of Z^T: tile p holds
+// samples 128 p .. 128 p + 127; zero past ks and past s
+__global__ void k_z_canon(const float* __restrict__ Z, int ks, int s, int kpad, int ntiles,
+                          unsigned char* __restrict__ Zc) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ntiles * kpad * 128) return;
+  const int n = (int)(idx & 127);
+  const int64_t rest = idx >> 7;
+  const int k = (int)(rest % kpad);
+  const int64_t tile = rest / kpad;
+  const int64_t j = tile * 128 + n;
+  const float v = (k < ks && j < s) ? Z[(int64_t)k * s + j] : 0.f;
+  canon_store(Zc, kpad, j, k, v);
+}
 
 // Philox4x32-10: 10 rounds of (hi0,lo0) = M0 x0, (hi1,lo1) = M1 x2,
 // x <- (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0), key += Weyl constants between rounds.
@@ -823,10 +846,17 @@ template love_status sampler_build<double>(const GridHost&, const FftPlan*, cons
                                            const double*, int, uint64_t, double, cudaStream_t);
 
 static size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+// FP32: the canonical tiles of G, mu, Z and the canonical tiles of Z^T; FP64: G, mu, Z
+static int canon_kpad(int ks) { return (ks + 7) / 8 * 8; }
 template <typename T>
 static size_t sample_ws_bytes_t(const love_cache* c, int64_t t, int s_count) {
   const int vec = 16 / (int)sizeof(T);
   const int ld_g = (c->ks + vec - 1) / vec * vec;
+  if (sizeof(T) == 4) {
+    const size_t tb = canon_tile_bytes(canon_kpad(c->ks));
+    return round256(tb * (size_t)ceil_div(t, UM)) + round256(sizeof(T) * (size_t)t) +
+           round256(sizeof(T) * (size_t)c->ks * s_count) + round256(tb * (size_t)ceil_div(s_count, UN));
+  }
   return round256(sizeof(T) * (size_t)t * ld_g) + round256(sizeof(T) * (size_t)t) +
          round256(sizeof(T) * (size_t)c->ks * s_count);
 }
@@ -839,17 +869,26 @@ static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_co
   const int ks = c->ks;
   const int vec = 16 / (int)sizeof(T);
   const int ld_g = (ks + vec - 1) / vec * vec;
-  Buf Gb(al, s), mub(al, s), zb(al, s);
+  constexpr bool tc = std::is_same<T, float>::value;   // the tensor-core product on canonical tiles
+  const int kpad = canon_kpad(ks);
+  const size_t tb = canon_tile_bytes(kpad);
+  const int64_t nti = ceil_div(t, UM), ntj = ceil_div((int64_t)s_count, UN);
+  const size_t gbytes = tc ? tb * (size_t)nti : sizeof(T) * (size_t)t * ld_g;
+  Buf Gb(al, s), mub(al, s), zb(al, s), zcb(al, s);
   T *Gp, *mup, *zp = nullptr;
+  unsigned char* zc = nullptr;
   if (ws) {
     char* w = (char*)ws;
     Gp = (T*)w;
-    mup = (T*)(w + round256(sizeof(T) * (size_t)t * ld_g));
+    mup = (T*)(w + round256(gbytes));
     zp = (T*)((char*)mup + round256(sizeof(T) * (size_t)t));
+    if (tc) zc = (unsigned char*)zp + round256(sizeof(T) * (size_t)ks * s_count);
   } else {
-    if (!Gb.get(sizeof(T) * (size_t)t * ld_g) || !mub.get(sizeof(T) * (size_t)t)) return LOVE_ERR_OOM;
+    if (!Gb.get(gbytes) || !mub.get(sizeof(T) * (size_t)t)) return LOVE_ERR_OOM;
+    if (tc && !zcb.get(tb * (size_t)ntj)) return LOVE_ERR_OOM;
     Gp = Gb.as<T>();
     mup = mub.as<T>();
+    zc = zcb.as<unsigned char>();
   }
   const T* Z = (const T*)z;
   if (!Z) {
@@ -873,8 +912,10 @@ static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_co
   a.ld_c = c->ld;
   a.kc = c->k_eff;
   a.cache_dtype = c->cache_dtype;
-  a.G = Gp;
+  a.G = tc ? nullptr : Gp;
   a.ld_g = ld_g;
+  a.Gc = tc ? reinterpret_cast<unsigned char*>(Gp) : nullptr;
+  a.kpad = kpad;
   a.mu = mup;
   a.status = c->status;
   int blocks = (int)std::min<int64_t>((t * 32 + 255) / 256, (int64_t)num_sms() * 16);
@@ -883,11 +924,15 @@ static love_status sample_impl(love_cache* c, int64_t t, const void* x, int s_co
     case 2: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 2><<<blocks, 256, 0, s>>>(a); break;
     default: LOVE_COUNT_LAUNCH(); k_sample_gather<T, 3><<<blocks, 256, 0, s>>>(a);
   }
-  if constexpr (std::is_same<T, float>::value) {
-    dim3 grid((unsigned)((t + UM - 1) / UM), (unsigned)((s_count + UN - 1) / UN));
-    LOVE_TRY(allow_smem(k_sample_gemm_tc05, U_SMEM));
+  if constexpr (tc) {
+    const int64_t nz = ntj * kpad * 128;
     LOVE_COUNT_LAUNCH();
-    k_sample_gemm_tc05<<<grid, 256, U_SMEM, s>>>(Gp, ld_g, Z, s_count, ks, mup, t, (float*)out, c->status);
+    k_z_canon<<<(unsigned)ceil_div(nz, 256), 256, 0, s>>>(Z, ks, s_count, kpad, (int)ntj, zc);
+    dim3 grid((unsigned)nti, (unsigned)ntj);
+    LOVE_TRY(allow_smem(k_sample_gemm_tc05, SG_SMEM));
+    LOVE_COUNT_LAUNCH();
+    k_sample_gemm_tc05<<<grid, 256, SG_SMEM, s>>>(reinterpret_cast<const unsigned char*>(Gp), zc, kpad, s_count,
+                                                    mup, t, (float*)out, c->status);
   } else {
     dim3 grid((unsigned)((t + 63) / 64), (unsigned)((s_count + 63) / 64));
     LOVE_COUNT_LAUNCH(); k_sample_gemm<T><<<grid, 256, 0, s>>>(Gp, ld_g, Z, s_count, ks, mup, t, (T*)out);
