@@ -101,11 +101,13 @@ __device__ __forceinline__ double local_quad_d(const double* w, const double* c)
   return r;
 }
 
-// acc[0..VC) = sum over the 4^D stencil rows r of w_r * (column group cg of row r)
-template <typename CT, typename R, int D>
+// acc[0..VC) = sum over the 4^D stencil rows r of w_r * (column group cg of row r);
+// with RS > 1 (3-D only) just the rows of first-dimension offsets
+// part (4 / RS) .. (part + 1)(4 / RS) - 1
+template <typename CT, typename R, int D, int RS = 1>
 __device__ __forceinline__ void gather_rows(const PredArgs& a, const typename VecOf<CT>::type* __restrict__ base_ptr,
                                             int NG, const int (&base)[D], const R (&w)[D][4], bool ok, int cg,
-                                            R (&acc)[VecOf<CT>::n]) {
+                                            R (&acc)[VecOf<CT>::n], int part = 0) {
   using V = typename VecOf<CT>::type;
   constexpr int VC = VecOf<CT>::n;
 #pragma unroll
@@ -139,12 +141,15 @@ __device__ __forceinline__ void gather_rows(const PredArgs& a, const typename Ve
     }
   } else {
 #pragma unroll
-    for (int r0 = 0; r0 < 4; ++r0)
+    for (int rr = 0; rr < 4 / RS; ++rr)
 #pragma unroll
       for (int r1 = 0; r1 < 4; ++r1) {
+        // (selects between static indices: w stays in registers)
+        const int r0 = RS == 2 ? 2 * part + rr : rr;
+        const R w0 = RS == 2 ? (part ? w[0][(rr + 2) & 3] : w[0][rr]) : w[0][rr];
         const int64_t row0 = (int64_t)(base[0] - 1 + r0) * a.g.stride[0] +
                              (int64_t)(base[1] - 1 + r1) * a.g.stride[1] + (base[D - 1] - 1);
-        const R w01 = w[0][r0] * w[1][r1];
+        const R w01 = w0 * w[1][r1];
 #pragma unroll
         for (int r2 = 0; r2 < 4; ++r2)
           vec_fma(acc, ldg_vec(base_ptr + (row0 + r2) * NG + cg), w01 * w[D - 1][r2]);
@@ -156,7 +161,12 @@ __device__ __forceinline__ void gather_rows(const PredArgs& a, const typename Ve
 // Serves points [.., a.t): the calling warp's first point is warp_first + lane / G
 // and every group advances by gstride, so all groups of a warp iterate the same
 // number of times (uniform shuffles).
-template <typename CT, typename R, int D, int G>
+// RS > 1 (3-D): the group's lanes form RS sets of G / RS lanes, set p gathering
+// the stencil rows of first-dimension offsets in its share (gather_rows); the
+// sets' partial sums are added by shuffles before the squares.  For a BF16
+// cache, whose rows hold half as many 16-byte vectors as FP32 ones, this keeps
+// every lane of the group loading.
+template <typename CT, typename R, int D, int G, int RS = 1>
 __device__ __forceinline__ void predict_groups(const PredArgs& a, int64_t warp_first, int64_t gstride) {
   using V = typename VecOf<CT>::type;
   constexpr int VC = VecOf<CT>::n;
@@ -198,9 +208,22 @@ __device__ __forceinline__ void predict_groups(const PredArgs& a, int64_t warp_f
     R sq = R(0);     // sum of squares of this lane's columns
     R mu = R(0);
     bool has_mu = false;
-    for (int cg = li; cg < NG; cg += G) {
+    constexpr int CGW = G / RS;   // lanes per row set
+    const int part = li / CGW;
+    const int iters = (NG + CGW - 1) / CGW;
+    for (int it = 0; it < iters; ++it) {
+      const int cg = li % CGW + it * CGW;
+      const bool act = cg < NG;
       R acc[VC];
-      gather_rows<CT, R, D>(a, base_ptr, NG, base, w, ok, cg, acc);
+      gather_rows<CT, R, D, RS>(a, base_ptr, NG, base, w, ok && act, cg, acc, part);
+      if (RS > 1) {
+#pragma unroll
+        for (int o = CGW; o < G; o <<= 1)
+#pragma unroll
+          for (int c = 0; c < VC; ++c) acc[c] += __shfl_xor_sync(gmask, acc[c], o, G);
+        if (part != 0) continue;
+      }
+      if (!act) continue;
       if ((cg + 1) * VC <= a.k) {
         // a group of variance columns only (all but the last one or two)
 #pragma unroll
@@ -297,11 +320,17 @@ __device__ __forceinline__ void predict_groups(const PredArgs& a, int64_t warp_f
   }
 }
 
+// rows split between lane sets: 3-D BF16 caches with a full warp per point
+template <typename CT, int D, int G> struct RowSplit {
+  static constexpr int v = (D == 3 && G == 32 && std::is_same<CT, __nv_bfloat16>::value) ? 2 : 1;
+};
+
 template <typename CT, typename R, int D, int G>
 __global__ void __launch_bounds__(256, D == 3 ? 2 : 4) k_predict(PredArgs a) {
   const int64_t groups_per_block = blockDim.x / G;
   const int64_t gid0 = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / G;
-  predict_groups<CT, R, D, G>(a, gid0 - ((threadIdx.x & 31) / G), (int64_t)gridDim.x * groups_per_block);
+  predict_groups<CT, R, D, G, RowSplit<CT, D, G>::v>(a, gid0 - ((threadIdx.x & 31) / G),
+                                                     (int64_t)gridDim.x * groups_per_block);
 }
 
 // Batched form: a persistent grid walks a list of row chunks, each inside one
@@ -329,7 +358,7 @@ __global__ void __launch_bounds__(256, D == 3 ? 2 : 4) k_predict_batched(const P
       begin = ch.begin;
     }
     __syncthreads();
-    predict_groups<CT, R, D, G>(sa, begin + (threadIdx.x / 32) * (32 / G), groups_per_block);
+    predict_groups<CT, R, D, G, RowSplit<CT, D, G>::v>(sa, begin + (threadIdx.x / 32) * (32 / G), groups_per_block);
   }
 }
 
