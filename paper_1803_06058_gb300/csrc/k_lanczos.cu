@@ -261,7 +261,6 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
   static_assert(TILE_R == 128 && TILE_T == 256, "row-quad mapping assumes 128 rows, 8 warps");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   LanczosState* st = a.st;
-  if (st->done || (MODE == MODE_UPDATE_NORM && a.detect && st->skip)) return;
   const int j = a.j;
   const int ncols = j + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -273,10 +272,6 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
       (reinterpret_cast<uintptr_t>(hp + NWARP * TILE_R) + 15) & ~uintptr_t(15));  // [stages]
   __shared__ Acc red[NWARP];
 
-  if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
-    const double* c = MODE == MODE_UPDATE_DOT ? st->coef : st->coef2;
-    for (int i = tid; i < ncols; i += TILE_T) cf[i] = (T)c[i];
-  }
   const int64_t ntiles = a.n_pad / TILE_R;
   if (tid == 0) {
     for (int s = 0; s < a.stages; ++s) mbar_init(&bar[s], 1);
@@ -300,12 +295,32 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
       tma_load_2d(dst + (size_t)b * a.bc * TILE_R, &a.qmap, (int)(tile * TILE_R), b * a.bc, &bar[s]);
     bulk_g2s(dst + (size_t)a.kpad * TILE_R, a.y + tile * TILE_R, col_bytes, &bar[s]);
   };
-  if (tid == 0) {
-    for (int s = 0; s < a.stages; ++s) {
-      int64_t t = blockIdx.x + (int64_t)s * gridDim.x;
-      if (t < ntiles) issue(t, s);
+  auto fill = [&]() {
+    if (tid == 0) {
+      for (int s = 0; s < a.stages; ++s) {
+        int64_t t = blockIdx.x + (int64_t)s * gridDim.x;
+        if (t < ntiles) issue(t, s);
+      }
     }
+  };
+  // Launched as a programmatic dependent of the previous sweep, the kernel may
+  // start while that sweep's last CTA still merges.  The update + dot sweep
+  // reads only what the sweep before it read (Q_j and y), so its ring fills
+  // before the wait; everything else waits for the previous grid first.
+  constexpr bool early = MODE == MODE_UPDATE_DOT;
+  if (early) fill();
+  grid_dep_wait();
+  if (st->done || (MODE == MODE_UPDATE_NORM && a.detect && st->skip)) {
+    if (early && tid == 0)   // let the copies already issued land before the shared memory is released
+      for (int s = 0; s < a.stages; ++s)
+        if (blockIdx.x + (int64_t)s * gridDim.x < ntiles) mbar_wait_bounded(&bar[s], 0u);
+    return;
   }
+  if (MODE == MODE_UPDATE_DOT || MODE == MODE_UPDATE_NORM) {
+    const double* c = MODE == MODE_UPDATE_DOT ? st->coef : st->coef2;
+    for (int i = tid; i < ncols; i += TILE_T) cf[i] = (T)c[i];
+  }
+  if (!early) fill();
 
   Acc acc[KPW];
 #pragma unroll
@@ -399,6 +414,9 @@ __global__ void __launch_bounds__(TILE_T, 2) k_lanczos_tile(const __grid_constan
     }
   }
 
+  // the next sweep may launch now: it waits for this grid before it reads
+  // what the merge below writes
+  grid_dep_launch();
   // every issued stage has been consumed: the ring is free for the merge
   sweep_epilogue<T, MODE, KPW>(a, acc, nacc, red, reinterpret_cast<double2*>(smem_raw), (int)gridDim.x,
                               (int)blockIdx.x);
@@ -661,6 +679,23 @@ inline TileGeom tile_geom(int kpad, int kcols, size_t elem) {
 template <typename T>
 love_status make_qmap(T* Q, int64_t ldq, int kcols, int bc, CUtensorMap* out);
 
+// a launch that may begin before the previous one on the stream has finished
+// (programmatic stream serialisation: the kernel orders its own reads)
+template <typename K, typename A>
+love_status launch_dependent(K kern, int grid, int threads, size_t smem, cudaStream_t s, const A& arg) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cuda_check(cudaLaunchKernelEx(&cfg, kern, arg));
+}
+
 template <typename T, int MODE>
 love_status tile_run(TileArgs<T> a, cudaStream_t s) {
   const int ncols = a.j + 1;
@@ -699,8 +734,8 @@ love_status tile_run(TileArgs<T> a, cudaStream_t s) {
     LOVE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE_T, smem));     \
     per_sm = std::min(std::max(per_sm, 1), tg.ctas);                                           \
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms());              \
-    LOVE_COUNT_LAUNCH(); kern<<<grid, TILE_T, smem, s>>>(a);                                   \
-    return cuda_check(cudaGetLastError());                                                     \
+    LOVE_COUNT_LAUNCH();                                                                       \
+    return launch_dependent(kern, grid, TILE_T, smem, s, a);                                   \
   }
   LOVE_TILE_CASE(1)
   LOVE_TILE_CASE(2)
