@@ -203,45 +203,58 @@ __global__ void k_scatter_multi(GridDev g, const T* __restrict__ xs, const int* 
   }
 }
 
-// out[:, c] = W Q[:, c] on a 1-D grid (FP32), a CTA per SMQ_NB grid nodes: the
-// points of the nodes' cells (sorted order) pass through shared memory
-// SMQ_PT at a time -- Q's columns read once, coalesced along the points, and
-// transposed -- with each point's stencil (first node, 4 Keys weights)
-// computed once; thread c of each half of the CTA keeps column c's sums for
-// the block's nodes in shared memory (Dot2 pairs, as k_scatter_multi), the
-// two halves taking the even and the odd points of a tile, and the halves'
-// sums are merged at the end: every sum is taken in a fixed order.  The
-// warp-per-node form read every value of Q once per node of its stencil.
-constexpr int SMQ_NB = 32, SMQ_PT = 64, SMQ_COLS = 128;
+// out[:, c] = W Q[:, c] on a 1-D grid (FP32), a CTA of SMQ_T threads per
+// SMQ_NB grid nodes, thread c summing column c.  The points of the nodes'
+// cells (sorted order) pass through shared memory SMQ_PT at a time -- Q's
+// columns read once, coalesced along the points and transposed, the next
+// tile's values prefetched into registers -- with each point's stencil (first
+// node, 4 Keys weights) computed once.  The points arrive by cell, and a node
+// n takes points from cells n - 2 .. n + 1 only, so a thread keeps the four
+// nodes of the current cell's stencil in registers (Dot2 pairs, as
+// k_scatter_multi) and retires the lowest one when the walk moves past its
+// last cell: every sum is taken in point order.  The warp-per-node form read
+// every value of Q once per node of its stencil.
+constexpr int SMQ_NB = 32, SMQ_PT = 64, SMQ_T = 128, SMQ_COLS_MAX = 128;
 constexpr size_t smq_smem(int ncol) {
-  return sizeof(float2) * 2 * SMQ_NB * SMQ_COLS + sizeof(float) * (size_t)SMQ_PT * (ncol + 1) +
-         sizeof(float4) * SMQ_PT + sizeof(int) * SMQ_PT;
+  return sizeof(float) * (size_t)SMQ_PT * (ncol + 1) + sizeof(float4) * SMQ_PT + sizeof(int) * SMQ_PT +
+         sizeof(float) * (size_t)SMQ_NB * (ncol + 1);
 }
-__global__ void __launch_bounds__(256) k_scatter_multi_1d(GridDev g, const float* __restrict__ xs,
-                                                          const int* __restrict__ cell_start,
-                                                          const float* __restrict__ Q, int64_t ldq, int ncol,
-                                                          float* __restrict__ out, int64_t ldo) {
+__global__ void __launch_bounds__(SMQ_T) k_scatter_multi_1d(GridDev g, const float* __restrict__ xs,
+                                                            const int* __restrict__ cell_start,
+                                                            const float* __restrict__ Q, int64_t ldq, int ncol,
+                                                            float* __restrict__ out, int64_t ldo) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* acc = reinterpret_cast<float2*>(smem_raw);                      // [2][SMQ_NB][SMQ_COLS]
-  float* qs = reinterpret_cast<float*>(acc + 2 * SMQ_NB * SMQ_COLS);      // [SMQ_PT][ncol + 1]
+  float* qs = reinterpret_cast<float*>(smem_raw);                         // [SMQ_PT][ncol + 1]
   float4* pw = reinterpret_cast<float4*>(qs + (size_t)SMQ_PT * (ncol + 1));
   int* pbase = reinterpret_cast<int*>(pw + SMQ_PT);
-  const int tid = threadIdx.x;
+  float* os = reinterpret_cast<float*>(pbase + SMQ_PT);                  // [SMQ_NB][ncol + 1]
+  const int tid = threadIdx.x, c = tid;
   const int n0 = blockIdx.x * SMQ_NB, n1 = min(n0 + SMQ_NB, g.m);
-  for (int i = tid; i < 2 * SMQ_NB * SMQ_COLS; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
   const int clo = max(n0 - 2, 0), chi = min(n1, g.g[0] - 1);
   const int p_begin = cell_start[clo], p_end = cell_start[chi + 1];
-  const int half = tid >> 7, c = tid & 127;   // thread: column c, points of parity `half`
-  float2* my = acc + (size_t)half * SMQ_NB * SMQ_COLS;
-  // a tile's Q values in registers (the next tile's loads are in flight while
-  // the current one is summed): element i = tid + 256 e of the tile
-  constexpr int PRE = SMQ_COLS * SMQ_PT / 256;
+  // the window: nodes lo .. lo + 3 (the stencil of cell lo + 1)
+  DotAccF w0, w1, w2, w3;
+  w0.zero();
+  w1.zero();
+  w2.zero();
+  w3.zero();
+  int lo = clo - 1;
+  auto retire = [&]() {   // node lo is complete: store it, slide the window by one node
+    const int nd = lo - n0;
+    if (nd >= 0 && nd < n1 - n0 && c < ncol) os[nd * (ncol + 1) + c] = (float)w0.value();
+    w0 = w1;
+    w1 = w2;
+    w2 = w3;
+    w3.zero();
+    ++lo;
+  };
+  constexpr int PRE = SMQ_COLS_MAX * SMQ_PT / SMQ_T;
   float pre[PRE];
   auto load_tile = [&](int p0) {
     const int np = min(SMQ_PT, p_end - p0);
 #pragma unroll
     for (int e = 0; e < PRE; ++e) {
-      const int i = tid + 256 * e, cc = i / SMQ_PT, pp = i - cc * SMQ_PT;
+      const int i = tid + SMQ_T * e, cc = i / SMQ_PT, pp = i - cc * SMQ_PT;
       pre[e] = (cc < ncol && pp < np) ? Q[(int64_t)cc * ldq + p0 + pp] : 0.f;
     }
   };
@@ -251,48 +264,34 @@ __global__ void __launch_bounds__(256) k_scatter_multi_1d(GridDev g, const float
     __syncthreads();   // the previous tile is consumed
 #pragma unroll
     for (int e = 0; e < PRE; ++e) {
-      const int i = tid + 256 * e, cc = i / SMQ_PT, pp = i - cc * SMQ_PT;
+      const int i = tid + SMQ_T * e, cc = i / SMQ_PT, pp = i - cc * SMQ_PT;
       if (cc < ncol) qs[pp * (ncol + 1) + cc] = pre[e];
     }
     if (tid < SMQ_PT) {
       int base = 0;
       float w[4] = {0.f, 0.f, 0.f, 0.f};
       if (tid < np) keys_weights(grid_coord(xs[p0 + tid], g, 0), g.g[0], base, w);
-      pbase[tid] = base - 1;   // the stencil's first node
+      pbase[tid] = base - 1;   // the stencil's first node (nondecreasing along the sorted points)
       pw[tid] = make_float4(w[0], w[1], w[2], w[3]);
     }
     __syncthreads();
     if (p0 + SMQ_PT < p_end) load_tile(p0 + SMQ_PT);
-    if (c < ncol) {
-      for (int pp = half; pp < np; pp += 2) {
-        const float q = qs[pp * (ncol + 1) + c];
-        const float4 w4 = pw[pp];
-        const float wr[4] = {w4.x, w4.y, w4.z, w4.w};
-        const int b = pbase[pp] - n0;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int nd = b + r;
-          if (nd < 0 || nd >= n1 - n0) continue;
-          float2& a = my[nd * SMQ_COLS + c];
-          DotAccF d;
-          d.s = a.x;
-          d.c = a.y;
-          d.add_prod(wr[r], q);
-          a = make_float2(d.s, d.c);
-        }
-      }
+    for (int pp = 0; pp < np; ++pp) {
+      const int b = pbase[pp];
+      while (lo < b) retire();
+      const float q = c < ncol ? qs[pp * (ncol + 1) + c] : 0.f;
+      const float4 w4 = pw[pp];
+      w0.add_prod(w4.x, q);
+      w1.add_prod(w4.y, q);
+      w2.add_prod(w4.z, q);
+      w3.add_prod(w4.w, q);
     }
   }
+  while (lo < n1) retire();
   __syncthreads();
-  for (int i = tid; i < SMQ_NB * ncol; i += blockDim.x) {
+  for (int i = tid; i < SMQ_NB * ncol; i += SMQ_T) {
     const int cc = i / SMQ_NB, nd = i - cc * SMQ_NB;
-    if (n0 + nd >= n1) continue;
-    DotAccF d;
-    d.s = acc[nd * SMQ_COLS + cc].x;
-    d.c = acc[nd * SMQ_COLS + cc].y;
-    const float2 o = acc[(size_t)SMQ_NB * SMQ_COLS + nd * SMQ_COLS + cc];
-    d.merge(o.x, o.y);
-    out[(int64_t)cc * ldo + n0 + nd] = (float)d.value();
+    if (n0 + nd < n1) out[(int64_t)cc * ldo + n0 + nd] = os[nd * (ncol + 1) + cc];
   }
 }
 
@@ -1064,11 +1063,11 @@ love_status scatter_multi(love_ski* ski, const T* Q, int64_t ldq, int ncol, T* o
     return cuda_check(cudaGetLastError());
   }
   int blocks = (int)std::min<int64_t>((g.m * 32 + 255) / 256, (int64_t)num_sms() * 16);
-  if (sizeof(T) == 4 && g.dim == 1 && ncol <= SMQ_COLS) {
+  if (sizeof(T) == 4 && g.dim == 1 && ncol <= SMQ_COLS_MAX) {
     const size_t sm = smq_smem(ncol);
     LOVE_TRY(allow_smem(k_scatter_multi_1d, sm));
     LOVE_COUNT_LAUNCH();
-    k_scatter_multi_1d<<<(unsigned)ceil_div(g.m, SMQ_NB), 256, sm, s>>>(
+    k_scatter_multi_1d<<<(unsigned)ceil_div(g.m, SMQ_NB), SMQ_T, sm, s>>>(
         g, (const float*)ski->xs, ski->cell_start, (const float*)Q, ldq, ncol, (float*)out, ldo);
     return cuda_check(cudaGetLastError());
   }
