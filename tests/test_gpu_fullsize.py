@@ -1,8 +1,9 @@
 """Full-size parity on the 1-D, n = 1e6, m = 1e4, k = 100, FP32 workload, in the
 launch configuration bench.py times: the GPU cache and all 1e6 predictive
 variances are checked by properties that hold at any size (finite, 0 <= var <= p,
-k_eff = k), and 2,000 sampled test points against the FP64 oracle LOVE run on
-the same data at the same k (|d var| / p <= 1e-6, the FP32 tolerance)."""
+k_eff = k), and every one of the 1e6 variances against the FP64 oracle LOVE run
+on the same data at the same k (|d var| / p <= 1e-6, the FP32 tolerance; the
+oracle's O(k) predict runs on the host in chunks of 1e5 points)."""
 import numpy as np
 import pytest
 
@@ -42,12 +43,13 @@ def test_c2_fullsize_variances(love):
     assert cache.device_status()["domain_errors"] == 0
     # oracle on the same data, same k, FP64
     oc = ol.precompute(os_.SKI(grid, x, wl.noise, y), k=wl.k, want_mean=False)
-    idx = np.random.default_rng(0).choice(xs.shape[0], 2000, replace=False)
-    _, v_ref = ol.predict(oc, xs[idx])
-    err = np.abs(v[idx] - v_ref) / p[idx]
-    rel = np.abs(v[idx] - v_ref) / v_ref
-    print(f"C2 |dvar|/p max {err.max():.3e} median {np.median(err):.3e}; "
-          f"relative median {np.median(rel):.3e} max {rel.max():.3e}; var/p median {np.median(v_ref / p[idx]):.3e}")
+    v_ref = np.empty_like(v)
+    for a in range(0, xs.shape[0], 100_000):
+        _, v_ref[a:a + 100_000] = ol.predict(oc, xs[a:a + 100_000])
+    err = np.abs(v - v_ref) / p
+    rel = np.abs(v - v_ref) / v_ref
+    print(f"C2 all {xs.shape[0]} points: |dvar|/p max {err.max():.3e} median {np.median(err):.3e}; "
+          f"relative median {np.median(rel):.3e}; var/p median {np.median(v_ref / p):.3e}")
     assert err.max() <= 1e-6
 
 
