@@ -204,6 +204,26 @@ cudaStream_t aux_stream() {
   return pool[next++ % pool.size()];
 }
 
+// High-priority streams (one per device, kept for the process's lifetime) for
+// the Lanczos run while the mean solve runs beside it on an auxiliary stream:
+// the block scheduler then fills freed SMs with the Lanczos kernels' CTAs first.
+cudaStream_t priority_stream() {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> per_dev;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1, nullptr);
+  if (!per_dev[dev]) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest) == cudaSuccess) per_dev[dev] = st;
+    else cudaGetLastError();
+  }
+  return per_dev[dev];
+}
+
 struct PhaseEvents {
   cudaEvent_t e[5] = {};
   bool ok = true;
@@ -617,8 +637,26 @@ static love_status precompute_impl(love_ski* ski, const love_precompute_opts* o,
     keff = pre->k_eff;
     skipped = pre->skipped;
   } else {
-    rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, s,
+    // beside a mean solve, the Lanczos run goes to a high-priority stream,
+    // ordered after the caller's stream and joined back to it
+    cudaStream_t ls = grid_cg ? priority_stream() : nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (ls && (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+               cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess ||
+               cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(ls, fork, 0) != cudaSuccess)) {
+      cudaGetLastError();
+      ls = nullptr;
+    }
+    rc = lanczos_run<T>(ski, k, tau, eta, Q, ldq, alpha.data(), beta.data(), &keff, &skipped, ls ? ls : s,
                         (flags & LOVE_TIME_REORTH) ? &reorth_ms : nullptr, lowsync);
+    if (ls) {
+      love_status jrc = cuda_check(cudaEventRecord(join, ls));
+      if (jrc == LOVE_OK) jrc = cuda_check(cudaStreamWaitEvent(s, join, 0));
+      if (jrc != LOVE_OK) jrc = cuda_check(cudaStreamSynchronize(ls));   // ordered by the host instead
+      if (rc == LOVE_OK) rc = jrc;
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
   }
   ev.record(1, s);
   if (rc != LOVE_OK) {
